@@ -1,0 +1,87 @@
+"""Pins of the oracle's adjoint: dot-product test of the post-processing adjoint and
+central finite differences of a waveform-power loss w.r.t. heights and NRCS."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+
+
+def _loss_and_grad_y(Y, target):
+    pw = np.abs(Y) ** 2
+    return float(((pw - target) ** 2).sum()), 4.0 * (pw - target) * Y
+
+
+def _safe_scatterers(orc, rd, pf, sc, pulses, nd, count, seed):
+    """Scatterers whose gate and bin coordinates stay well away from integer edges."""
+    ok = np.ones(sc["x"].size, bool)
+    for p in pulses:
+        g, b, gc, bc = orc.cells(rd, pf, sc, p, nd)
+        ok &= (g >= 0) & (g < rd.n_gates)
+        ok &= np.abs(gc - np.round(gc)) > 2e-3
+        ok &= np.abs(bc - np.round(bc)) > 2e-2
+    idx = np.nonzero(ok)[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.choice(idx, size=count, replace=False)
+
+
+def _perturbed(sc, key, n, value):
+    s2 = dict(sc)
+    a = sc[key].copy()
+    a[n] = value
+    s2[key] = a
+    return s2
+
+
+def test_synth_adjoint_dot_product(orc):
+    """<G_Y, synth(T)> = <synth_grad(G_Y), T> (real inner product Re sum conj(a) b)."""
+    S, G, nd, nf = 5, 7, 16, 12
+    T = sg.random_spectra(S, G, nd, seed=1)
+    P = (S - 2) * nf + 5
+    GY = sg.random_iq(P, G, seed=2)
+    for w in ("sqrt_linear", "sqrt_raised_cosine", "linear"):
+        Y = orc.synth(T, 0, nf, 3, P, w)
+        GT = orc.synth_grad(GY, S, 0, nf, nd, 3, w)
+        lhs = np.real(np.vdot(GY, Y))
+        rhs = np.real(np.vdot(GT, T))
+        assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["fast", "regular"])
+def test_gradient_vs_central_differences(orc, mode):
+    rd = sg.RadarParams()
+    P, nf, nd = 128, 64, 64
+    pf = sg.nadir_track(P)
+    sc = sg.sea_surface(24, 4)
+    S = (P - 1) // nf + 2
+
+    def forward(scene):
+        if mode == "fast":
+            T = orc.doppler_spectra(rd, pf, scene, 0, S, nf, nd)
+            return orc.synth(T, 0, nf, 0, P, "sqrt_raised_cosine")
+        return orc.direct_sum(rd, pf, scene, 0, P)
+
+    Y = forward(sc)
+    target = sg.target_waveform(P, rd.n_gates, 4242, (np.abs(Y) ** 2).mean(axis=0))
+    L0, GY = _loss_and_grad_y(Y, target)
+    if mode == "fast":
+        GT = orc.synth_grad(GY, S, 0, nf, nd, 0, "sqrt_raised_cosine")
+        gz, gs = orc.fast_grad(rd, pf, sc, 0, nf, GT)
+        pulses = [i * nf for i in range(S)]
+    else:
+        gz, gs = orc.direct_grad(rd, pf, sc, 0, GY)
+        pulses = list(range(0, P, 7))
+    picks = _safe_scatterers(orc, rd, pf, sc, pulses, nd, 6, seed=5)
+    h = 2.0 ** -16
+    for n in picks:
+        z0 = sc["z"][n]
+        zp, zm = np.float32(z0 + h), np.float32(z0 - h)
+        Lp, _ = _loss_and_grad_y(forward(_perturbed(sc, "z", n, zp)), target)
+        Lm, _ = _loss_and_grad_y(forward(_perturbed(sc, "z", n, zm)), target)
+        fd = (Lp - Lm) / (float(zp) - float(zm))
+        assert gz[n] == pytest.approx(fd, rel=2e-4, abs=1e-6 * np.abs(gz).max())
+        s0 = sc["nrcs"][n]
+        sp, sm = np.float32(s0 * (1 + 2 ** -10)), np.float32(s0 * (1 - 2 ** -10))
+        Lp, _ = _loss_and_grad_y(forward(_perturbed(sc, "nrcs", n, sp)), target)
+        Lm, _ = _loss_and_grad_y(forward(_perturbed(sc, "nrcs", n, sm)), target)
+        fd = (Lp - Lm) / (float(sp) - float(sm))
+        assert gs[n] == pytest.approx(fd, rel=2e-4, abs=1e-6 * np.abs(gs).max())
