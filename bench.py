@@ -1,0 +1,425 @@
+"""Benchmark of the fast-mode hot path on GB300.
+
+Workload (default): the 2048 x 2048 seeded sea surface (4,194,304 scatterers, 1 m
+grid), nadir Ku-band altimeter at 800 km, 4096 pulses at 18 kHz, spectra every
+n_fast = 64 pulses (65 spectra of 128 gates x 64 Doppler bins), square-root
+raised-cosine blend, split precision.  One step = the whole fast-mode path:
+Algorithm 1 scatterer pass for every update (rsim_doppler_accumulate) and the
+post-processing (rsim_synth_pulses), inputs resident in HBM.
+
+Prints ONE JSON line (rank 0).  `value` is fast-mode IQ pulses per second over
+all ranks; also reported: scatterer-updates/s of the dominant kernel with its
+roofline, the regular-mode direct sum on the same surface (scatterer-pulse
+contributions/s), the FP64 path and the split-vs-FP64 error, an end-to-end
+figure through host buffers, the oracle on the host cores, and SM clocks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rsim|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scenegen as sg  # noqa: E402
+
+METRIC = "scatterer-pulse contribs/s & fast-mode IQ pulses/s at stated err vs FP64, % roofline"
+UNIT = "IQ pulses/s"
+# FP32-pipe operations of the split-path evaluation of one scatterer at one update
+# (two-way range excess, gate, antenna angle, amplitude exponent, phase, pulse-pair
+# Doppler bin, cell key), counted from the formulation; plus 3 MUFU (ex2, sin, cos).
+OPS_PER_UPDATE = 78
+OPS_PER_PULSE_REGULAR = 50
+SMS = 152
+LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- oracle leg
+def oracle_fast_sample(radar, platform, scene, n_pulses, fp, target_s=10.0, threads=None):
+    """Time the FP64 oracle (as it stands) on the first n_s scatterers for the whole
+    fast-mode path (all spectra + post-processing); n_s chosen for ~target_s seconds.
+    Returns (IQ pulses/s extrapolated to the full scene, cores, sample description, seconds)."""
+    import oracle
+    orc = oracle.Oracle(threads)
+    N = scene["x"].size
+    u0, S = 0, (n_pulses - 1) // fp.n_fast + 2
+
+    def sub(n):
+        return {k: (v[:n] if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
+
+    n_probe = min(N, 1 << 15)
+    t = time.perf_counter()
+    orc.doppler_spectra(radar, platform, sub(n_probe), u0, S, fp.n_fast, fp.n_doppler)
+    per = (time.perf_counter() - t) / n_probe
+    n_s = int(min(N, max(n_probe, target_s / max(per, 1e-12))))
+    n_s = max(1024, (n_s // 1024) * 1024) if N >= 1024 else N
+    sc = sub(n_s)
+    t = time.perf_counter()
+    T = orc.doppler_spectra(radar, platform, sc, u0, S, fp.n_fast, fp.n_doppler)
+    t_acc = time.perf_counter() - t
+    t = time.perf_counter()
+    orc.synth(T, u0, fp.n_fast, 0, n_pulses, fp.window)
+    t_syn = time.perf_counter() - t
+    t_full = t_acc * (N / n_s) + t_syn
+    desc = ("first %d of %d scatterers, all %d spectra + post-processing of %d pulses; "
+            "scatterer pass scaled by %.2f" % (n_s, N, S, n_pulses, N / n_s))
+    return n_pulses / t_full, orc.threads, desc, t_acc + t_syn
+
+
+# --------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rsim", choices=["rsim", "reference"])
+    ap.add_argument("--precision", default="split", choices=["split", "fp64"])
+    ap.add_argument("--L", type=int, default=None, help="surface side (default: 2048)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e / regular / FP64 / oracle legs (profiling runs)")
+    args = ap.parse_args()
+
+    rank, world, local = dist_env()
+    c = sg.config(1)
+    L = args.L or c["L"]
+    rd, pf, fp, P = c["radar"], c["platform"], c["fast"], c["n_pulses"]
+    workload = "fast_%dx%d_p%d" % (L, L, P)
+    S = (P - 1) // fp.n_fast + 2
+    N = L * L
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, rd, pf, fp, P, L, c, workload, S)
+        return
+
+    import torch
+    import paper_2408_11472_gb300 as rsim
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev_name = "cuda:%d" % local
+
+    # Each rank simulates its own independent surface realization (weak scaling).
+    seed = c["seed"] + 1000 * rank
+    scene = sg.sea_surface(L, seed)
+    dev = rsim.Scatterers.from_arrays(scene, dev_name)
+    ws = torch.empty(rsim.workspace_size(S, rd.n_gates, fp.n_doppler), dtype=torch.uint8,
+                     device=dev_name)
+    T = torch.zeros((S, rd.n_gates, fp.n_doppler), dtype=torch.complex64, device=dev_name)
+    Y = torch.empty((P, rd.n_gates), dtype=torch.complex64, device=dev_name)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev_name)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        T.zero_()
+        rsim.doppler_accumulate(rd, pf, dev, 0, S, fp.n_fast, fp.n_doppler, args.precision,
+                                out=T, workspace=ws)
+        rsim.synth_pulses(rd, T, 0, fp.n_fast, 0, P, fp.window, out=Y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    t0 = time.perf_counter()
+    for e0, e1, e2 in ev:
+        flush.fill_(1.0)                       # evict L2 between steps (not timed)
+        e0.record(stream)
+        T.zero_()
+        rsim.doppler_accumulate(rd, pf, dev, 0, S, fp.n_fast, fp.n_doppler, args.precision,
+                                out=T, workspace=ws)
+        e1.record(stream)
+        rsim.synth_pulses(rd, T, 0, fp.n_fast, 0, P, fp.window, out=Y)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in ev]
+    acc_ms = [e0.elapsed_time(e1) for e0, e1, e2 in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev_name, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * P * args.steps / (total_ms / 1e3)
+    acc_mean_ms = statistics.mean(acc_ms)
+
+    units = N * S                           # scatterer-updates per launch
+    achieved = units * OPS_PER_UPDATE / (acc_mean_ms / 1e3) / 1e12
+    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "accumulate_split_kernel<DOPPLER=true>",
+                "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "ops_per_unit": OPS_PER_UPDATE, "units_per_launch": units,
+                "launch_ms": round(acc_mean_ms, 4),
+                "hbm_bytes_per_launch_algorithmic": N * 28,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock), 1 op/lane/clk"}
+    prof_traffic = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_traffic):
+        try:
+            tr = json.load(open(prof_traffic))
+            if tr.get("workload") == workload and tr.get("kernel_hash") == kernel_hash():
+                roofline["traffic"] = tr.get("dram_bytes_per_launch")
+        except Exception:
+            pass
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_name)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "split" else "f64",
+        "data": "synthetic (seeded linear deep-water wave field, lognormal NRCS)",
+        "config": {"workload": workload, "scatterers": N, "pulses": P, "n_fast": fp.n_fast,
+                   "spectra": S, "gates": rd.n_gates, "doppler_bins": fp.n_doppler,
+                   "window": fp.window, "precision": args.precision,
+                   "l2": "flushed between steps (512 MiB write, untimed)",
+                   "parallelism": "replicas: one independent surface per rank"},
+        "contribs_per_s": {"scatterer_updates_per_s": round(world * units * args.steps / (total_ms / 1e3), 1),
+                           "equivalent_scatterer_pulses_per_s": round(world * N * P * args.steps / (total_ms / 1e3), 1)},
+        "roofline": roofline,
+        "gpu_launches": 3 * args.steps,
+        "wall_s_timed_region": round(wall, 4),
+    }
+    if clk is not None:
+        line["clocks"] = clk
+    line.update(extras)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rsim_internal.cuh", "accumulate.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2408_11472_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_name):
+    out = {}
+    N = dev.n
+    # -- end to end through the public API with host buffers (pinned), copies timed.
+    keys = ("x", "y", "z", "vx", "vy", "vz", "nrcs")
+    host = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).pin_memory() for k in keys}
+    dbuf = {k: torch.empty(N, dtype=torch.float32, device=dev_name) for k in keys}
+    yhost = torch.empty((P, rd.n_gates), dtype=torch.complex64).pin_memory()
+    dsc = rsim.Scatterers(**dbuf, origin=scene["origin"], area=scene["area"])
+    stream = torch.cuda.current_stream()
+
+    def e2e_step():
+        for k in keys:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        rsim.simulate_fast(rd, pf, dsc, P, fp.n_fast, fp.n_doppler, fp.window, args.precision,
+                           workspace=ws, spectra=T, out=Y)
+        yhost.copy_(Y, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    k = max(3, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3 / k
+    out["e2e"] = {"value": round(P / t_e2e, 1), "unit": UNIT,
+                  "h2d_bytes_per_step": int(7 * 4 * N),
+                  "d2h_bytes_per_step": int(P * rd.n_gates * 8),
+                  "ms_per_step": round(t_e2e * 1e3, 4)}
+
+    # -- regular mode on the same surface: direct sum over a block of pulses.
+    Pr = 256
+    Yr = torch.zeros((Pr, rd.n_gates), dtype=torch.complex64, device=dev_name)
+    wsr = torch.empty(rsim.workspace_size(Pr, rd.n_gates, 1), dtype=torch.uint8, device=dev_name)
+    for _ in range(2):
+        rsim.direct_sum(rd, pf, dev, 1920, Pr, "split", out=Yr, workspace=wsr)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps = 3
+    for _ in range(reps):
+        rsim.direct_sum(rd, pf, dev, 1920, Pr, "split", out=Yr, workspace=wsr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_reg = e0.elapsed_time(e1) / 1e3 / reps
+    reg_rate = N * Pr / t_reg
+    t_fast = None
+    # -- FP64 path and split-vs-FP64 error on the full workload.
+    T64 = torch.zeros((S, rd.n_gates, fp.n_doppler), dtype=torch.complex128, device=dev_name)
+    ws64 = ws
+    rsim.doppler_accumulate(rd, pf, dev, 0, S, fp.n_fast, fp.n_doppler, "fp64", out=T64,
+                            workspace=ws64)
+    Y64 = rsim.synth_pulses(rd, T64, 0, fp.n_fast, 0, P, fp.window)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    T64.zero_()
+    rsim.doppler_accumulate(rd, pf, dev, 0, S, fp.n_fast, fp.n_doppler, "fp64", out=T64,
+                            workspace=ws64)
+    rsim.synth_pulses(rd, T64, 0, fp.n_fast, 0, P, fp.window, out=Y64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    Ts, Ysp = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, "split",
+                                 workspace=ws)
+    torch.cuda.synchronize()
+
+    def rl2(a, b):
+        return float(torch.linalg.vector_norm(a.to(torch.complex128) - b) /
+                     torch.linalg.vector_norm(b))
+
+    e0.record(stream)
+    rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, "split",
+                       workspace=ws, spectra=Ts, out=Ysp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_fast = e0.elapsed_time(e1) / 1e3
+    out["regular_mode"] = {"scatterer_pulse_contribs_per_s": round(reg_rate, 1),
+                           "pulses": Pr, "ms": round(t_reg * 1e3, 3),
+                           "roofline_frac_alu": round(reg_rate * OPS_PER_PULSE_REGULAR /
+                                                      (SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6), 4)}
+    out["fast_vs_regular"] = {
+        "fast_equivalent_contribs_per_s": round(N * P / t_fast, 1),
+        "regular_contribs_per_s": round(reg_rate, 1),
+        "speedup": round((N * P / t_fast) / reg_rate, 2)}
+    out["split_vs_fp64"] = {"fp64_iq_pulses_per_s": round(P / t64, 1),
+                            "rel_l2_spectra": rl2(Ts, T64), "rel_l2_iq": rl2(Ysp, Y64),
+                            "note": "end-to-end on the full workload, bin/gate flips included"}
+    # -- the FP64 oracle on the host cores, bounded sample of the same workload.
+    try:
+        v, cores, desc, secs = oracle_fast_sample(rd, pf, scene, P, fp)
+        out["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": cores,
+                               "kind": "oracle", "sample": desc, "seconds": round(secs, 2)}
+    except Exception as e:  # the oracle needs gcc on the host
+        out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                               "sample": "failed: %s" % e}
+    return out
+
+
+def run_reference(args, rd, pf, fp, P, L, c, workload, S):
+    """The oracle (FP64, host cores) as the reference arm: each step is a bounded sample
+    of the same workload; the figure is extrapolated to the full scene."""
+    scene = sg.sea_surface(L, c["seed"])
+    per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    vals, secs = [], 0.0
+    cores, desc = None, ""
+    for i in range(args.warmup + args.steps):
+        v, cores, desc, s = oracle_fast_sample(rd, pf, scene, P, fp, target_s=per_step)
+        if i >= args.warmup:
+            vals.append(v)
+            secs += s
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * P / value, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded linear deep-water wave field, lognormal NRCS)",
+            "config": {"workload": workload, "scatterers": L * L, "pulses": P,
+                       "n_fast": fp.n_fast, "spectra": S, "gates": rd.n_gates,
+                       "doppler_bins": fp.n_doppler, "window": fp.window},
+            "impl": "reference",
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

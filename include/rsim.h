@@ -1,0 +1,220 @@
+/*
+ * rsim.h -- C ABI of the GB300 (sm_103a) radar raw-data summation library.
+ *
+ * The library computes the coherent summation of many moving sea-surface
+ * scatterers into complex IQ range gates, as described in arXiv 2408.11472
+ * ("High Performance Simulation of Spaceborne Radar for Remote-Sensing
+ * Oceanography"):
+ *
+ *   - regular mode (Section II.A, Fig. 1 step 4; n_fast = 0 in Section IV):
+ *       Y[p, g] = sum_n C_n(t_p) [gate_n(t_p) = g]          -> rsim_direct_sum
+ *   - fast mode (Section III): one scatterer pass per surface update i
+ *     (pulse p_i = i * n_fast) accumulating a Doppler spectrum per range gate
+ *     (Algorithm 1, pulse-pair Doppler + rasterize)          -> rsim_doppler_accumulate
+ *     then a batched 1-D inverse FFT per gate, the Eq. (1) weights and the sum
+ *     of weighted segments (Section III.B post-processing)  -> rsim_synth_pulses
+ *   - adjoints of the three operations (gradients of a real loss w.r.t.
+ *     scatterer heights and NRCS)                            -> rsim_*_backward
+ *
+ * Model (every function uses the same one):
+ *   t_p = p / PRF; scatterer n at s(t) = origin + r_n + v_n t; platform at
+ *   P(t) = p0 + v t; d = P - s; R = |d|; range-window reference
+ *   r_ref(t) = r_ref0 + r_ref_rate t;
+ *   gate = floor((R - r_ref) / gate_width + n_gates / 2), dropped unless
+ *   0 <= gate < n_gates;
+ *   off-nadir angle theta = atan2(|d_xy|, d_z);
+ *   C = sqrt(nrcs * area) * exp(-2 ln2 theta^2 / beamwidth^2) * (r_ref / R)^2
+ *       * exp(-j 4 pi R / lambda),  lambda = c / carrier;
+ *   pulse-pair Doppler of the pair (p_i, p_i + 1): nu = phase advance of C per
+ *   pulse in cycles, wrapped to [-1/2, 1/2); bin = floor(nu * n_doppler + 1/2)
+ *   mod n_doppler (so bin k holds the tone exp(+j 2 pi k m / n_doppler));
+ *   inverse transform unnormalised: s_i[g, m] = sum_k T[i, g, k] e^{+j 2 pi k m / n_doppler};
+ *   Y[x, g] = W(|p_i - x| / n_fast) s_i[g, (x - p_i) mod n_doppler]
+ *           + W(|p_{i+1} - x| / n_fast) s_{i+1}[g, (x - p_{i+1}) mod n_doppler],
+ *   i = floor(x / n_fast), with the blend window W of rsim_window.
+ *
+ * Conventions shared by every entry point:
+ *   - Memory: every array argument is a DEVICE pointer to caller-owned memory
+ *     (structs themselves are host memory, read during the call only).  The
+ *     library makes no allocation of its own; scratch space is the explicit
+ *     workspace argument, sized by rsim_workspace_size().
+ *   - Execution: asynchronous on the given stream (0 = legacy default stream).
+ *     A call only enqueues work; outputs are valid after the stream is
+ *     synchronised.  Calls are thread-safe; a workspace must not be shared by
+ *     calls that may overlap on the device.
+ *   - Complex arrays are interleaved (re, im): complex64 (2 x float) when
+ *     precision == RSIM_SPLIT, complex128 (2 x double) when RSIM_FP64.
+ *   - Errors: a non-zero rsim_status is returned and nothing is enqueued for
+ *     RSIM_ERR_INVALID_ARG / RSIM_ERR_UNSUPPORTED / RSIM_ERR_WORKSPACE;
+ *     RSIM_ERR_CUDA reports a failed launch.  rsim_last_error() gives a
+ *     per-thread message for the last failure.  Nothing throws across the ABI.
+ *   - Scatterer order: any order is accepted; RSIM_SPLIT is most accurate when
+ *     consecutive scatterers are spatially close (e.g. a row-major grid),
+ *     because each block of 1024 consecutive scatterers shares one FP64
+ *     reference point.
+ *   - Accumulation is exact: contributions are summed in 64-bit fixed point
+ *     (2^-32 resolution, |sum| < 2^31 per cell), so results are bitwise
+ *     reproducible run to run regardless of scheduling.
+ */
+#ifndef RSIM_H
+#define RSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSIM_ABI_VERSION 1
+
+typedef enum {
+    RSIM_OK = 0,
+    RSIM_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, size or value out of range     */
+    RSIM_ERR_CUDA = 2,         /* a CUDA launch or stream operation failed                 */
+    RSIM_ERR_UNSUPPORTED = 3,  /* valid request this build does not implement             */
+    RSIM_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                       */
+    RSIM_ERR_WORKSPACE = 5     /* workspace missing, misaligned or smaller than required   */
+} rsim_status;
+
+/* Arithmetic of the per-scatterer path.
+ * RSIM_FP64  : every per-scatterer quantity in IEEE double (slow on GB300's FP64 pipe).
+ * RSIM_SPLIT : FP64 only per (block of scatterers, pulse) -- platform position, reference
+ *              range and phase of a block reference point -- and FP32 for the per-scatterer
+ *              differential range, phase, sincos and weights; gate and Doppler-bin decisions
+ *              that fall within rounding distance of a cell edge are re-taken in FP64. */
+typedef enum { RSIM_FP64 = 0, RSIM_SPLIT = 1 } rsim_precision;
+
+/* Blend window W(d), d = |p_i - x| / n_fast in [0, 1], zero at d >= 1.
+ * RSIM_WIN_SQRT_LINEAR        : (1 - d)^(1/2)           -- Eq. (1) of the paper.
+ * RSIM_WIN_SQRT_RAISED_COSINE : cos(pi d / 2)           -- squared weights form a raised cosine.
+ * RSIM_WIN_LINEAR             : 1 - d                   -- linear amplitude crossfade (tests). */
+typedef enum {
+    RSIM_WIN_SQRT_LINEAR = 0,
+    RSIM_WIN_SQRT_RAISED_COSINE = 1,
+    RSIM_WIN_LINEAR = 2
+} rsim_window;
+
+/* Instrument constants (SI).  1 <= n_gates <= 4096; all doubles finite and > 0. */
+typedef struct {
+    double carrier_hz;     /* carrier frequency f_c                               */
+    double prf_hz;         /* pulse repetition frequency                          */
+    double c_mps;          /* propagation speed                                   */
+    double gate_width_m;   /* range-gate width                                    */
+    double beamwidth_rad;  /* two-way 3 dB full beamwidth of the Gaussian pattern */
+    int32_t n_gates;       /* number of range gates N_g                           */
+    int32_t reserved;      /* must be 0                                           */
+} rsim_radar;
+
+/* Platform track in the scene frame (metres, seconds): P(t) = p0 + v t;
+ * range-window reference r_ref(t) = r_ref0 + r_ref_rate t (gate n_gates/2 starts there). */
+typedef struct {
+    double p0[3];
+    double v[3];
+    double r_ref0;
+    double r_ref_rate;
+} rsim_platform;
+
+/* Scatterer set, structure of arrays of n float32 DEVICE arrays: positions relative
+ * to origin (m), velocities (m/s), NRCS (linear, >= 0).  facet_area_m2 > 0. */
+typedef struct {
+    int64_t n;
+    const float *x, *y, *z, *vx, *vy, *vz, *nrcs;
+    double origin[3];
+    double facet_area_m2;
+} rsim_scatterers;
+
+/* Library version (RSIM_ABI_VERSION). */
+int rsim_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *rsim_last_error(void);
+
+/* Bytes of workspace rsim_direct_sum / rsim_doppler_accumulate need for n_samples
+ * samples (pulses, or updates) of n_gates x n_doppler cells (n_doppler = 1 for
+ * rsim_direct_sum).  Returns 0 for invalid sizes. */
+size_t rsim_workspace_size(int32_t n_samples, int32_t n_gates, int32_t n_doppler);
+
+/* Regular mode (Section II.A, Fig. 1 step 4):
+ *   iq[p][g] += sum_n C_n(t_{pulse0+p}) [gate_n = g],  p in [0, n_pulses).
+ * iq        : [n_pulses][n_gates] complex (see precision), accumulated (+=).
+ * workspace : >= rsim_workspace_size(n_pulses, n_gates, 1) bytes, 16-byte aligned.
+ * pulse0 >= 0, n_pulses >= 0 (0: no-op). */
+rsim_status rsim_direct_sum(const rsim_radar *radar, const rsim_platform *platform,
+                            const rsim_scatterers *scat, int64_t pulse0, int32_t n_pulses,
+                            rsim_precision precision, void *iq, void *workspace,
+                            size_t workspace_bytes, cudaStream_t stream);
+
+/* Fast-mode Doppler spectra (Algorithm 1 of Section III.B) for the updates
+ * i in [update0, update0 + n_updates): pulse pair (p_i, p_i + 1), p_i = i n_fast,
+ *   spectra[i - update0][g][k] += sum of C_n(t_{p_i}) over scatterers with gate g, bin k.
+ * spectra   : [n_updates][n_gates][n_doppler] complex, accumulated (+=).
+ * n_fast >= 1; n_doppler a power of two in [1, 4096]; update0 >= 0.
+ * workspace : >= rsim_workspace_size(n_updates, n_gates, n_doppler) bytes, 16-byte aligned. */
+rsim_status rsim_doppler_accumulate(const rsim_radar *radar, const rsim_platform *platform,
+                                    const rsim_scatterers *scat, int64_t update0,
+                                    int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                    rsim_precision precision, void *spectra, void *workspace,
+                                    size_t workspace_bytes, cudaStream_t stream);
+
+/* Fast-mode post-processing (Section III.B steps 2-4 with Eq. (1)): batched
+ * n_doppler-point inverse FFT per gate of each spectrum, blend window, sum into
+ * the pulses x in [pulse0, pulse0 + n_pulses).
+ * spectra   : [n_spectra][n_gates][n_doppler] complex; spectra[s] belongs to update update0 + s.
+ * iq        : [n_pulses][n_gates] complex, OVERWRITTEN.
+ * Every pulse x must find its spectra: floor(x / n_fast) >= update0, and
+ * floor(x / n_fast) + 1 < update0 + n_spectra unless x is a multiple of n_fast.
+ * n_doppler a power of two in [2, 1024]; n_gates * n_doppler <= 2^20. */
+rsim_status rsim_synth_pulses(const rsim_radar *radar, const void *spectra, int32_t n_spectra,
+                              int64_t update0, int32_t n_fast, int32_t n_doppler,
+                              int64_t pulse0, int32_t n_pulses, rsim_window window,
+                              rsim_precision precision, void *iq, cudaStream_t stream);
+
+/* Index decisions (for tests and diagnostics): for every scatterer, the range gate at
+ * pulse p and the Doppler bin of the pulse pair (p, p + 1), with the pre-floor
+ * coordinates (dR / gate_width + n_gates/2 and nu n_doppler + 1/2).  Gate is reported
+ * even when out of the window.  Any output pointer may be NULL.
+ * gate, bin : [n] int32;  gate_coord, bin_coord : [n] double. */
+rsim_status rsim_scatterer_cells(const rsim_radar *radar, const rsim_platform *platform,
+                                 const rsim_scatterers *scat, int64_t pulse, int32_t n_doppler,
+                                 rsim_precision precision, int32_t *gate, int32_t *bin,
+                                 double *gate_coord, double *bin_coord, cudaStream_t stream);
+
+/* Adjoint of rsim_synth_pulses (gradient convention dL/dRe + j dL/dIm):
+ *   grad_spectra[s][g][k] = sum_m exp(-j 2 pi k m / n_doppler)
+ *                           sum_x W_s(x) grad_iq[x][g] [ (x - p_s) mod n_doppler = m ].
+ * grad_iq      : [n_pulses][n_gates] complex;  grad_spectra : [n_spectra][n_gates][n_doppler]
+ * complex, OVERWRITTEN.  Same size rules as rsim_synth_pulses. */
+rsim_status rsim_synth_pulses_backward(const rsim_radar *radar, const void *grad_iq,
+                                       int32_t n_spectra, int64_t update0, int32_t n_fast,
+                                       int32_t n_doppler, int64_t pulse0, int32_t n_pulses,
+                                       rsim_window window, rsim_precision precision,
+                                       void *grad_spectra, cudaStream_t stream);
+
+/* Adjoint of rsim_doppler_accumulate: for each scatterer n,
+ *   grad_z[n]    += sum_i Re(conj(G_i) dC_n/dz_n),
+ *   grad_nrcs[n] += sum_i Re(conj(G_i) C_n) / (2 nrcs_n)   (0 where nrcs_n = 0),
+ * G_i = grad_spectra[i - update0][gate_n][bin_n] (gate/bin are piecewise constant and
+ * carry no gradient).  grad_z, grad_nrcs : [n] float32 (either may be NULL).
+ * Per-scatterer phase and amplitude are recomputed, not stored.  Deterministic. */
+rsim_status rsim_doppler_accumulate_backward(const rsim_radar *radar,
+                                             const rsim_platform *platform,
+                                             const rsim_scatterers *scat, int64_t update0,
+                                             int32_t n_updates, int32_t n_fast,
+                                             int32_t n_doppler, rsim_precision precision,
+                                             const void *grad_spectra, float *grad_z,
+                                             float *grad_nrcs, cudaStream_t stream);
+
+/* Adjoint of rsim_direct_sum with G = grad_iq[p][gate_n(t_p)] ([n_pulses][n_gates] complex). */
+rsim_status rsim_direct_sum_backward(const rsim_radar *radar, const rsim_platform *platform,
+                                     const rsim_scatterers *scat, int64_t pulse0,
+                                     int32_t n_pulses, rsim_precision precision,
+                                     const void *grad_iq, float *grad_z, float *grad_nrcs,
+                                     cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSIM_H */

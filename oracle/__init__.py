@@ -137,6 +137,11 @@ class Oracle:
                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _DP, _DP]
         L.or_direct_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int64, ctypes.c_int32, _DP, _DP, _DP]
+        L.or_direct_sum_cells.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_int32, _IP, _DP]
+        L.or_doppler_spectra_cells.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, _IP, _IP, _DP]
         L.or_set_threads.argtypes = [ctypes.c_int]
         L.or_get_threads.restype = ctypes.c_int
         if threads:
@@ -182,7 +187,34 @@ class Oracle:
                                int(n_pulses), _d(out))
         return _cplx_out(out)
 
+    def direct_sum_cells(self, radar, platform, scene, pulse0: int, gates) -> np.ndarray:
+        """Regular-mode sums with gate decisions supplied, ``gates`` int32 [n_pulses, n]."""
+        sc, keep = _scene(scene)
+        g = np.ascontiguousarray(gates, dtype=np.int32)
+        if g.ndim != 2 or g.shape[1] != sc.n:
+            raise ValueError("gates must be [n_pulses, n]")
+        out = np.zeros((g.shape[0], radar.n_gates, 2))
+        rd, pf = _radar(radar), _platform(platform)
+        self.lib.or_direct_sum_cells(ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc),
+                                     int(pulse0), g.shape[0], g.ctypes.data_as(_IP), _d(out))
+        return _cplx_out(out)
+
     # -- fast mode -----------------------------------------------------------
+    def doppler_spectra_cells(self, radar, platform, scene, update0: int, n_fast: int,
+                              n_doppler: int, gates, bins) -> np.ndarray:
+        """Algorithm 1 rasterisation with (gate, bin) decisions supplied ([n_updates, n] each)."""
+        sc, keep = _scene(scene)
+        g = np.ascontiguousarray(gates, dtype=np.int32)
+        b = np.ascontiguousarray(bins, dtype=np.int32)
+        if g.shape != b.shape or g.ndim != 2 or g.shape[1] != sc.n:
+            raise ValueError("gates/bins must be [n_updates, n]")
+        out = np.zeros((g.shape[0], radar.n_gates, n_doppler, 2))
+        rd, pf = _radar(radar), _platform(platform)
+        self.lib.or_doppler_spectra_cells(ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc),
+                                          int(update0), g.shape[0], int(n_fast), int(n_doppler),
+                                          g.ctypes.data_as(_IP), b.ctypes.data_as(_IP), _d(out))
+        return _cplx_out(out)
+
     def doppler_spectra(self, radar, platform, scene, update0: int, n_updates: int, n_fast: int,
                         n_doppler: int) -> np.ndarray:
         sc, keep = _scene(scene)

@@ -449,3 +449,96 @@ void or_direct_grad(const or_radar *rd, const or_platform *pf, const or_scene *s
         grad_nrcs[n] = gsig;
     }
 }
+
+/* Regular mode with the gate decisions supplied (gate[p * n + j] for pulse pulse0 + p,
+ * scatterer j): sums the FP64 amplitudes C_j(t_p) into those gates.  Lets a test compare
+ * sums with an implementation whose gate decisions were taken in another precision
+ * (a decision whose coordinate is within rounding of a gate edge may go either way). */
+void or_direct_sum_cells(const or_radar *rd, const or_platform *pf, const or_scene *sc,
+                         int64_t pulse0, int32_t n_pulses, const int32_t *gate, double *iq) {
+    const int G = rd->n_gates;
+    const int64_t N = sc->n;
+    const int64_t csz = (N + OR_NCHUNK - 1) / OR_NCHUNK;
+    double *part = (double *)calloc((size_t)OR_NCHUNK * G * 4, sizeof(double));
+    for (int32_t p = 0; p < n_pulses; ++p) {
+        double t = (double)(pulse0 + p) / rd->prf_hz;
+        const int32_t *gp = gate + (size_t)p * N;
+        memset(part, 0, sizeof(double) * (size_t)OR_NCHUNK * G * 4);
+#pragma omp parallel for schedule(static)
+        for (int ch = 0; ch < OR_NCHUNK; ++ch) {
+            double *pp = part + (size_t)ch * G * 4;
+            int64_t lo = ch * csz, hi = lo + csz < N ? lo + csz : N;
+            for (int64_t n = lo; n < hi; ++n) {
+                int gi = gp[n];
+                if (gi < 0 || gi >= G) continue;
+                or_echo e;
+                echo_at(rd, pf, sc, n, t, &e);
+                neu_add(&pp[gi * 4 + 0], &pp[gi * 4 + 1], e.re);
+                neu_add(&pp[gi * 4 + 2], &pp[gi * 4 + 3], e.im);
+            }
+        }
+        for (int g = 0; g < G; ++g) {
+            double sr = 0, cr = 0, si = 0, ci = 0;
+            for (int ch = 0; ch < OR_NCHUNK; ++ch) {
+                const double *pp = part + (size_t)ch * G * 4 + g * 4;
+                neu_add(&sr, &cr, pp[0]);
+                neu_add(&sr, &cr, pp[1]);
+                neu_add(&si, &ci, pp[2]);
+                neu_add(&si, &ci, pp[3]);
+            }
+            iq[((size_t)p * G + g) * 2 + 0] = sr + cr;
+            iq[((size_t)p * G + g) * 2 + 1] = si + ci;
+        }
+    }
+    free(part);
+}
+
+/* Fast-mode rasterisation of Algorithm 1 with the (gate, bin) decisions supplied
+ * (gate[u * n + j], bin[u * n + j] for update update0 + u): T[u, gate, bin] += C_j(t_{p_u}). */
+void or_doppler_spectra_cells(const or_radar *rd, const or_platform *pf, const or_scene *sc,
+                              int64_t update0, int32_t n_updates, int32_t n_fast,
+                              int32_t n_doppler, const int32_t *gate, const int32_t *bin,
+                              double *T) {
+    const int G = rd->n_gates;
+    const int K = n_doppler;
+    const int64_t cells = (int64_t)G * K;
+    const int64_t N = sc->n;
+    const int64_t csz = (N + OR_NCHUNK - 1) / OR_NCHUNK;
+    double *part = (double *)malloc(sizeof(double) * (size_t)OR_NCHUNK * cells * 4);
+    for (int32_t u = 0; u < n_updates; ++u) {
+        int64_t p_i = (update0 + u) * (int64_t)n_fast;
+        double t_i = (double)p_i / rd->prf_hz;
+        const int32_t *gu = gate + (size_t)u * N;
+        const int32_t *bu = bin + (size_t)u * N;
+        memset(part, 0, sizeof(double) * (size_t)OR_NCHUNK * cells * 4);
+#pragma omp parallel for schedule(static)
+        for (int ch = 0; ch < OR_NCHUNK; ++ch) {
+            double *pp = part + (size_t)ch * cells * 4;
+            int64_t lo = ch * csz, hi = lo + csz < N ? lo + csz : N;
+            for (int64_t n = lo; n < hi; ++n) {
+                int32_t g = gu[n], k = bu[n];
+                if (g < 0 || g >= G || k < 0 || k >= K) continue;
+                or_echo ci;
+                echo_at(rd, pf, sc, n, t_i, &ci);
+                int64_t cell = (int64_t)g * K + k;
+                neu_add(&pp[cell * 4 + 0], &pp[cell * 4 + 1], ci.re);
+                neu_add(&pp[cell * 4 + 2], &pp[cell * 4 + 3], ci.im);
+            }
+        }
+        double *Tu = T + (size_t)u * cells * 2;
+#pragma omp parallel for schedule(static)
+        for (int64_t cell = 0; cell < cells; ++cell) {
+            double sr = 0, cr = 0, si = 0, cci = 0;
+            for (int ch = 0; ch < OR_NCHUNK; ++ch) {
+                const double *pp = part + (size_t)ch * cells * 4 + cell * 4;
+                neu_add(&sr, &cr, pp[0]);
+                neu_add(&sr, &cr, pp[1]);
+                neu_add(&si, &cci, pp[2]);
+                neu_add(&si, &cci, pp[3]);
+            }
+            Tu[cell * 2 + 0] = sr + cr;
+            Tu[cell * 2 + 1] = si + cci;
+        }
+    }
+    free(part);
+}

@@ -1,0 +1,343 @@
+"""GB300-native coherent summation of sea-surface scatterers into radar IQ range gates.
+
+Hot path of the raw-data simulator of arXiv 2408.11472 (Monnier, Camus,
+Hellouvry): regular mode (every scatterer into every pulse, Section II.A) and
+the fast mode of Section III (one Doppler-spectrum pass per surface update,
+Algorithm 1; batched per-gate inverse FFT, Eq. (1) weights and overlap-add,
+Section III.B), plus the adjoints of both.
+
+Every step runs in the hand-written sm_103a kernels of ``librsim.so`` behind
+the C ABI of ``include/rsim.h``; this module only marshals torch tensors
+(device memory, streams) into those calls.  There is no CPU fallback: importing
+the package fails if the CUDA library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+from typing import Optional, Tuple
+
+import torch
+
+from . import _lib
+from ._lib import PRECISIONS, WINDOWS, RsimError
+
+__all__ = [
+    "Radar", "Platform", "Scatterers", "RsimError", "workspace_size", "direct_sum",
+    "doppler_accumulate", "synth_pulses", "scatterer_cells", "synth_pulses_backward",
+    "doppler_accumulate_backward", "direct_sum_backward", "spectra_range", "simulate_fast",
+    "FastMode", "RegularMode", "version", "PRECISIONS", "WINDOWS",
+]
+
+_KEYS = ("x", "y", "z", "vx", "vy", "vz", "nrcs")
+
+
+@dataclasses.dataclass(frozen=True)
+class Radar:
+    """Instrument constants (SI).  Defaults: Sentinel-3 SRAL-like Ku-band altimeter."""
+
+    carrier_hz: float = 13.575e9
+    prf_hz: float = 18_000.0
+    c_mps: float = 299_792_458.0
+    gate_width_m: float = 0.47
+    beamwidth_rad: float = math.radians(1.3)
+    n_gates: int = 128
+
+
+@dataclasses.dataclass(frozen=True)
+class Platform:
+    """Track P(t) = p0 + v t (scene frame) and range reference r_ref(t) = r_ref0 + r_ref_rate t."""
+
+    p0: tuple = (0.0, 0.0, 800e3)
+    v: tuple = (7_000.0, 0.0, 0.0)
+    r_ref0: float = 800e3
+    r_ref_rate: float = 0.0
+
+
+class Scatterers:
+    """Structure-of-arrays scatterer set on a CUDA device (float32, contiguous)."""
+
+    def __init__(self, x, y, z, vx, vy, vz, nrcs, origin=(0.0, 0.0, 0.0), area=1.0):
+        arrs = [x, y, z, vx, vy, vz, nrcs]
+        n = arrs[0].numel()
+        for a in arrs:
+            if not isinstance(a, torch.Tensor) or a.dtype != torch.float32 or not a.is_cuda:
+                raise TypeError("scatterer arrays must be float32 CUDA tensors")
+            if a.numel() != n or not a.is_contiguous():
+                raise ValueError("scatterer arrays must be contiguous and of equal length")
+        self.x, self.y, self.z, self.vx, self.vy, self.vz, self.nrcs = arrs
+        self.origin = tuple(float(o) for o in origin)
+        self.area = float(area)
+
+    @classmethod
+    def from_arrays(cls, d, device="cuda") -> "Scatterers":
+        """Copy a dict of arrays (numpy or torch; keys x, y, z, vx, vy, vz, nrcs,
+        optional origin and area) to ``device``."""
+        t = [torch.as_tensor(d[k]).to(device=device, dtype=torch.float32).contiguous() for k in _KEYS]
+        return cls(*t, origin=d.get("origin", (0.0, 0.0, 0.0)), area=d.get("area", 1.0))
+
+    def replace(self, **kw) -> "Scatterers":
+        arrs = {k: kw.get(k, getattr(self, k)) for k in _KEYS}
+        return Scatterers(**arrs, origin=self.origin, area=self.area)
+
+    @property
+    def n(self) -> int:
+        return self.x.numel()
+
+    @property
+    def device(self) -> torch.device:
+        return self.x.device
+
+    def c_struct(self) -> _lib.Scatterers:
+        return _lib.Scatterers(self.n, *[getattr(self, k).data_ptr() for k in _KEYS],
+                               (ctypes.c_double * 3)(*self.origin), self.area)
+
+
+def version() -> int:
+    return int(_lib.lib.rsim_version())
+
+
+def _prec(precision) -> int:
+    try:
+        return PRECISIONS[precision]
+    except KeyError:
+        raise ValueError("precision must be one of %s" % list(PRECISIONS)) from None
+
+
+def _cdtype(precision) -> torch.dtype:
+    return torch.complex128 if _prec(precision) == 0 else torch.complex64
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _need(t: torch.Tensor, dtype, shape, device, what):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or t.device != device or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor of shape %s on %s"
+                         % (what, dtype, tuple(shape), device))
+
+
+def workspace_size(n_samples: int, n_gates: int, n_doppler: int = 1) -> int:
+    """Bytes of fixed-point scratch a summation call needs (see rsim_workspace_size)."""
+    return int(_lib.lib.rsim_workspace_size(int(n_samples), int(n_gates), int(n_doppler)))
+
+
+def _workspace(workspace, nbytes, device):
+    if workspace is None:
+        return torch.empty(max(nbytes, 16), dtype=torch.uint8, device=device)
+    if workspace.numel() * workspace.element_size() < nbytes:
+        raise ValueError("workspace smaller than %d bytes" % nbytes)
+    return workspace
+
+
+def direct_sum(radar, platform, scat: Scatterers, pulse0: int, n_pulses: int,
+               precision: str = "split", out: Optional[torch.Tensor] = None,
+               workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Regular mode: IQ [n_pulses, n_gates] (+= into ``out`` if given, else a new zeroed tensor)."""
+    shape = (n_pulses, radar.n_gates)
+    if out is None:
+        out = torch.zeros(shape, dtype=_cdtype(precision), device=scat.device)
+    _need(out, _cdtype(precision), shape, scat.device, "out")
+    ws = _workspace(workspace, workspace_size(n_pulses, radar.n_gates, 1), scat.device)
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_direct_sum(ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc),
+                                        int(pulse0), int(n_pulses), _prec(precision),
+                                        _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
+                                        _stream(stream)))
+    return out
+
+
+def doppler_accumulate(radar, platform, scat: Scatterers, update0: int, n_updates: int,
+                       n_fast: int, n_doppler: int, precision: str = "split",
+                       out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                       stream=None) -> torch.Tensor:
+    """Fast-mode Doppler spectra [n_updates, n_gates, n_doppler] of updates update0.. (Algorithm 1)."""
+    shape = (n_updates, radar.n_gates, n_doppler)
+    if out is None:
+        out = torch.zeros(shape, dtype=_cdtype(precision), device=scat.device)
+    _need(out, _cdtype(precision), shape, scat.device, "out")
+    ws = _workspace(workspace, workspace_size(n_updates, radar.n_gates, n_doppler), scat.device)
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_doppler_accumulate(
+        ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(update0), int(n_updates),
+        int(n_fast), int(n_doppler), _prec(precision), _ptr(out), _ptr(ws),
+        ws.numel() * ws.element_size(), _stream(stream)))
+    return out
+
+
+def _prec_of(t: torch.Tensor) -> str:
+    if t.dtype == torch.complex128:
+        return "fp64"
+    if t.dtype == torch.complex64:
+        return "split"
+    raise TypeError("expected a complex64 or complex128 tensor")
+
+
+def synth_pulses(radar, spectra: torch.Tensor, update0: int, n_fast: int, pulse0: int,
+                 n_pulses: int, window: str = "sqrt_raised_cosine",
+                 out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Post-processing of Section III.B: IQ [n_pulses, n_gates] from spectra [S, n_gates, N_d]."""
+    precision = _prec_of(spectra)
+    S, G, K = spectra.shape
+    if G != radar.n_gates:
+        raise ValueError("spectra gate axis does not match radar.n_gates")
+    if not spectra.is_contiguous():
+        raise ValueError("spectra must be contiguous")
+    shape = (n_pulses, G)
+    if out is None:
+        out = torch.empty(shape, dtype=spectra.dtype, device=spectra.device)
+    _need(out, spectra.dtype, shape, spectra.device, "out")
+    rd = _lib.make_radar(radar)
+    _lib.check(_lib.lib.rsim_synth_pulses(ctypes.byref(rd), _ptr(spectra), int(S), int(update0),
+                                          int(n_fast), int(K), int(pulse0), int(n_pulses),
+                                          WINDOWS[window], _prec(precision), _ptr(out),
+                                          _stream(stream)))
+    return out
+
+
+def scatterer_cells(radar, platform, scat: Scatterers, pulse: int, n_doppler: int,
+                    precision: str = "split", stream=None):
+    """Per-scatterer gate and Doppler-bin decisions at pulse (pair (pulse, pulse+1)),
+    with their pre-floor coordinates: (gate int32, bin int32, gate_coord f64, bin_coord f64)."""
+    dev = scat.device
+    gate = torch.empty(scat.n, dtype=torch.int32, device=dev)
+    bins = torch.empty(scat.n, dtype=torch.int32, device=dev)
+    gc = torch.empty(scat.n, dtype=torch.float64, device=dev)
+    bc = torch.empty(scat.n, dtype=torch.float64, device=dev)
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_scatterer_cells(ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc),
+                                             int(pulse), int(n_doppler), _prec(precision),
+                                             _ptr(gate), _ptr(bins), _ptr(gc), _ptr(bc),
+                                             _stream(stream)))
+    return gate, bins, gc, bc
+
+
+def synth_pulses_backward(radar, grad_iq: torch.Tensor, n_spectra: int, update0: int,
+                          n_fast: int, n_doppler: int, pulse0: int,
+                          window: str = "sqrt_raised_cosine", out: Optional[torch.Tensor] = None,
+                          stream=None) -> torch.Tensor:
+    """Adjoint of synth_pulses: dL/dT [n_spectra, n_gates, n_doppler] from dL/dY."""
+    precision = _prec_of(grad_iq)
+    P, G = grad_iq.shape
+    shape = (n_spectra, G, n_doppler)
+    if out is None:
+        out = torch.empty(shape, dtype=grad_iq.dtype, device=grad_iq.device)
+    _need(out, grad_iq.dtype, shape, grad_iq.device, "out")
+    grad_iq = grad_iq.contiguous()
+    rd = _lib.make_radar(radar)
+    _lib.check(_lib.lib.rsim_synth_pulses_backward(
+        ctypes.byref(rd), _ptr(grad_iq), int(n_spectra), int(update0), int(n_fast), int(n_doppler),
+        int(pulse0), int(P), WINDOWS[window], _prec(precision), _ptr(out), _stream(stream)))
+    return out
+
+
+def _grads(scat, grad_z, grad_nrcs):
+    if grad_z is None:
+        grad_z = torch.zeros(scat.n, dtype=torch.float32, device=scat.device)
+    if grad_nrcs is None:
+        grad_nrcs = torch.zeros(scat.n, dtype=torch.float32, device=scat.device)
+    for t in (grad_z, grad_nrcs):
+        _need(t, torch.float32, (scat.n,), scat.device, "gradient buffer")
+    return grad_z, grad_nrcs
+
+
+def doppler_accumulate_backward(radar, platform, scat: Scatterers, update0: int, n_fast: int,
+                                grad_spectra: torch.Tensor, grad_z=None, grad_nrcs=None,
+                                stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Adjoint of doppler_accumulate: (dL/dz, dL/dnrcs) accumulated into float32 [n] buffers."""
+    precision = _prec_of(grad_spectra)
+    S, G, K = grad_spectra.shape
+    grad_spectra = grad_spectra.contiguous()
+    grad_z, grad_nrcs = _grads(scat, grad_z, grad_nrcs)
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_doppler_accumulate_backward(
+        ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(update0), int(S), int(n_fast),
+        int(K), _prec(precision), _ptr(grad_spectra), _ptr(grad_z), _ptr(grad_nrcs),
+        _stream(stream)))
+    return grad_z, grad_nrcs
+
+
+def direct_sum_backward(radar, platform, scat: Scatterers, pulse0: int, grad_iq: torch.Tensor,
+                        grad_z=None, grad_nrcs=None, stream=None):
+    """Adjoint of direct_sum: (dL/dz, dL/dnrcs) accumulated into float32 [n] buffers."""
+    precision = _prec_of(grad_iq)
+    P, G = grad_iq.shape
+    grad_iq = grad_iq.contiguous()
+    grad_z, grad_nrcs = _grads(scat, grad_z, grad_nrcs)
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_direct_sum_backward(
+        ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(pulse0), int(P),
+        _prec(precision), _ptr(grad_iq), _ptr(grad_z), _ptr(grad_nrcs), _stream(stream)))
+    return grad_z, grad_nrcs
+
+
+def spectra_range(pulse0: int, n_pulses: int, n_fast: int) -> Tuple[int, int]:
+    """(update0, n_spectra) of the updates whose spectra the pulses [pulse0, pulse0+n_pulses)
+    blend: floor(pulse0/n_fast) .. floor((pulse0+n_pulses-1)/n_fast) + 1."""
+    u0 = pulse0 // n_fast
+    u1 = (pulse0 + n_pulses - 1) // n_fast + 1
+    return u0, u1 - u0 + 1
+
+
+def simulate_fast(radar, platform, scat: Scatterers, n_pulses: int, n_fast: int, n_doppler: int,
+                  window: str = "sqrt_raised_cosine", precision: str = "split", pulse0: int = 0,
+                  workspace=None, spectra=None, out=None, stream=None):
+    """Fast mode end to end: spectra of every update the pulses need, then the blended IQ.
+    Returns (spectra [S, G, N_d], iq [n_pulses, G])."""
+    u0, S = spectra_range(pulse0, n_pulses, n_fast)
+    if spectra is not None:
+        spectra.zero_()
+    T = doppler_accumulate(radar, platform, scat, u0, S, n_fast, n_doppler, precision,
+                           out=spectra, workspace=workspace, stream=stream)
+    Y = synth_pulses(radar, T, u0, n_fast, pulse0, n_pulses, window, out=out, stream=stream)
+    return T, Y
+
+
+class FastMode(torch.autograd.Function):
+    """IQ of the fast mode as a differentiable function of scatterer heights z and NRCS.
+
+    forward(z, nrcs, scat, radar, platform, pulse0, n_pulses, n_fast, n_doppler, window,
+    precision) -> complex IQ [n_pulses, n_gates].  The backward pass runs the adjoint
+    kernels (per-scatterer phase recomputed, not stored)."""
+
+    @staticmethod
+    def forward(ctx, z, nrcs, scat, radar, platform, pulse0, n_pulses, n_fast, n_doppler,
+                window="sqrt_raised_cosine", precision="split"):
+        s = scat.replace(z=z.detach().contiguous(), nrcs=nrcs.detach().contiguous())
+        _, Y = simulate_fast(radar, platform, s, n_pulses, n_fast, n_doppler, window, precision,
+                             pulse0)
+        ctx.args = (s, radar, platform, pulse0, n_pulses, n_fast, n_doppler, window)
+        return Y
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        s, radar, platform, pulse0, n_pulses, n_fast, n_doppler, window = ctx.args
+        u0, S = spectra_range(pulse0, n_pulses, n_fast)
+        gT = synth_pulses_backward(radar, grad_y.contiguous(), S, u0, n_fast, n_doppler, pulse0,
+                                   window)
+        gz, gs = doppler_accumulate_backward(radar, platform, s, u0, n_fast, gT)
+        return gz, gs, None, None, None, None, None, None, None, None, None
+
+
+class RegularMode(torch.autograd.Function):
+    """IQ of the regular mode as a differentiable function of heights z and NRCS."""
+
+    @staticmethod
+    def forward(ctx, z, nrcs, scat, radar, platform, pulse0, n_pulses, precision="split"):
+        s = scat.replace(z=z.detach().contiguous(), nrcs=nrcs.detach().contiguous())
+        Y = direct_sum(radar, platform, s, pulse0, n_pulses, precision)
+        ctx.args = (s, radar, platform, pulse0)
+        return Y
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        s, radar, platform, pulse0 = ctx.args
+        gz, gs = direct_sum_backward(radar, platform, s, pulse0, grad_y.contiguous())
+        return gz, gs, None, None, None, None, None, None

@@ -1,0 +1,103 @@
+"""ctypes view of librsim.so (the C ABI declared in include/rsim.h).
+
+Argument marshalling only: structs mirroring the header, prototypes, status
+checking.  Importing this module loads the in-tree library and raises if it is
+missing -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsim.so")
+
+RSIM_OK = 0
+STATUS_NAMES = {0: "RSIM_OK", 1: "RSIM_ERR_INVALID_ARG", 2: "RSIM_ERR_CUDA",
+                3: "RSIM_ERR_UNSUPPORTED", 4: "RSIM_ERR_TIMEOUT", 5: "RSIM_ERR_WORKSPACE"}
+PRECISIONS = {"fp64": 0, "split": 1}
+WINDOWS = {"sqrt_linear": 0, "sqrt_raised_cosine": 1, "linear": 2}
+
+
+class RsimError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+
+
+class Radar(ctypes.Structure):
+    _fields_ = [("carrier_hz", ctypes.c_double), ("prf_hz", ctypes.c_double),
+                ("c_mps", ctypes.c_double), ("gate_width_m", ctypes.c_double),
+                ("beamwidth_rad", ctypes.c_double), ("n_gates", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Platform(ctypes.Structure):
+    _fields_ = [("p0", ctypes.c_double * 3), ("v", ctypes.c_double * 3),
+                ("r_ref0", ctypes.c_double), ("r_ref_rate", ctypes.c_double)]
+
+
+class Scatterers(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
+                                          ("x", "y", "z", "vx", "vy", "vz", "nrcs")] + [
+        ("origin", ctypes.c_double * 3), ("facet_area_m2", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_RP = ctypes.POINTER(Radar)
+_PP = ctypes.POINTER(Platform)
+_SP = ctypes.POINTER(Scatterers)
+_I32, _I64 = ctypes.c_int32, ctypes.c_int64
+
+PROTOTYPES = {
+    "rsim_version": ([], ctypes.c_int),
+    "rsim_last_error": ([], ctypes.c_char_p),
+    "rsim_workspace_size": ([_I32, _I32, _I32], ctypes.c_size_t),
+    "rsim_direct_sum": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, ctypes.c_size_t, _P],
+                        ctypes.c_int),
+    "rsim_doppler_accumulate": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int, _P, _P,
+                                 ctypes.c_size_t, _P], ctypes.c_int),
+    "rsim_synth_pulses": ([_RP, _P, _I32, _I64, _I32, _I32, _I64, _I32, ctypes.c_int,
+                           ctypes.c_int, _P, _P], ctypes.c_int),
+    "rsim_scatterer_cells": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P, _P],
+                             ctypes.c_int),
+    "rsim_synth_pulses_backward": ([_RP, _P, _I32, _I64, _I32, _I32, _I64, _I32, ctypes.c_int,
+                                    ctypes.c_int, _P, _P], ctypes.c_int),
+    "rsim_doppler_accumulate_backward": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
+                                          _P, _P, _P, _P], ctypes.c_int),
+    "rsim_direct_sum_backward": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P],
+                                 ctypes.c_int),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            "librsim.so is not built (%s); run `python -m paper_2408_11472_gb300.build` "
+            "(the CUDA library is required; there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in PROTOTYPES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = load()
+
+
+def check(status: int) -> None:
+    if status != RSIM_OK:
+        msg = lib.rsim_last_error()
+        raise RsimError(status, msg.decode() if msg else "")
+
+
+def make_radar(r) -> Radar:
+    return Radar(float(r.carrier_hz), float(r.prf_hz), float(r.c_mps), float(r.gate_width_m),
+                 float(r.beamwidth_rad), int(r.n_gates), 0)
+
+
+def make_platform(p) -> Platform:
+    return Platform((ctypes.c_double * 3)(*[float(v) for v in p.p0]),
+                    (ctypes.c_double * 3)(*[float(v) for v in p.v]), float(p.r_ref0),
+                    float(p.r_ref_rate))

@@ -1,0 +1,394 @@
+// abi.cu -- the C ABI of librsim (declared in include/rsim.h): argument validation,
+// workspace checks, model constants and kernel launches.  No allocation happens here;
+// every device buffer, including scratch, belongs to the caller.
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+
+#include "rsim.h"
+#include "rsim_internal.cuh"
+#include "rsim_kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rsim_status fail(rsim_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+rsim_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(RSIM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int device_sms() {
+    static int cache[256] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 132;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 132;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+rsim_status check_radar(const rsim_radar* r) {
+    if (!r) return fail(RSIM_ERR_INVALID_ARG, "radar is NULL");
+    if (!finite_pos(r->carrier_hz) || !finite_pos(r->prf_hz) || !finite_pos(r->c_mps) ||
+        !finite_pos(r->gate_width_m) || !finite_pos(r->beamwidth_rad))
+        return fail(RSIM_ERR_INVALID_ARG, "radar constants must be finite and > 0");
+    if (r->n_gates < 1 || r->n_gates > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "n_gates=%d outside [1, 4096]", r->n_gates);
+    if (r->reserved != 0) return fail(RSIM_ERR_INVALID_ARG, "radar.reserved must be 0");
+    return RSIM_OK;
+}
+
+rsim_status check_platform(const rsim_platform* p) {
+    if (!p) return fail(RSIM_ERR_INVALID_ARG, "platform is NULL");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(p->p0[i]) || !std::isfinite(p->v[i]))
+            return fail(RSIM_ERR_INVALID_ARG, "platform position/velocity must be finite");
+    if (!finite_pos(p->r_ref0) || !std::isfinite(p->r_ref_rate))
+        return fail(RSIM_ERR_INVALID_ARG, "r_ref0 must be finite and > 0, r_ref_rate finite");
+    return RSIM_OK;
+}
+
+rsim_status check_scat(const rsim_scatterers* s) {
+    if (!s) return fail(RSIM_ERR_INVALID_ARG, "scatterers is NULL");
+    if (s->n < 0) return fail(RSIM_ERR_INVALID_ARG, "scatterer count %lld < 0", (long long)s->n);
+    if (s->n > ((int64_t)1 << 40)) return fail(RSIM_ERR_INVALID_ARG, "scatterer count too large");
+    if (s->n > 0) {
+        const float* p[7] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->nrcs};
+        for (int i = 0; i < 7; ++i) {
+            if (!p[i]) return fail(RSIM_ERR_INVALID_ARG, "scatterer array %d is NULL", i);
+            if (!aligned(p[i], 4)) return fail(RSIM_ERR_INVALID_ARG, "scatterer array %d misaligned", i);
+        }
+    }
+    if (!finite_pos(s->facet_area_m2)) return fail(RSIM_ERR_INVALID_ARG, "facet_area_m2 must be > 0");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(s->origin[i])) return fail(RSIM_ERR_INVALID_ARG, "origin must be finite");
+    return RSIM_OK;
+}
+
+rsim_status check_precision(rsim_precision p) {
+    if (p != RSIM_FP64 && p != RSIM_SPLIT) return fail(RSIM_ERR_INVALID_ARG, "unknown precision %d", (int)p);
+    return RSIM_OK;
+}
+
+rsim::Model make_model(const rsim_radar* r, const rsim_platform* p, const rsim_scatterers* s,
+                       int n_doppler) {
+    rsim::Model m;
+    std::memset(&m, 0, sizeof(m));
+    m.prf = r->prf_hz;
+    m.inv_prf = 1.0 / r->prf_hz;
+    for (int i = 0; i < 3; ++i) {
+        m.p0[i] = p->p0[i] - s->origin[i];
+        m.v[i] = p->v[i];
+    }
+    m.r_ref0 = p->r_ref0;
+    m.r_ref_rate = p->r_ref_rate;
+    m.two_over_lambda = 2.0 * r->carrier_hz / r->c_mps;
+    m.inv_gw = 1.0 / r->gate_width_m;
+    m.half_gates = 0.5 * (double)r->n_gates;
+    m.beam_k = -2.0 / (r->beamwidth_rad * r->beamwidth_rad);
+    m.area = s->facet_area_m2;
+    m.n_gates = r->n_gates;
+    m.n_doppler = n_doppler;
+    m.inv_gw_f = (float)m.inv_gw;
+    m.beam_k_f = (float)m.beam_k;
+    m.chi_hi = (float)m.two_over_lambda;
+    m.chi_lo = (float)(m.two_over_lambda - (double)m.chi_hi);
+    m.dt_f = (float)m.inv_prf;
+    m.hdt_f = (float)(0.5 * m.inv_prf);
+    for (int i = 0; i < 3; ++i) m.ep[i] = (float)(p->v[i] * m.inv_prf);
+    return m;
+}
+
+rsim::Scat make_scat(const rsim_scatterers* s) {
+    rsim::Scat sc;
+    sc.x = s->x; sc.y = s->y; sc.z = s->z;
+    sc.vx = s->vx; sc.vy = s->vy; sc.vz = s->vz; sc.nrcs = s->nrcs;
+    sc.n = s->n;
+    const float* p[7] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->nrcs};
+    int vec = 1;
+    for (int i = 0; i < 7; ++i) vec &= aligned(p[i], 16) ? 1 : 0;
+    sc.vec4 = vec;
+    sc.pad = 0;
+    return sc;
+}
+
+size_t ws_bytes(int64_t n_samples, int n_gates, int n_doppler) {
+    return (size_t)n_samples * (size_t)n_gates * (size_t)n_doppler * 16u;
+}
+
+// Shared body of rsim_direct_sum and rsim_doppler_accumulate.
+rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platform,
+                           const rsim_scatterers* scat, int64_t pulse_base, int32_t stride,
+                           int32_t n_samples, int32_t n_doppler, bool doppler,
+                           rsim_precision precision, void* out, void* workspace,
+                           size_t workspace_bytes, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_platform(platform)) != RSIM_OK) return st;
+    if ((st = check_scat(scat)) != RSIM_OK) return st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (n_samples < 0) return fail(RSIM_ERR_INVALID_ARG, "sample count %d < 0", n_samples);
+    if (pulse_base < 0) return fail(RSIM_ERR_INVALID_ARG, "first pulse/update index < 0");
+    if (pulse_base + (int64_t)n_samples * stride > ((int64_t)1 << 52))
+        return fail(RSIM_ERR_INVALID_ARG, "pulse index out of range");
+    if (n_samples == 0 || scat->n == 0) return RSIM_OK;  // nothing to add
+    if (!out) return fail(RSIM_ERR_INVALID_ARG, "output is NULL");
+    const bool fp64 = precision == RSIM_FP64;
+    if (!aligned(out, fp64 ? 16 : 8)) return fail(RSIM_ERR_INVALID_ARG, "output misaligned");
+    const size_t need = ws_bytes(n_samples, radar->n_gates, n_doppler);
+    if (!workspace) return fail(RSIM_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
+    if (!aligned(workspace, 16)) return fail(RSIM_ERR_WORKSPACE, "workspace not 16-byte aligned");
+    if (workspace_bytes < need)
+        return fail(RSIM_ERR_WORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, need);
+
+    const rsim::Model m = make_model(radar, platform, scat, n_doppler);
+    const rsim::Scat sc = make_scat(scat);
+    const int64_t chunks = (scat->n + rsim::kChunk - 1) / rsim::kChunk;
+    if (chunks > 0x7fffffff) return fail(RSIM_ERR_INVALID_ARG, "too many scatterers");
+    // Split the samples over gridDim.y only when the scatterer chunks alone cannot fill the
+    // GPU (about 8 resident CTAs' worth per SM).
+    const int64_t target = (int64_t)device_sms() * 8;
+    int64_t groups = (target + chunks - 1) / chunks;
+    if (groups < 1) groups = 1;
+    if (groups > n_samples) groups = n_samples;
+    int64_t spg = (n_samples + groups - 1) / groups;
+    if (spg < (n_samples + 65534) / 65535) spg = (n_samples + 65534) / 65535;
+    groups = (n_samples + spg - 1) / spg;
+    rsim::Schedule sch;
+    sch.pulse_base = pulse_base;
+    sch.pulse_stride = stride;
+    sch.n_samples = n_samples;
+    sch.samples_per_group = (int32_t)spg;
+    sch.pad = 0;
+
+    cudaError_t e = cudaMemsetAsync(workspace, 0, need, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    e = rsim::launch_accumulate(m, sch, sc, fp64, doppler,
+                                static_cast<unsigned long long*>(workspace),
+                                dim3((unsigned)chunks, (unsigned)groups), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "summation kernel launch");
+    e = rsim::launch_finalize(workspace, out, (int64_t)(need / 8), fp64, device_sms(), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
+    return RSIM_OK;
+}
+
+rsim_status check_synth_args(const rsim_radar* radar, int32_t n_spectra, int64_t update0,
+                             int32_t n_fast, int32_t n_doppler, int64_t pulse0, int32_t n_pulses,
+                             int window, rsim_precision precision) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (window < 0 || window > 2) return fail(RSIM_ERR_INVALID_ARG, "unknown window %d", window);
+    if (n_fast < 1) return fail(RSIM_ERR_INVALID_ARG, "n_fast=%d < 1 (regular mode is rsim_direct_sum)", n_fast);
+    if (!is_pow2(n_doppler) || n_doppler < 2 || n_doppler > 1024)
+        return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [2, 1024]", n_doppler);
+    if ((int64_t)radar->n_gates * n_doppler > (1 << 20))
+        return fail(RSIM_ERR_INVALID_ARG, "n_gates * n_doppler > 2^20");
+    if (n_spectra < 0 || n_pulses < 0 || update0 < 0 || pulse0 < 0)
+        return fail(RSIM_ERR_INVALID_ARG, "negative count or index");
+    if (pulse0 + (int64_t)n_pulses > ((int64_t)1 << 52))
+        return fail(RSIM_ERR_INVALID_ARG, "pulse index out of range");
+    if (n_pulses == 0) return RSIM_OK;
+    const int64_t first = pulse0 / n_fast;
+    const int64_t x_last = pulse0 + n_pulses - 1;
+    const int64_t need_last = (x_last % n_fast == 0) ? x_last / n_fast : x_last / n_fast + 1;
+    if (first < update0 || need_last > update0 + (int64_t)n_spectra - 1)
+        return fail(RSIM_ERR_INVALID_ARG,
+                    "pulses [%lld, %lld] need spectra of updates [%lld, %lld], given [%lld, %lld]",
+                    (long long)pulse0, (long long)x_last, (long long)first, (long long)need_last,
+                    (long long)update0, (long long)(update0 + n_spectra - 1));
+    return RSIM_OK;
+}
+
+rsim::SynthArgs make_synth_args(const rsim_radar* radar, int32_t n_spectra, int64_t update0,
+                                int32_t n_fast, int32_t n_doppler, int64_t pulse0,
+                                int32_t n_pulses, int window) {
+    rsim::SynthArgs a;
+    a.n_gates = radar->n_gates;
+    a.n_doppler = n_doppler;
+    int L = 0;
+    while ((1 << L) < n_doppler) ++L;
+    a.log2_nd = L;
+    a.n_fast = n_fast;
+    a.n_spectra = n_spectra;
+    a.n_pulses = n_pulses;
+    a.update0 = update0;
+    a.pulse0 = pulse0;
+    a.window = window;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rsim_version(void) { return RSIM_ABI_VERSION; }
+
+const char* rsim_last_error(void) { return g_last_error.c_str(); }
+
+size_t rsim_workspace_size(int32_t n_samples, int32_t n_gates, int32_t n_doppler) {
+    if (n_samples < 0 || n_gates < 1 || n_gates > 4096 || !is_pow2(n_doppler) || n_doppler > 4096)
+        return 0;
+    return ws_bytes(n_samples, n_gates, n_doppler);
+}
+
+rsim_status rsim_direct_sum(const rsim_radar* radar, const rsim_platform* platform,
+                            const rsim_scatterers* scat, int64_t pulse0, int32_t n_pulses,
+                            rsim_precision precision, void* iq, void* workspace,
+                            size_t workspace_bytes, cudaStream_t stream) {
+    return run_accumulate(radar, platform, scat, pulse0, 1, n_pulses, 1, false, precision, iq,
+                          workspace, workspace_bytes, stream);
+}
+
+rsim_status rsim_doppler_accumulate(const rsim_radar* radar, const rsim_platform* platform,
+                                    const rsim_scatterers* scat, int64_t update0,
+                                    int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                    rsim_precision precision, void* spectra, void* workspace,
+                                    size_t workspace_bytes, cudaStream_t stream) {
+    if (n_fast < 1) return fail(RSIM_ERR_INVALID_ARG, "n_fast=%d < 1 (regular mode is rsim_direct_sum)", n_fast);
+    if (!is_pow2(n_doppler) || n_doppler > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [1, 4096]", n_doppler);
+    if (radar && (int64_t)radar->n_gates * n_doppler > ((int64_t)1 << 24))
+        return fail(RSIM_ERR_INVALID_ARG, "n_gates * n_doppler > 2^24");
+    if (update0 < 0) return fail(RSIM_ERR_INVALID_ARG, "update0 < 0");
+    if (update0 > (((int64_t)1 << 52) / n_fast)) return fail(RSIM_ERR_INVALID_ARG, "update0 too large");
+    return run_accumulate(radar, platform, scat, update0 * (int64_t)n_fast, n_fast, n_updates,
+                          n_doppler, true, precision, spectra, workspace, workspace_bytes, stream);
+}
+
+rsim_status rsim_synth_pulses(const rsim_radar* radar, const void* spectra, int32_t n_spectra,
+                              int64_t update0, int32_t n_fast, int32_t n_doppler,
+                              int64_t pulse0, int32_t n_pulses, rsim_window window,
+                              rsim_precision precision, void* iq, cudaStream_t stream) {
+    rsim_status st = check_synth_args(radar, n_spectra, update0, n_fast, n_doppler, pulse0,
+                                      n_pulses, (int)window, precision);
+    if (st != RSIM_OK) return st;
+    if (n_pulses == 0) return RSIM_OK;
+    const bool fp64 = precision == RSIM_FP64;
+    if (!spectra || !iq) return fail(RSIM_ERR_INVALID_ARG, "spectra / iq is NULL");
+    if (!aligned(spectra, fp64 ? 16 : 8) || !aligned(iq, fp64 ? 16 : 8))
+        return fail(RSIM_ERR_INVALID_ARG, "spectra / iq misaligned");
+    const rsim::SynthArgs a = make_synth_args(radar, n_spectra, update0, n_fast, n_doppler, pulse0,
+                                              n_pulses, (int)window);
+    const cudaError_t e = rsim::launch_synth(a, fp64, spectra, iq, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synth kernel launch");
+    return RSIM_OK;
+}
+
+rsim_status rsim_scatterer_cells(const rsim_radar* radar, const rsim_platform* platform,
+                                 const rsim_scatterers* scat, int64_t pulse, int32_t n_doppler,
+                                 rsim_precision precision, int32_t* gate, int32_t* bin,
+                                 double* gate_coord, double* bin_coord, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_platform(platform)) != RSIM_OK) return st;
+    if ((st = check_scat(scat)) != RSIM_OK) return st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (!is_pow2(n_doppler) || n_doppler > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [1, 4096]", n_doppler);
+    if (pulse < 0 || pulse > ((int64_t)1 << 52)) return fail(RSIM_ERR_INVALID_ARG, "pulse out of range");
+    if (scat->n == 0) return RSIM_OK;
+    const rsim::Model m = make_model(radar, platform, scat, n_doppler);
+    const rsim::Scat sc = make_scat(scat);
+    const cudaError_t e = rsim::launch_cells(m, pulse, precision == RSIM_FP64, n_doppler > 1, sc,
+                                             gate, bin, gate_coord, bin_coord, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cells kernel launch");
+    return RSIM_OK;
+}
+
+rsim_status rsim_synth_pulses_backward(const rsim_radar* radar, const void* grad_iq,
+                                       int32_t n_spectra, int64_t update0, int32_t n_fast,
+                                       int32_t n_doppler, int64_t pulse0, int32_t n_pulses,
+                                       rsim_window window, rsim_precision precision,
+                                       void* grad_spectra, cudaStream_t stream) {
+    rsim_status st = check_synth_args(radar, n_spectra, update0, n_fast, n_doppler, pulse0,
+                                      n_pulses, (int)window, precision);
+    if (st != RSIM_OK) return st;
+    if (n_spectra == 0) return RSIM_OK;
+    const bool fp64 = precision == RSIM_FP64;
+    if (!grad_spectra || (n_pulses > 0 && !grad_iq))
+        return fail(RSIM_ERR_INVALID_ARG, "grad_iq / grad_spectra is NULL");
+    if (!aligned(grad_spectra, fp64 ? 16 : 8) || (grad_iq && !aligned(grad_iq, fp64 ? 16 : 8)))
+        return fail(RSIM_ERR_INVALID_ARG, "grad_iq / grad_spectra misaligned");
+    const rsim::SynthArgs a = make_synth_args(radar, n_spectra, update0, n_fast, n_doppler, pulse0,
+                                              n_pulses, (int)window);
+    const cudaError_t e = rsim::launch_synth_backward(a, fp64, grad_iq, grad_spectra, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synth backward kernel launch");
+    return RSIM_OK;
+}
+
+static rsim_status run_backward(const rsim_radar* radar, const rsim_platform* platform,
+                                const rsim_scatterers* scat, int64_t pulse_base, int32_t stride,
+                                int32_t n_samples, int32_t n_doppler, bool doppler,
+                                rsim_precision precision, const void* G, float* grad_z,
+                                float* grad_nrcs, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_platform(platform)) != RSIM_OK) return st;
+    if ((st = check_scat(scat)) != RSIM_OK) return st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (n_samples < 0 || pulse_base < 0) return fail(RSIM_ERR_INVALID_ARG, "negative count or index");
+    if (pulse_base + (int64_t)n_samples * stride > ((int64_t)1 << 52))
+        return fail(RSIM_ERR_INVALID_ARG, "pulse index out of range");
+    if (n_samples == 0 || scat->n == 0 || (!grad_z && !grad_nrcs)) return RSIM_OK;
+    const bool fp64 = precision == RSIM_FP64;
+    if (!G) return fail(RSIM_ERR_INVALID_ARG, "incoming gradient is NULL");
+    if (!aligned(G, fp64 ? 16 : 8)) return fail(RSIM_ERR_INVALID_ARG, "incoming gradient misaligned");
+    const rsim::Model m = make_model(radar, platform, scat, n_doppler);
+    const rsim::Scat sc = make_scat(scat);
+    rsim::Schedule sch;
+    sch.pulse_base = pulse_base;
+    sch.pulse_stride = stride;
+    sch.n_samples = n_samples;
+    sch.samples_per_group = n_samples;
+    sch.pad = 0;
+    const cudaError_t e = rsim::launch_backward(m, sch, sc, fp64, doppler, G, grad_z, grad_nrcs, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
+    return RSIM_OK;
+}
+
+rsim_status rsim_doppler_accumulate_backward(const rsim_radar* radar,
+                                             const rsim_platform* platform,
+                                             const rsim_scatterers* scat, int64_t update0,
+                                             int32_t n_updates, int32_t n_fast,
+                                             int32_t n_doppler, rsim_precision precision,
+                                             const void* grad_spectra, float* grad_z,
+                                             float* grad_nrcs, cudaStream_t stream) {
+    if (n_fast < 1) return fail(RSIM_ERR_INVALID_ARG, "n_fast=%d < 1", n_fast);
+    if (!is_pow2(n_doppler) || n_doppler > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [1, 4096]", n_doppler);
+    if (update0 < 0 || update0 > (((int64_t)1 << 52) / n_fast))
+        return fail(RSIM_ERR_INVALID_ARG, "update0 out of range");
+    return run_backward(radar, platform, scat, update0 * (int64_t)n_fast, n_fast, n_updates,
+                        n_doppler, true, precision, grad_spectra, grad_z, grad_nrcs, stream);
+}
+
+rsim_status rsim_direct_sum_backward(const rsim_radar* radar, const rsim_platform* platform,
+                                     const rsim_scatterers* scat, int64_t pulse0,
+                                     int32_t n_pulses, rsim_precision precision,
+                                     const void* grad_iq, float* grad_z, float* grad_nrcs,
+                                     cudaStream_t stream) {
+    return run_backward(radar, platform, scat, pulse0, 1, n_pulses, 1, false, precision, grad_iq,
+                        grad_z, grad_nrcs, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,452 @@
+// rsim_internal.cuh -- device-side model, per-scatterer evaluation and the
+// deterministic warp-level scatter-add shared by the summation kernels.
+//
+// Method: arXiv 2408.11472.  Regular mode: complex sum of every scatterer into its
+// range gate at each pulse (Section II.A, Fig. 1 step 4).  Fast mode: Algorithm 1 of
+// Section III.B -- at each update pulse p_i the scatterer's complex amplitude C_i,
+// range R_i and pulse-pair Doppler D_i = arg(conj(C_{i+1}) C_i) PRF are rasterised
+// into a (gate, Doppler bin) spectrum.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsim {
+
+constexpr int kThreads = 256;                 // summation CTA size
+constexpr int kItems = 4;                     // consecutive scatterers per thread
+constexpr int kChunk = kThreads * kItems;     // scatterers sharing one FP64 reference point
+constexpr int kTab = 64;                      // samples per block of reference constants
+constexpr double kFixScale = 4294967296.0;    // fixed point: value = q * 2^-32
+constexpr float kFixScaleF = 4294967296.0f;
+// Split path: an FP32 gate / bin coordinate this close to an integer edge is re-decided
+// in FP64 (the FP32 coordinate errors are below ~1e-6 gates and ~3e-7 bins).
+constexpr float kGateEps = 2e-5f;
+constexpr float kBinEps = 5e-6f;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+constexpr float kInvLn2F = 1.44269504088896340736f;
+
+// Host-prepared constants of the model (kernel parameter).
+struct Model {
+    double prf, inv_prf;
+    double p0[3];           // platform position at t = 0, relative to the scene origin
+    double v[3];            // platform velocity
+    double r_ref0, r_ref_rate;
+    double two_over_lambda; // cycles of two-way phase per metre of range
+    double inv_gw;          // 1 / gate width
+    double half_gates;      // n_gates / 2
+    double beam_k;          // exponent of 2 in the pattern: -2 / beamwidth^2
+    double area;            // facet area
+    int n_gates;
+    int n_doppler;          // 1 in regular mode
+    // FP32 copies for the split path
+    float inv_gw_f, beam_k_f, chi_hi, chi_lo, dt_f, hdt_f, ep[3];
+};
+
+// Sample schedule: sample s is pulse pulse_base + s * pulse_stride.
+struct Schedule {
+    int64_t pulse_base;
+    int32_t pulse_stride;
+    int32_t n_samples;
+    int32_t samples_per_group;  // gridDim.y splits the samples into groups of this size
+    int32_t pad;
+};
+
+struct Scat {
+    const float *x, *y, *z, *vx, *vy, *vz, *nrcs;
+    int64_t n;
+    int vec4;  // all arrays 16-byte aligned: load 4 consecutive scatterers as float4
+    int pad;
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ int clamp_floor(double v) {
+    return (int)floor(fmax(fmin(v, 1.0e9), -1.0e9));
+}
+
+__device__ __forceinline__ double platform_coord(const Model& m, int i, double t) {
+    return fma(m.v[i], t, m.p0[i]);
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 geometry of one scatterer at time t, platform at (Px, Py, Pz) relative to the
+// origin, reference range rref.  Range excess in the cancellation-free form
+// dR = (rho^2 + (dz - r_ref)(dz + r_ref)) / (R + r_ref).
+struct GeomD {
+    double dx, dy, dz, rho2, R, dR;
+};
+
+__device__ __forceinline__ GeomD geom_fp64(double t, double Px, double Py, double Pz, double rref,
+                                           double x, double y, double z, double vx, double vy,
+                                           double vz) {
+    GeomD g;
+    g.dx = Px - fma(vx, t, x);
+    g.dy = Py - fma(vy, t, y);
+    g.dz = Pz - fma(vz, t, z);
+    g.rho2 = fma(g.dx, g.dx, g.dy * g.dy);
+    g.R = sqrt(fma(g.dz, g.dz, g.rho2));
+    g.dR = fma(g.dz - rref, g.dz + rref, g.rho2) / (g.R + rref);
+    return g;
+}
+
+// Pre-floor pulse-pair Doppler bin coordinate nu n_doppler + 1/2 in FP64, with the range
+// change over one PRI D = (2 d.e + |e|^2) / (R + R'), e = (V - v) dt, and
+// nu = -2 D / lambda wrapped to [-1/2, 1/2) (phase advance of C per pulse, cycles).
+__device__ __forceinline__ double bin_coord_fp64(const Model& m, const GeomD& g, double vx,
+                                                 double vy, double vz) {
+    const double dt = m.inv_prf;
+    const double ex = (m.v[0] - vx) * dt, ey = (m.v[1] - vy) * dt, ez = (m.v[2] - vz) * dt;
+    const double n2 = fma(2.0, fma(g.dx, ex, fma(g.dy, ey, g.dz * ez)),
+                          fma(ex, ex, fma(ey, ey, ez * ez)));
+    const double D0 = n2 / (2.0 * g.R);
+    const double D = n2 / fma(2.0, g.R, D0);
+    double nu = -D * m.two_over_lambda;
+    nu -= rint(nu);
+    return fma(nu, (double)m.n_doppler, 0.5);
+}
+
+// FP64 index decisions (gate and pulse-pair Doppler bin) of one scatterer at time t.
+// Used by the FP64 path and to re-decide near-edge split-path items, so both paths take
+// bit-identical decisions.
+__device__ __forceinline__ void decide_fp64(const Model& m, double t, double x, double y, double z,
+                                            double vx, double vy, double vz, bool doppler,
+                                            int& g, int& kb, double& gc, double& bc) {
+    const double rref = fma(m.r_ref_rate, t, m.r_ref0);
+    const GeomD gd = geom_fp64(t, platform_coord(m, 0, t), platform_coord(m, 1, t),
+                               platform_coord(m, 2, t), rref, x, y, z, vx, vy, vz);
+    gc = fma(gd.dR, m.inv_gw, m.half_gates);
+    g = clamp_floor(gc);
+    kb = 0;
+    bc = 0.5;
+    if (doppler) {
+        bc = bin_coord_fp64(m, gd, vx, vy, vz);
+        kb = clamp_floor(bc) & (m.n_doppler - 1);
+    }
+}
+
+// Per-sample constants of the FP64 path.
+struct Fp64Const {
+    double t, Px, Py, Pz;    // platform relative to the origin
+    double rref;             // r_ref(t)
+    double psiref;           // 2 r_ref / lambda - rint(.)  [cycles]
+};
+
+__device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, int64_t pulse) {
+    Fp64Const k;
+    k.t = (double)pulse * m.inv_prf;
+    k.Px = platform_coord(m, 0, k.t);
+    k.Py = platform_coord(m, 1, k.t);
+    k.Pz = platform_coord(m, 2, k.t);
+    k.rref = fma(m.r_ref_rate, k.t, m.r_ref0);
+    const double psi = k.rref * m.two_over_lambda;
+    k.psiref = psi - rint(psi);
+    return k;
+}
+
+// ---------------------------------------------------------------------------------------
+// Per (reference point c, sample) constants of the split path, computed in FP64 once
+// per CTA and sample and rounded to FP32.  D = P(t) - origin - c, R_c = |D|.
+struct SplitConst {
+    float t;                 // seconds
+    float Dx, Dy, Dz;        // D
+    float ux, uy, uz;        // D / R_c
+    float h;                 // 1 / (2 R_c)
+    float invRc;             // 1 / R_c
+    float gfrac;             // frac of the gate coordinate of c
+    int gint;                // floor of the gate coordinate of c
+    float psic;              // 2 R_c / lambda - rint(.)   [cycles]
+    float kappa;             // (r_ref / R_c)^2
+    float invDz, invDz2;     // 1 / D_z, 1 / D_z^2
+    float Mx, My, Mz;        // D + e_p / 2, e_p = platform displacement over one PRI
+    float K0hi, K0lo;        // (D + e_p/2) . e_p split into two floats
+    float pad;
+};
+
+__device__ __forceinline__ SplitConst make_split_const(const Model& m, int64_t pulse, float cx,
+                                                       float cy) {
+    SplitConst k;
+    const double t = (double)pulse * m.inv_prf;
+    const double Dx = platform_coord(m, 0, t) - (double)cx;
+    const double Dy = platform_coord(m, 1, t) - (double)cy;
+    const double Dz = platform_coord(m, 2, t);
+    const double Rc = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
+    const double rref = fma(m.r_ref_rate, t, m.r_ref0);
+    const double G = (Rc - rref) * m.inv_gw + m.half_gates;
+    const double Gi = floor(G);
+    double psi = Rc * m.two_over_lambda;
+    psi -= rint(psi);
+    const double inv = 1.0 / Rc;
+    const double dt = m.inv_prf;
+    const double epx = m.v[0] * dt, epy = m.v[1] * dt, epz = m.v[2] * dt;
+    const double Mx = Dx + 0.5 * epx, My = Dy + 0.5 * epy, Mz = Dz + 0.5 * epz;
+    const double K0 = Mx * epx + My * epy + Mz * epz;
+    k.t = (float)t;
+    k.Dx = (float)Dx; k.Dy = (float)Dy; k.Dz = (float)Dz;
+    k.ux = (float)(Dx * inv); k.uy = (float)(Dy * inv); k.uz = (float)(Dz * inv);
+    k.h = (float)(0.5 * inv);
+    k.invRc = (float)inv;
+    k.gint = (int)fmax(fmin(Gi, 1.0e9), -1.0e9);
+    k.gfrac = (float)(G - Gi);
+    k.psic = (float)psi;
+    k.kappa = (float)((rref * inv) * (rref * inv));
+    k.invDz = (float)(1.0 / Dz);
+    k.invDz2 = (float)(1.0 / (Dz * Dz));
+    k.Mx = (float)Mx; k.My = (float)My; k.Mz = (float)Mz;
+    k.K0hi = (float)K0;
+    k.K0lo = (float)(K0 - (double)k.K0hi);
+    k.pad = 0.f;
+    return k;
+}
+
+// Squared off-nadir angle from q^2 = (rho / d_z)^2: atan(q)^2 as a series for small q.
+__device__ __forceinline__ float theta2_f(float q2, float rho2, float dz) {
+    if (q2 < 1e-2f) return q2 * fmaf(q2, fmaf(q2, 23.0f / 45.0f, -2.0f / 3.0f), 1.0f);
+    const float th = atan2f(sqrtf(rho2), dz);
+    return th * th;
+}
+
+__device__ __forceinline__ double theta2_d(double rho2, double dz) {
+    const double q2 = rho2 / (dz * dz);
+    if (q2 < 1e-3) {
+        return q2 * fma(q2, fma(q2, fma(q2, -44.0 / 105.0, 23.0 / 45.0), -2.0 / 3.0), 1.0);
+    }
+    const double th = atan2(sqrt(rho2), dz);
+    return th * th;
+}
+
+// Scatterer registers of the split path (positions relative to the CTA reference point).
+struct ItemF {
+    float lx0, ly0, z, vx, vy, vz, amp0;
+};
+
+// Quantities the adjoint needs besides C.
+struct DerivF {
+    float dlna;  // d ln|C| / dz
+    float dphi;  // d arg C / dz  [rad / m]
+};
+
+// Split-path evaluation of one scatterer at the sample described by k.  Returns the
+// cell key g * n_doppler + bin, or -1 when out of the range window or not a scatterer.
+// gc_out / bc_out (optional) receive the pre-floor coordinates behind the decision.
+template <bool DOPPLER, bool DERIV>
+__device__ __forceinline__ int eval_split(const Model& m, const SplitConst& k, const ItemF& it,
+                                          const Scat& sc, int64_t n, int64_t pulse, float& re,
+                                          float& im, DerivF* dv, int* g_out = nullptr,
+                                          double* gc_out = nullptr, double* bc_out = nullptr) {
+    const float lx = fmaf(it.vx, k.t, it.lx0);
+    const float ly = fmaf(it.vy, k.t, it.ly0);
+    const float lz = fmaf(it.vz, k.t, it.z);
+    // R - R_c = (|l|^2 - 2 D.l) / (R + R_c)
+    const float ul = fmaf(k.ux, lx, fmaf(k.uy, ly, k.uz * lz));
+    const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+    const float dR0 = fmaf(ll, k.h, -ul);
+    const float dR = dR0 * fmaf(-dR0, k.h, 1.0f);
+    const float gcf = fmaf(dR, m.inv_gw_f, k.gfrac);
+    int g = k.gint + (int)floorf(gcf);
+    bool refine = fabsf(gcf - rintf(gcf)) < kGateEps;
+    // antenna: theta^2 with 1 / d_z^2 ~ (1 / D_z^2)(1 + 2 l_z / D_z)
+    const float dx = k.Dx - lx, dy = k.Dy - ly;
+    const float rho2 = fmaf(dx, dx, dy * dy);
+    const float q2 = rho2 * (k.invDz2 * fmaf(2.0f * lz, k.invDz, 1.0f));
+    const float th2 = theta2_f(q2, rho2, k.Dz - lz);
+    // |C| = sqrt(sigma A) 2^(-2 theta^2 / theta_b^2) (r_ref / R_c)^2 (1 + dR / R_c)^-2
+    const float xr = dR * k.invRc;
+    const float E = fmaf(th2, m.beam_k_f, xr * fmaf(xr, kInvLn2F, -2.0f * kInvLn2F));
+    const float a = it.amp0 * k.kappa * ex2_approx(E);
+    // phase in cycles: psi_c + dR * 2 / lambda (2/lambda as hi + lo, product error-free)
+    const float p = dR * m.chi_hi;
+    const float perr = fmaf(dR, m.chi_hi, -p);
+    float f = (p - rintf(p)) + (k.psic + fmaf(dR, m.chi_lo, perr));
+    f -= rintf(f);
+    float sn, cs;
+    __sincosf(kTwoPiF * f, &sn, &cs);
+    re = a * cs;
+    im = -a * sn;
+    int kb = 0;
+    float bc = 0.5f;
+    if (DOPPLER) {
+        // D = R(t + dt) - R(t) = 2 (d + e/2).e / (R + R'),  d = D - l,  e = e_p - v dt,
+        // (d + e/2).e = K0 - dt (M.v) - (l + v dt / 2).e
+        const float ex = fmaf(-it.vx, m.dt_f, m.ep[0]);
+        const float ey = fmaf(-it.vy, m.dt_f, m.ep[1]);
+        const float ez = fmaf(-it.vz, m.dt_f, m.ep[2]);
+        const float mx = fmaf(it.vx, m.hdt_f, lx);
+        const float my = fmaf(it.vy, m.hdt_f, ly);
+        const float mz = fmaf(it.vz, m.hdt_f, lz);
+        const float Mv = fmaf(k.Mx, it.vx, fmaf(k.My, it.vy, k.Mz * it.vz));
+        const float me = fmaf(mx, ex, fmaf(my, ey, mz * ez));
+        const float hn2 = (fmaf(-m.dt_f, Mv, k.K0hi) - me) + k.K0lo;
+        const float D = hn2 * k.invRc * fmaf(-dR, k.invRc, 1.0f);
+        float nu = -D * m.chi_hi;
+        nu -= rintf(nu);
+        bc = fmaf(nu, (float)m.n_doppler, 0.5f);
+        kb = ((int)floorf(bc)) & (m.n_doppler - 1);
+        refine |= fabsf(bc - rintf(bc)) < kBinEps;
+    }
+    if (DERIV) {
+        // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
+        // d ln a / dz = 2 d_z / R^2 - 4 ln2 theta rho / (theta_b^2 R^2), d phi / dz = 4 pi d_z / (lambda R)
+        const float dz = k.Dz - lz;
+        const float invR = k.invRc * fmaf(-dR, k.invRc, 1.0f);
+        const float invR2 = invR * invR;
+        float rho_theta;
+        if (q2 < 1e-2f) {
+            rho_theta = rho2 / dz * fmaf(q2, fmaf(q2, 0.2f, -1.0f / 3.0f), 1.0f);
+        } else {
+            rho_theta = sqrtf(rho2) * atan2f(sqrtf(rho2), dz);
+        }
+        // beam_k = -2 / theta_b^2 (base 2), so -4 ln2 / theta_b^2 = 2 ln2 beam_k
+        dv->dlna = (2.0f * dz + 1.38629436111989061883f * m.beam_k_f * rho_theta) * invR2;
+        dv->dphi = kTwoPiF * (m.chi_hi + m.chi_lo) * dz * invR;  // chi = 2 / lambda
+    }
+    double gcd = (double)k.gint + (double)gcf, bcd = (double)bc;
+    if (refine && n < sc.n) {
+        int g2, kb2;
+        decide_fp64(m, (double)pulse * m.inv_prf, (double)__ldg(sc.x + n), (double)__ldg(sc.y + n),
+                    (double)it.z, (double)it.vx, (double)it.vy, (double)it.vz, DOPPLER, g2, kb2,
+                    gcd, bcd);
+        g = g2;
+        kb = kb2;
+    }
+    if (g_out) *g_out = g;
+    if (gc_out) *gc_out = gcd;
+    if (bc_out) *bc_out = bcd;
+    return (n < sc.n && g >= 0 && g < m.n_gates) ? g * m.n_doppler + kb : -1;
+}
+
+// Scatterer registers of the FP64 path (positions relative to the origin).
+struct ItemD {
+    float x, y, z, vx, vy, vz;
+    double amp0;
+};
+
+struct DerivD {
+    double dlna, dphi;
+};
+
+template <bool DOPPLER, bool DERIV>
+__device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, const ItemD& it,
+                                         int64_t n, int64_t n_total, double& re, double& im,
+                                         DerivD* dv, int* g_out = nullptr,
+                                         double* gc_out = nullptr, double* bc_out = nullptr) {
+    const double vx = it.vx, vy = it.vy, vz = it.vz;
+    const GeomD gd = geom_fp64(k.t, k.Px, k.Py, k.Pz, k.rref, (double)it.x, (double)it.y,
+                               (double)it.z, vx, vy, vz);
+    const double gc = fma(gd.dR, m.inv_gw, m.half_gates);
+    const int g = clamp_floor(gc);
+    const double th2 = theta2_d(gd.rho2, gd.dz);
+    const double rr = k.rref / gd.R;
+    const double a = it.amp0 * exp2(m.beam_k * th2) * rr * rr;
+    double f = k.psiref + gd.dR * m.two_over_lambda;
+    f -= rint(f);
+    double sn, cs;
+    sincospi(2.0 * f, &sn, &cs);
+    re = a * cs;
+    im = -a * sn;
+    int kb = 0;
+    double bc = 0.5;
+    if (DOPPLER) {
+        bc = bin_coord_fp64(m, gd, vx, vy, vz);
+        kb = clamp_floor(bc) & (m.n_doppler - 1);
+    }
+    if (DERIV) {
+        const double R2 = gd.R * gd.R;
+        double rho_theta;
+        const double q2 = gd.rho2 / (gd.dz * gd.dz);
+        if (q2 < 1e-3) {
+            rho_theta = gd.rho2 / gd.dz * fma(q2, fma(q2, fma(q2, -1.0 / 7.0, 0.2), -1.0 / 3.0), 1.0);
+        } else {
+            rho_theta = sqrt(gd.rho2) * atan2(sqrt(gd.rho2), gd.dz);
+        }
+        dv->dlna = (2.0 * gd.dz + 2.0 * 0.69314718055994530942 * m.beam_k * rho_theta) / R2;
+        dv->dphi = 2.0 * 3.14159265358979323846 * m.two_over_lambda * gd.dz / gd.R;
+    }
+    if (g_out) *g_out = g;
+    if (gc_out) *gc_out = gc;
+    if (bc_out) *bc_out = bc;
+    return (n < n_total && g >= 0 && g < m.n_gates) ? g * m.n_doppler + kb : -1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Deterministic scatter-add.  Contributions are summed in 64-bit fixed point
+// (q = rint(v * 2^32)); integer addition is associative, so the result does not depend
+// on the order in which atomics land.  Before touching memory, each warp merges runs of
+// equal keys: in-lane over the thread's consecutive scatterers, then across lanes with a
+// segmented Hillis-Steele scan (fixed order), so only run tails are emitted.
+template <typename T>
+__device__ __forceinline__ long long to_fixed(T v);
+template <>
+__device__ __forceinline__ long long to_fixed<float>(float v) { return __float2ll_rn(v * kFixScaleF); }
+template <>
+__device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v * kFixScale); }
+
+template <typename T>
+__device__ __forceinline__ void emit_cell(unsigned long long* __restrict__ base, int key, T re,
+                                          T im) {
+    const long long qr = to_fixed(re), qi = to_fixed(im);
+    if (qr) atomicAdd(base + 2 * (int64_t)key, (unsigned long long)qr);
+    if (qi) atomicAdd(base + 2 * (int64_t)key + 1, (unsigned long long)qi);
+}
+
+template <typename T, int J>
+__device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&re)[J],
+                                                 const T (&im)[J],
+                                                 unsigned long long* __restrict__ base) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    T rr = re[0], ri = im[0];
+    T first_r = T(0), first_i = T(0);
+    bool split = false;  // the lane holds more than one run
+#pragma unroll
+    for (int q = 1; q < J; ++q) {
+        if (key[q] != key[q - 1]) {
+            if (!split) {
+                first_r = rr;
+                first_i = ri;
+                split = true;
+            } else if (key[q - 1] >= 0) {
+                emit_cell(base, key[q - 1], rr, ri);  // interior run: complete
+            }
+            rr = re[q];
+            ri = im[q];
+        } else {
+            rr += re[q];
+            ri += im[q];
+        }
+    }
+    const int kfirst = key[0], klast = key[J - 1];
+    const int prev_last = __shfl_up_sync(kFull, klast, 1);
+    const bool link = lane > 0 && prev_last == kfirst;  // first run continues lane-1's last run
+    T cr = rr, ci = ri;
+    int head = (split || !link) ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T ur = __shfl_up_sync(kFull, cr, d);
+        const T ui = __shfl_up_sync(kFull, ci, d);
+        const int uh = __shfl_up_sync(kFull, head, d);
+        if (lane >= d && !head) {
+            cr = ur + cr;
+            ci = ui + ci;
+            head = uh;
+        }
+    }
+    T in_r = __shfl_up_sync(kFull, cr, 1), in_i = __shfl_up_sync(kFull, ci, 1);
+    const int next_link = __shfl_down_sync(kFull, link ? 1 : 0, 1);
+    const bool tail = (lane == 31) || !next_link;
+    if (split) {
+        if (kfirst >= 0) {
+            if (!link) { in_r = T(0); in_i = T(0); }
+            emit_cell(base, kfirst, in_r + first_r, in_i + first_i);
+        }
+        if (tail && klast >= 0) emit_cell(base, klast, rr, ri);
+    } else if (tail && klast >= 0) {
+        emit_cell(base, klast, cr, ci);
+    }
+}
+
+}  // namespace rsim

@@ -1,0 +1,36 @@
+// rsim_kernels.h -- host-side launchers of the library's kernels (internal interface
+// between the C ABI in abi.cu and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsim {
+
+struct Model;
+struct Schedule;
+struct Scat;
+
+cudaError_t launch_accumulate(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
+                              bool doppler, unsigned long long* ws, dim3 grid,
+                              cudaStream_t stream);
+cudaError_t launch_finalize(const void* ws, void* out, int64_t n_vals, bool fp64, int n_sms,
+                            cudaStream_t stream);
+cudaError_t launch_cells(const Model& m, int64_t pulse, bool fp64, bool doppler, const Scat& sc,
+                         int32_t* gate, int32_t* bin, double* gc, double* bc, cudaStream_t stream);
+cudaError_t launch_backward(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
+                            bool doppler, const void* G, float* grad_z, float* grad_nrcs,
+                            cudaStream_t stream);
+
+// Post-processing (synth.cu).
+struct SynthArgs {
+    int n_gates, n_doppler, log2_nd, n_fast, n_spectra, n_pulses;
+    int64_t update0, pulse0;
+    int window;
+};
+cudaError_t launch_synth(const SynthArgs& a, bool fp64, const void* spectra, void* iq,
+                         cudaStream_t stream);
+cudaError_t launch_synth_backward(const SynthArgs& a, bool fp64, const void* grad_iq,
+                                  void* grad_spectra, cudaStream_t stream);
+
+}  // namespace rsim

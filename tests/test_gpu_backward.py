@@ -1,0 +1,132 @@
+"""GPU adjoint of the summation: parity with the FP64 oracle gradient, central finite
+differences of a waveform-power loss, and the autograd.Function wrappers (cfg4 shape,
+reduced surface)."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from helpers import DELTA_BIN, DELTA_GATE, np_, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsim():
+    import paper_2408_11472_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def case4():
+    c = sg.config(4)
+    L = 256
+    return c, sg.sea_surface(L, c["seed"])
+
+
+def _stable_mask(orc, rd, pf, sc, pulses, nd):
+    """Scatterers whose gate and bin coordinates are away from every edge at every pulse."""
+    ok = np.ones(sc["x"].size, bool)
+    for p in pulses:
+        g, b, gc, bc = orc.cells(rd, pf, sc, p, nd)
+        ok &= np.abs(gc - np.round(gc)) > 10 * DELTA_GATE
+        ok &= np.abs(bc - np.round(bc)) > 10 * DELTA_BIN
+    return ok
+
+
+def _target(Y):
+    return sg.target_waveform(Y.shape[0], Y.shape[1], 4242, (np.abs(Y) ** 2).mean(axis=0))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_fast_backward_vs_oracle_gradient(rsim, orc, case4, precision):
+    c, sc = case4
+    rd, pf, fp, P = c["radar"], c["platform"], c["fast"], c["n_pulses"]
+    dev = rsim.Scatterers.from_arrays(sc)
+    u0, S = rsim.spectra_range(0, P, fp.n_fast)
+    _, Y = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, precision)
+    Yn = np_(Y).astype(np.complex128)
+    target = _target(Yn)
+    GY = 4.0 * (np.abs(Yn) ** 2 - target) * Yn
+    cdt = torch.complex128 if precision == "fp64" else torch.complex64
+    GT = rsim.synth_pulses_backward(rd, torch.as_tensor(GY).to("cuda", cdt), S, u0, fp.n_fast,
+                                    fp.n_doppler, 0, fp.window)
+    gz, gs = rsim.doppler_accumulate_backward(rd, pf, dev, u0, fp.n_fast, GT)
+    GTref = orc.synth_grad(GY, S, u0, fp.n_fast, fp.n_doppler, 0, fp.window)
+    gz_o, gs_o = orc.fast_grad(rd, pf, sc, u0, fp.n_fast, GTref)
+    mask = _stable_mask(orc, rd, pf, sc, [(u0 + s) * fp.n_fast for s in range(S)], fp.n_doppler)
+    assert mask.mean() > 0.99
+    tol = 1e-5 if precision == "fp64" else 2e-3
+    assert rel_l2(np_(gz)[mask], gz_o[mask]) <= tol
+    assert rel_l2(np_(gs)[mask], gs_o[mask]) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_regular_backward_vs_oracle_gradient(rsim, orc, precision):
+    c = sg.config(0)
+    rd, pf = c["radar"], c["platform"]
+    sc = sg.sea_surface(128, 3)
+    dev = rsim.Scatterers.from_arrays(sc)
+    P = 16
+    Y = np_(rsim.direct_sum(rd, pf, dev, 0, P, precision)).astype(np.complex128)
+    GY = 4.0 * (np.abs(Y) ** 2 - _target(Y)) * Y
+    cdt = torch.complex128 if precision == "fp64" else torch.complex64
+    gz, gs = rsim.direct_sum_backward(rd, pf, dev, 0, torch.as_tensor(GY).to("cuda", cdt))
+    gz_o, gs_o = orc.direct_grad(rd, pf, sc, 0, GY)
+    mask = _stable_mask(orc, rd, pf, sc, range(P), 1)
+    tol = 1e-5 if precision == "fp64" else 2e-3
+    assert rel_l2(np_(gz)[mask], gz_o[mask]) <= tol
+    assert rel_l2(np_(gs)[mask], gs_o[mask]) <= tol
+
+
+def test_autograd_fast_mode_central_differences(rsim, orc, case4):
+    """torch.autograd through FastMode (FP64 path) vs central differences of the loss
+    L = sum (|Y|^2 - P*)^2 evaluated on the GPU, on 64 random scatterers."""
+    c, sc = case4
+    rd, pf, fp, P = c["radar"], c["platform"], c["fast"], c["n_pulses"]
+    dev = rsim.Scatterers.from_arrays(sc)
+    z = dev.z.clone().requires_grad_(True)
+    s = dev.nrcs.clone().requires_grad_(True)
+    Y = rsim.FastMode.apply(z, s, dev, rd, pf, 0, P, fp.n_fast, fp.n_doppler, fp.window, "fp64")
+    target = torch.as_tensor(_target(np_(Y))).cuda()
+    loss = ((Y.abs() ** 2 - target) ** 2).sum()
+    loss.backward()
+
+    def L_of(zz, ss):
+        Yp = rsim.FastMode.apply(zz, ss, dev, rd, pf, 0, P, fp.n_fast, fp.n_doppler, fp.window,
+                                 "fp64")
+        return ((Yp.abs() ** 2 - target) ** 2).sum().item()
+
+    u0, S = rsim.spectra_range(0, P, fp.n_fast)
+    mask = _stable_mask(orc, rd, pf, sc, [(u0 + q) * fp.n_fast for q in range(S)], fp.n_doppler)
+    rng = np.random.Generator(np.random.PCG64(64))
+    picks = rng.choice(np.nonzero(mask)[0], size=64, replace=False)
+    h = 2.0 ** -16
+    gz = np_(z.grad)
+    gsn = np_(s.grad)
+    for n in picks:
+        zp, zm = dev.z.clone(), dev.z.clone()
+        zp[n] += h
+        zm[n] -= h
+        fd = (L_of(zp, dev.nrcs) - L_of(zm, dev.nrcs)) / float(zp[n] - zm[n])
+        assert gz[n] == pytest.approx(fd, rel=2e-3, abs=2e-4 * np.abs(gz).max())
+    for n in picks[:16]:
+        sp, sm = dev.nrcs.clone(), dev.nrcs.clone()
+        sp[n] *= 1 + 2.0 ** -10
+        sm[n] *= 1 - 2.0 ** -10
+        fd = (L_of(dev.z, sp) - L_of(dev.z, sm)) / float(sp[n] - sm[n])
+        assert gsn[n] == pytest.approx(fd, rel=2e-3, abs=2e-4 * np.abs(gsn).max())
+
+
+def test_autograd_regular_mode_matches_direct_calls(rsim):
+    c = sg.config(0)
+    rd, pf = c["radar"], c["platform"]
+    dev = rsim.Scatterers.from_arrays(sg.sea_surface(64, 2))
+    z = dev.z.clone().requires_grad_(True)
+    s = dev.nrcs.clone().requires_grad_(True)
+    Y = rsim.RegularMode.apply(z, s, dev, rd, pf, 0, 8, "split")
+    loss = (Y.abs() ** 2).sum()
+    loss.backward()
+    GY = 2.0 * Y.detach()
+    gz, gs = rsim.direct_sum_backward(rd, pf, dev, 0, GY)
+    assert torch.equal(z.grad, gz) and torch.equal(s.grad, gs)

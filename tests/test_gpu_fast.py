@@ -1,0 +1,150 @@
+"""GPU parity of the fast mode (Algorithm 1 spectra + Section III.B post-processing)
+against the FP64 oracle, through the C ABI, from small scenes to the full cfg1 scene."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from helpers import TOL, gpu_cells, index_agreement, np_, rel_l2
+
+pytestmark = pytest.mark.gpu
+PRECISIONS = ["fp64", "split"]
+
+
+@pytest.fixture(scope="module")
+def rsim():
+    import paper_2408_11472_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def small():
+    c = sg.config(1)
+    return c, sg.sea_surface(256, 1)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_spectra_parity_small(rsim, orc, small, precision):
+    """256 x 256 surface on the cfg1 track; 9 updates from update 30 (several CTAs, ragged
+    sample blocks, Doppler on both sides of zero)."""
+    c, sc = small
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    dev = rsim.Scatterers.from_arrays(sc)
+    u0, S = 30, 9
+    T = np_(rsim.doppler_accumulate(rd, pf, dev, u0, S, fp.n_fast, fp.n_doppler, precision))
+    pulses = [(u0 + s) * fp.n_fast for s in range(S)]
+    G, B = gpu_cells(rsim, rd, pf, dev, pulses, fp.n_doppler, precision)
+    for j, p in enumerate(pulses[::4]):
+        g_o, b_o, gc_o, bc_o = orc.cells(rd, pf, sc, p, fp.n_doppler)
+        index_agreement(G[4 * j], B[4 * j], gc_o, bc_o, g_o, b_o, fp.n_doppler)
+    Tref = orc.doppler_spectra_cells(rd, pf, sc, u0, fp.n_fast, fp.n_doppler, G, B)
+    err = rel_l2(T, Tref)
+    assert err <= TOL[precision], err
+    # honest end-to-end error against the oracle's own decisions (bin flips included)
+    Tor = orc.doppler_spectra(rd, pf, sc, u0, S, fp.n_fast, fp.n_doppler)
+    assert rel_l2(T, Tor) <= 3e-2
+
+
+def test_spectra_deterministic(rsim, small):
+    c, sc = small
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    dev = rsim.Scatterers.from_arrays(sc)
+    for precision in PRECISIONS:
+        a = rsim.doppler_accumulate(rd, pf, dev, 3, 5, fp.n_fast, fp.n_doppler, precision)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b = rsim.doppler_accumulate(rd, pf, dev, 3, 5, fp.n_fast, fp.n_doppler, precision)
+        s.synchronize()
+        assert torch.equal(a, b)
+
+
+def test_single_bin_spectra_equal_regular_mode_bitwise(rsim, small):
+    """With one Doppler bin the spectrum of update i is the regular-mode pulse p_i: the
+    same contributions in the same cells give identical fixed-point sums."""
+    c, sc = small
+    rd, pf = c["radar"], c["platform"]
+    dev = rsim.Scatterers.from_arrays(sc)
+    for precision in PRECISIONS:
+        T = rsim.doppler_accumulate(rd, pf, dev, 2, 3, 64, 1, precision)
+        for s in range(3):
+            Y = rsim.direct_sum(rd, pf, dev, (2 + s) * 64, 1, precision)
+            assert torch.equal(T[s, :, 0], Y[0])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_simulate_fast_ragged_pulse_range(rsim, orc, small, precision):
+    """A pulse range that starts and ends mid-segment: spectra and blended pulses."""
+    c, sc = small
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    dev = rsim.Scatterers.from_arrays(sc)
+    p0, P = 1000, 301
+    T, Y = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, precision, p0)
+    u0, S = rsim.spectra_range(p0, P, fp.n_fast)
+    Tn = np_(T)
+    G, B = gpu_cells(rsim, rd, pf, dev, [(u0 + s) * fp.n_fast for s in range(S)], fp.n_doppler,
+                     precision)
+    Tref = orc.doppler_spectra_cells(rd, pf, sc, u0, fp.n_fast, fp.n_doppler, G, B)
+    assert rel_l2(Tn, Tref) <= TOL[precision]
+    Yref = orc.synth(Tref, u0, fp.n_fast, p0, P, fp.window)
+    assert rel_l2(np_(Y), Yref) <= TOL[precision]
+
+
+def test_fast_mode_equals_regular_at_update_pulses(rsim, small):
+    c, sc = small
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    dev = rsim.Scatterers.from_arrays(sc)
+    T, Y = rsim.simulate_fast(rd, pf, dev, 256, fp.n_fast, fp.n_doppler, fp.window, "fp64", 128)
+    for x in (128, 192, 256, 320):
+        Yr = rsim.direct_sum(rd, pf, dev, x, 1, "fp64")[0]
+        assert rel_l2(np_(Y[x - 128]), np_(Yr)) < 1e-12
+
+
+def test_large_cell_grids(rsim, orc):
+    """4096 gates x 16 bins against the oracle; the largest grid (128 x 4096 bins) through
+    its index decisions and its bin-summed spectrum (= the single-bin spectrum)."""
+    rd = sg.RadarParams(n_gates=4096, gate_width_m=0.05)
+    pf = sg.nadir_track(4096)
+    sc = sg.sea_surface(64, 12)
+    dev = rsim.Scatterers.from_arrays(sc)
+    for precision in PRECISIONS:
+        T = np_(rsim.doppler_accumulate(rd, pf, dev, 10, 1, 64, 16, precision))
+        G, B = gpu_cells(rsim, rd, pf, dev, [640], 16, precision)
+        Tref = orc.doppler_spectra_cells(rd, pf, sc, 10, 64, 16, G, B)
+        assert np.abs(Tref).max() > 0
+        assert rel_l2(T, Tref) <= TOL[precision]
+    rd = sg.RadarParams()
+    for precision in PRECISIONS:
+        T = rsim.doppler_accumulate(rd, pf, dev, 10, 2, 64, 4096, precision)
+        T1 = rsim.doppler_accumulate(rd, pf, dev, 10, 2, 64, 1, precision)
+        assert rel_l2(np_(T.sum(-1)), np_(T1[..., 0])) < 1e-6
+        g, b, _, _ = rsim.scatterer_cells(rd, pf, dev, 640, 4096, precision)
+        g_o, b_o, gc_o, bc_o = orc.cells(rd, pf, sc, 640, 4096)
+        index_agreement(np_(g), np_(b), gc_o, bc_o, g_o, b_o, 4096)
+
+
+def test_full_cfg1_sampled(rsim, orc):
+    """cfg1 at full size in the benchmark's launch configuration: 4.19M scatterers,
+    65 spectra of 128 x 64, 4096 pulses, split precision.  Spectra checked on 5 sampled
+    updates against the oracle (GPU decisions) -- plus the index decisions and the honest
+    end-to-end error with the oracle's own decisions; the pulses checked against the
+    oracle's post-processing of the GPU spectra."""
+    c = sg.config(1)
+    rd, pf, fp, P = c["radar"], c["platform"], c["fast"], c["n_pulses"]
+    sc = sg.sea_surface(c["L"], c["seed"])
+    dev = rsim.Scatterers.from_arrays(sc)
+    T, Y = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, "split")
+    Tn, Yn = np_(T), np_(Y)
+    assert Tn.shape == (65, 128, 64) and Yn.shape == (4096, 128)
+    samp = [0, 16, 32, 48, 64]
+    G, B = gpu_cells(rsim, rd, pf, dev, [u * fp.n_fast for u in samp], fp.n_doppler, "split")
+    for j, u in enumerate(samp):
+        Tref = orc.doppler_spectra_cells(rd, pf, sc, u, fp.n_fast, fp.n_doppler, G[j:j + 1],
+                                         B[j:j + 1])
+        assert rel_l2(Tn[u:u + 1], Tref) <= TOL["split"]
+    g_o, b_o, gc_o, bc_o = orc.cells(rd, pf, sc, 32 * fp.n_fast, fp.n_doppler)
+    fg, fb = index_agreement(G[2], B[2], gc_o, bc_o, g_o, b_o, fp.n_doppler)
+    assert fg < 1e-4 and fb < 1e-3
+    Tor = orc.doppler_spectra(rd, pf, sc, 32, 1, fp.n_fast, fp.n_doppler)
+    assert rel_l2(Tn[32:33], Tor) <= 3e-2
+    Yref = orc.synth(Tn.astype(np.complex128), 0, fp.n_fast, 0, P, fp.window)
+    assert rel_l2(Yn, Yref) <= 1e-5

@@ -277,3 +277,19 @@ def test_empty_scene(orc):
     sc = {k: np.zeros(0, np.float32) for k in ("x", "y", "z", "vx", "vy", "vz", "nrcs")}
     assert np.all(orc.direct_sum(rd, pf, sc, 0, 3) == 0)
     assert np.all(orc.doppler_spectra(rd, pf, sc, 0, 2, 64, 64) == 0)
+
+
+def test_decided_cell_variants_reproduce_the_oracle(orc):
+    """With the oracle's own decisions, the decided-cell variants give the same sums."""
+    rd = sg.RadarParams()
+    P, nf, nd = 128, 32, 32
+    pf = sg.nadir_track(P)
+    sc = _small_scene(40, 9)
+    gates = np.stack([orc.cells(rd, pf, sc, p, nd)[0] for p in range(3, 9)])
+    np.testing.assert_array_equal(orc.direct_sum_cells(rd, pf, sc, 3, gates),
+                                  orc.direct_sum(rd, pf, sc, 3, 6))
+    cells = [orc.cells(rd, pf, sc, u * nf, nd) for u in range(1, 4)]
+    G = np.stack([c[0] for c in cells])
+    B = np.stack([c[1] for c in cells])
+    np.testing.assert_array_equal(orc.doppler_spectra_cells(rd, pf, sc, 1, nf, nd, G, B),
+                                  orc.doppler_spectra(rd, pf, sc, 1, 3, nf, nd))
