@@ -73,7 +73,7 @@ PROTOTYPES = {
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise ImportError(
-            "librsim.so is not built (%s); run `python -m paper_2408_11472_gb300.build` "
+            "librsim.so is not built (%s); run `python paper_2408_11472_gb300/build.py` "
             "(the CUDA library is required; there is no CPU fallback)" % path)
     lib = ctypes.CDLL(path)
     for name, (args, res) in PROTOTYPES.items():

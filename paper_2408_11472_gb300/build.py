@@ -4,7 +4,7 @@ Each translation unit is compiled in parallel for ``sm_103a`` only, then linked
 into ``paper_2408_11472_gb300/librsim.so`` (static CUDA runtime).  Rebuilds
 only when a source or header is newer than the library.
 
-    python -m paper_2408_11472_gb300.build [--force] [--verbose-ptxas]
+    python paper_2408_11472_gb300/build.py [--force] [--verbose-ptxas]
 """
 from __future__ import annotations
 
