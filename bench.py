@@ -61,7 +61,7 @@ def dist_env():
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -76,12 +76,13 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t_begin=None, t_end=None):
+        """Stop sampling; keep the samples stamped within [t_begin, t_end] (epoch s)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -91,10 +92,18 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            if ts is not None and t_begin is not None and not (t_begin - 0.05 <= ts <= t_end + 0.05):
+                continue
+            f = f[1:]
             try:
                 sm.append(float(f[1]))
                 smax.append(float(f[2]))
@@ -147,7 +156,7 @@ def oracle_fast_sample(radar, platform, scene, n_pulses, fp, target_s=10.0, thre
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsim", choices=["rsim", "reference"])
     ap.add_argument("--precision", default="split", choices=["split", "fp64"])
@@ -196,19 +205,22 @@ def main():
                                 out=T, workspace=ws)
         rsim.synth_pulses(rd, T, 0, fp.n_fast, 0, P, fp.window, out=Y)
 
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()                      # sampler warms up during the untimed warm-up
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if clocks:
+        time.sleep(0.3)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
     t0 = time.perf_counter()
+    t0_epoch = time.time()
     for e0, e1, e2 in ev:
         flush.fill_(1.0)                       # evict L2 between steps (not timed)
         e0.record(stream)
@@ -222,7 +234,8 @@ def main():
     wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
-    clk = clocks.stop() if clocks else None
+    t1_epoch = time.time()
+    clk = clocks.stop(t0_epoch, t1_epoch) if clocks else None
     step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in ev]
     acc_ms = [e0.elapsed_time(e1) for e0, e1, e2 in ev]
     total_ms = float(sum(step_ms))

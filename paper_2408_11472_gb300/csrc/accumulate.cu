@@ -19,11 +19,23 @@ namespace rsim {
 
 namespace {
 
-__device__ __forceinline__ void load4(const float* __restrict__ p, int64_t base, int64_t n,
-                                      bool vec, float (&v)[kItems]) {
+// Load kItems consecutive floats starting at base (vectorised when all arrays are 16-byte
+// aligned and the items are in range; base is a multiple of kItems).
+__device__ __forceinline__ void load_items(const float* __restrict__ p, int64_t base, int64_t n,
+                                           bool vec, float (&v)[kItems]) {
     if (vec && base + kItems <= n) {
-        const float4 q = __ldcs(reinterpret_cast<const float4*>(p + base));
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        if (kItems % 4 == 0) {
+#pragma unroll
+            for (int j = 0; j < kItems / 4; ++j) {
+                const float4 q = __ldcs(reinterpret_cast<const float4*>(p + base) + j);
+                v[4 * j + 0] = q.x; v[4 * j + 1] = q.y; v[4 * j + 2] = q.z; v[4 * j + 3] = q.w;
+            }
+        } else if (kItems == 2) {
+            const float2 q = __ldcs(reinterpret_cast<const float2*>(p + base));
+            v[0] = q.x; v[kItems - 1] = q.y;
+        } else {
+            v[0] = __ldcs(p + base);
+        }
     } else {
 #pragma unroll
         for (int q = 0; q < kItems; ++q) v[q] = (base + q < n) ? __ldcs(p + base + q) : 0.0f;
@@ -36,13 +48,13 @@ struct Raw {
 
 __device__ __forceinline__ void load_raw(const Scat& sc, int64_t base, Raw& r) {
     const bool vec = sc.vec4 != 0;
-    load4(sc.x, base, sc.n, vec, r.x);
-    load4(sc.y, base, sc.n, vec, r.y);
-    load4(sc.z, base, sc.n, vec, r.z);
-    load4(sc.vx, base, sc.n, vec, r.vx);
-    load4(sc.vy, base, sc.n, vec, r.vy);
-    load4(sc.vz, base, sc.n, vec, r.vz);
-    load4(sc.nrcs, base, sc.n, vec, r.s);
+    load_items(sc.x, base, sc.n, vec, r.x);
+    load_items(sc.y, base, sc.n, vec, r.y);
+    load_items(sc.z, base, sc.n, vec, r.z);
+    load_items(sc.vx, base, sc.n, vec, r.vx);
+    load_items(sc.vy, base, sc.n, vec, r.vy);
+    load_items(sc.vz, base, sc.n, vec, r.vz);
+    load_items(sc.nrcs, base, sc.n, vec, r.s);
 }
 
 // Reference point of the CTA's chunk: the (x, y) of its middle scatterer.
@@ -87,7 +99,7 @@ __device__ __forceinline__ int64_t sample_pulse(const Schedule& sch, int s) {
 
 // ------------------------------------------------------------------------------- forward
 template <bool DOPPLER>
-__global__ void __launch_bounds__(kThreads) accumulate_split_kernel(
+__global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
     Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
     __shared__ SplitConst tab[kTab];
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;

@@ -13,12 +13,24 @@
 
 namespace rsim {
 
-constexpr int kThreads = 256;                 // summation CTA size
-constexpr int kItems = 4;                     // consecutive scatterers per thread
+// Launch shape of the summation kernels (compile-time; the defaults are the tuned values).
+#ifndef RSIM_THREADS
+#define RSIM_THREADS 256
+#endif
+#ifndef RSIM_ITEMS
+#define RSIM_ITEMS 4
+#endif
+#ifndef RSIM_MIN_BLOCKS
+#define RSIM_MIN_BLOCKS 2
+#endif
+constexpr int kThreads = RSIM_THREADS;        // summation CTA size
+constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (1, 2, 4, 8)
+constexpr int kMinBlocks = RSIM_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
 constexpr int kChunk = kThreads * kItems;     // scatterers sharing one FP64 reference point
 constexpr int kTab = 64;                      // samples per block of reference constants
 constexpr double kFixScale = 4294967296.0;    // fixed point: value = q * 2^-32
-constexpr float kFixScaleF = 4294967296.0f;
+static_assert(kItems == 1 || kItems == 2 || kItems == 4 || kItems == 8, "items per thread");
+static_assert(kThreads >= kTab && kThreads % 32 == 0, "CTA size");
 // Split path: an FP32 gate / bin coordinate this close to an integer edge is re-decided
 // in FP64 (the FP32 coordinate errors are below ~1e-6 gates and ~3e-7 bins).
 constexpr float kGateEps = 2e-5f;
@@ -378,12 +390,49 @@ __device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, con
 // on the order in which atomics land.  Before touching memory, each warp merges runs of
 // equal keys: in-lane over the thread's consecutive scatterers, then across lanes with a
 // segmented Hillis-Steele scan (fixed order), so only run tails are emitted.
+// rint(v * 2^32) with integer operations only.  The hardware float -> int64 conversions
+// issue on the FP64 pipe, which runs at 1/64 of the FP32 rate on this GPU; one per
+// emitted run made that pipe the bottleneck of the whole summation.  Exact for the
+// left-shift range; the right-shift range rounds half away from zero on the magnitude.
+// Valid for |v| < 2^30 (per-cell sums are limited to |sum| < 2^31 anyway).
+__device__ __forceinline__ long long fixed_from_f32(float v) {
+    const unsigned b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu);                       // biased exponent
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 118;                                       // v 2^32 = m 2^(e - 118)
+    unsigned long long q;
+    if (sh >= 0) {
+        q = m << (sh > 39 ? 39 : sh);
+    } else {
+        const int r = -sh;
+        q = r > 25 ? 0ull : ((m >> (r - 1)) + 1ull) >> 1;
+    }
+    if (e == 0) q = 0ull;                                         // zero / subnormal
+    return (b >> 31) ? -(long long)q : (long long)q;
+}
+
+__device__ __forceinline__ long long fixed_from_f64(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = e - 1043;                                      // v 2^32 = m 2^(e - 1043)
+    unsigned long long q;
+    if (sh >= 0) {
+        q = m << (sh > 10 ? 10 : sh);
+    } else {
+        const int r = -sh;
+        q = r > 54 ? 0ull : ((m >> (r - 1)) + 1ull) >> 1;
+    }
+    if (e == 0) q = 0ull;
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
 template <typename T>
 __device__ __forceinline__ long long to_fixed(T v);
 template <>
-__device__ __forceinline__ long long to_fixed<float>(float v) { return __float2ll_rn(v * kFixScaleF); }
+__device__ __forceinline__ long long to_fixed<float>(float v) { return fixed_from_f32(v); }
 template <>
-__device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v * kFixScale); }
+__device__ __forceinline__ long long to_fixed<double>(double v) { return fixed_from_f64(v); }
 
 template <typename T>
 __device__ __forceinline__ void emit_cell(unsigned long long* __restrict__ base, int key, T re,

@@ -129,4 +129,6 @@ def test_autograd_regular_mode_matches_direct_calls(rsim):
     loss.backward()
     GY = 2.0 * Y.detach()
     gz, gs = rsim.direct_sum_backward(rd, pf, dev, 0, GY)
-    assert torch.equal(z.grad, gz) and torch.equal(s.grad, gs)
+    # torch forms d|Y|^2/dY in its own FP32 order: equal up to the last bits
+    torch.testing.assert_close(z.grad, gz, rtol=1e-5, atol=1e-5 * gz.abs().max().item())
+    torch.testing.assert_close(s.grad, gs, rtol=1e-5, atol=1e-5 * gs.abs().max().item())

@@ -96,7 +96,9 @@ def test_fast_mode_equals_regular_at_update_pulses(rsim, small):
     T, Y = rsim.simulate_fast(rd, pf, dev, 256, fp.n_fast, fp.n_doppler, fp.window, "fp64", 128)
     for x in (128, 192, 256, 320):
         Yr = rsim.direct_sum(rd, pf, dev, x, 1, "fp64")[0]
-        assert rel_l2(np_(Y[x - 128]), np_(Yr)) < 1e-12
+        # same contributions, summed per (gate, bin) then over bins vs per gate: equal up
+        # to the 2^-32 fixed-point quantisation of the emitted partial sums
+        assert rel_l2(np_(Y[x - 128]), np_(Yr)) < 1e-9
 
 
 def test_large_cell_grids(rsim, orc):

@@ -50,7 +50,9 @@ def test_direct_sum_parity_cfg0(rsim, orc, cfg0, precision):
     err = rel_l2(Y, Yref)
     assert err <= TOL[precision], err
     if precision == "fp64":
-        np.testing.assert_allclose(Y, Yref, rtol=0, atol=1e-9 * np.abs(Yref).max())
+        # element-wise: the oracle's phase of a ~7e7-cycle two-way range carries ~1e-8-cycle
+        # FP64 rounding (~1e-7 relative per contribution), the GPU's sums 2^-32 fixed point
+        np.testing.assert_allclose(Y, Yref, rtol=0, atol=1e-6 * np.abs(Yref).max())
     # end-to-end against the oracle's own decisions (reported; flips are rare here)
     Yor = orc.direct_sum(rd, pf, sc, 0, P)
     assert rel_l2(Y, Yor) <= 3 * TOL[precision]
