@@ -115,6 +115,7 @@ rsim::Model make_model(const rsim_radar* r, const rsim_platform* p, const rsim_s
     m.dt_f = (float)m.inv_prf;
     m.hdt_f = (float)(0.5 * m.inv_prf);
     for (int i = 0; i < 3; ++i) m.ep[i] = (float)(p->v[i] * m.inv_prf);
+    m.inv_nd = (float)(1.0 / (double)n_doppler);
     return m;
 }
 

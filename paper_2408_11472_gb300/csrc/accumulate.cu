@@ -65,7 +65,7 @@ __device__ __forceinline__ void chunk_ref(const Scat& sc, int64_t chunk0, float&
 }
 
 __device__ __forceinline__ void items_split(const Model& m, const Raw& r, float cx, float cy,
-                                            ItemF (&it)[kItems]) {
+                                            int64_t base, int64_t n, ItemF (&it)[kItems]) {
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
         it[q].lx0 = r.x[q] - cx;
@@ -75,6 +75,10 @@ __device__ __forceinline__ void items_split(const Model& m, const Raw& r, float 
         it[q].vy = r.vy[q];
         it[q].vz = r.vz[q];
         it[q].amp0 = sqrtf(r.s[q] * (float)m.area);
+        const float epv = fmaf(m.ep[0], r.vx[q], fmaf(m.ep[1], r.vy[q], m.ep[2] * r.vz[q]));
+        const float vv = fmaf(r.vx[q], r.vx[q], fmaf(r.vy[q], r.vy[q], r.vz[q] * r.vz[q]));
+        it[q].c1 = m.hdt_f * fmaf(-m.dt_f, vv, epv);
+        it[q].ok = (base + q < n) ? 1 : 0;
     }
 }
 
@@ -102,6 +106,8 @@ template <bool DOPPLER>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
     Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
     __shared__ SplitConst tab[kTab];
+    __shared__ Fp64Const tab64[kTab];
+    constexpr unsigned kFull = 0xffffffffu;
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
     const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
     float cx, cy;
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
     {
         Raw r;
         load_raw(sc, base, r);
-        items_split(m, r, cx, cy, it);
+        items_split(m, r, cx, cy, base, sc.n, it);
     }
     const int cells = m.n_gates * m.n_doppler;
     const int s_begin = blockIdx.y * sch.samples_per_group;
@@ -118,17 +124,36 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
     for (int sb = s_begin; sb < s_end; sb += kTab) {
         const int nb = min(kTab, s_end - sb);
         __syncthreads();
-        if (threadIdx.x < nb) tab[threadIdx.x] = make_split_const(m, sample_pulse(sch, sb + threadIdx.x), cx, cy);
+        if (threadIdx.x < nb) {
+            const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
+            tab[threadIdx.x] = make_split_const(m, pulse, cx, cy);
+            tab64[threadIdx.x] = make_fp64_const(m, pulse);
+        }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
             const int s = sb + j;
-            const int64_t pulse = sample_pulse(sch, s);
-            const SplitConst& k = tab[j];
+            const SampleF k = load_sample(tab[j]);
             int key[kItems];
             float re[kItems], im[kItems];
+            int fl = 0;
 #pragma unroll
-            for (int q = 0; q < kItems; ++q)
-                key[q] = eval_split<DOPPLER, false>(m, k, it[q], sc, base + q, pulse, re[q], im[q], nullptr);
+            for (int q = 0; q < kItems; ++q) {
+                int f;
+                key[q] = eval_split<DOPPLER, false, false>(m, k, it[q], re[q], im[q], f);
+                fl |= f << (2 * q);
+            }
+            // rare: items near a cell edge or far off nadir, re-evaluated exactly
+            if (__any_sync(kFull, fl != 0)) {
+#pragma unroll
+                for (int q = 0; q < kItems; ++q) {
+                    if ((fl >> (2 * q)) & 3) {
+                        int f;
+                        key[q] = eval_split<DOPPLER, true, false>(
+                            m, k, it[q], re[q], im[q], f, &tab64[j], __ldg(sc.x + base + q),
+                            __ldg(sc.y + base + q));
+                    }
+                }
+            }
             warp_reduce_emit<float, kItems>(key, re, im, ws + (int64_t)s * cells * 2);
         }
     }
@@ -191,13 +216,16 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
         float cx, cy;
         chunk_ref(sc, chunk0, cx, cy);
         ItemF it[kItems];
-        items_split(m, r, cx, cy, it);
-        const SplitConst k = make_split_const(m, pulse, cx, cy);
+        items_split(m, r, cx, cy, base, sc.n, it);
+        const SampleF k = load_sample(make_split_const(m, pulse, cx, cy));
+        const Fp64Const k64 = make_fp64_const(m, pulse);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) {
             float re, im;
-            key[q] = doppler ? eval_split<true, false>(m, k, it[q], sc, base + q, pulse, re, im, nullptr, &g[q], &gc[q], &bc[q])
-                             : eval_split<false, false>(m, k, it[q], sc, base + q, pulse, re, im, nullptr, &g[q], &gc[q], &bc[q]);
+            int f;
+            key[q] = doppler
+                ? eval_split<true, true, false>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q])
+                : eval_split<false, true, false>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q]);
         }
     } else {
         ItemD it[kItems];
@@ -228,18 +256,19 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     Model m, Schedule sch, Scat sc, const float2* __restrict__ G, float* __restrict__ grad_z,
     float* __restrict__ grad_nrcs) {
     __shared__ SplitConst tab[kTab];
+    __shared__ Fp64Const tab64[kTab];
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
     const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
     float cx, cy;
     chunk_ref(sc, chunk0, cx, cy);
     ItemF it[kItems];
-    float sig[kItems];
+    float sig[kItems], xo[kItems], yo[kItems];
     {
         Raw r;
         load_raw(sc, base, r);
-        items_split(m, r, cx, cy, it);
+        items_split(m, r, cx, cy, base, sc.n, it);
 #pragma unroll
-        for (int q = 0; q < kItems; ++q) sig[q] = r.s[q];
+        for (int q = 0; q < kItems; ++q) { sig[q] = r.s[q]; xo[q] = r.x[q]; yo[q] = r.y[q]; }
     }
     float gz[kItems], gs[kItems];
 #pragma unroll
@@ -248,17 +277,22 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     for (int sb = 0; sb < sch.n_samples; sb += kTab) {
         const int nb = min(kTab, sch.n_samples - sb);
         __syncthreads();
-        if (threadIdx.x < nb) tab[threadIdx.x] = make_split_const(m, sample_pulse(sch, sb + threadIdx.x), cx, cy);
+        if (threadIdx.x < nb) {
+            const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
+            tab[threadIdx.x] = make_split_const(m, pulse, cx, cy);
+            tab64[threadIdx.x] = make_fp64_const(m, pulse);
+        }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
             const int s = sb + j;
-            const int64_t pulse = sample_pulse(sch, s);
-            const SplitConst& k = tab[j];
+            const SampleF k = load_sample(tab[j]);
 #pragma unroll
             for (int q = 0; q < kItems; ++q) {
                 float re, im;
+                int f;
                 DerivF dv;
-                const int key = eval_split<DOPPLER, true>(m, k, it[q], sc, base + q, pulse, re, im, &dv);
+                const int key = eval_split<DOPPLER, true, true>(m, k, it[q], re, im, f, &tab64[j],
+                                                                 xo[q], yo[q], &dv);
                 if (key >= 0) {
                     const float2 g = __ldg(G + (int64_t)s * cells + key);
                     const float cr = fmaf(g.x, re, g.y * im);   // Re(conj(G) C)

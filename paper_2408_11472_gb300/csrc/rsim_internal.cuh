@@ -27,14 +27,17 @@ constexpr int kThreads = RSIM_THREADS;        // summation CTA size
 constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (1, 2, 4, 8)
 constexpr int kMinBlocks = RSIM_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
 constexpr int kChunk = kThreads * kItems;     // scatterers sharing one FP64 reference point
-constexpr int kTab = 64;                      // samples per block of reference constants
+constexpr int kTab = 128;                     // samples per block of reference constants
 constexpr double kFixScale = 4294967296.0;    // fixed point: value = q * 2^-32
 static_assert(kItems == 1 || kItems == 2 || kItems == 4 || kItems == 8, "items per thread");
 static_assert(kThreads >= kTab && kThreads % 32 == 0, "CTA size");
 // Split path: an FP32 gate / bin coordinate this close to an integer edge is re-decided
-// in FP64 (the FP32 coordinate errors are below ~1e-6 gates and ~3e-7 bins).
+// in FP64.  The FP32 coordinate error grows with the coordinate's distance from the
+// CTA reference point (about 3e-7 of it) on top of a few 1e-7 absolute, so the band is
+// base + 4e-7 |coordinate| -- ten times the worst error seen.
 constexpr float kGateEps = 2e-5f;
 constexpr float kBinEps = 5e-6f;
+constexpr float kEpsSlope = 4e-7f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kInvLn2F = 1.44269504088896340736f;
 
@@ -52,7 +55,7 @@ struct Model {
     int n_gates;
     int n_doppler;          // 1 in regular mode
     // FP32 copies for the split path
-    float inv_gw_f, beam_k_f, chi_hi, chi_lo, dt_f, hdt_f, ep[3];
+    float inv_gw_f, beam_k_f, chi_hi, chi_lo, dt_f, hdt_f, ep[3], inv_nd;
 };
 
 // Sample schedule: sample s is pulse pulse_base + s * pulse_stride.
@@ -161,27 +164,37 @@ __device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, int64_t pul
 }
 
 // ---------------------------------------------------------------------------------------
-// Per (reference point c, sample) constants of the split path, computed in FP64 once
-// per CTA and sample and rounded to FP32.  D = P(t) - origin - c, R_c = |D|.
-struct SplitConst {
-    float t;                 // seconds
-    float Dx, Dy, Dz;        // D
-    float ux, uy, uz;        // D / R_c
-    float h;                 // 1 / (2 R_c)
-    float invRc;             // 1 / R_c
-    float gfrac;             // frac of the gate coordinate of c
-    int gint;                // floor of the gate coordinate of c
-    float psic;              // 2 R_c / lambda - rint(.)   [cycles]
-    float kappa;             // (r_ref / R_c)^2
-    float invDz, invDz2;     // 1 / D_z, 1 / D_z^2
-    float Mx, My, Mz;        // D + e_p / 2, e_p = platform displacement over one PRI
-    float K0hi, K0lo;        // (D + e_p/2) . e_p split into two floats
-    float pad;
+// Per (reference point c, sample) constants of the split path, computed in FP64 once per
+// CTA and sample, rounded to FP32 and packed for 128-bit shared-memory loads.
+// D = P(t) - origin - c, R_c = |D|, e_p = platform displacement over one PRI.
+struct __align__(16) SplitConst {
+    float4 a;   // t, D_x, D_y, D_z
+    float4 b;   // D / R_c (x, y, z), 1 / (2 R_c)
+    float4 c;   // 1 / R_c, frac of the gate coordinate of c, 2 R_c / lambda - rint(.), (r_ref/R_c)^2
+    float4 d;   // 1 / D_z^2, M = D + e_p / 2 (x, y, z)
+    float4 e;   // K0 = M . e_p as hi + lo, floor of the gate coordinate of c (int bits), -n_doppler 2/(lambda R_c)
 };
+
+// Register copy of one table entry.
+struct SampleF {
+    float t, Dx, Dy, Dz, ux, uy, uz, h, invRc, gfrac, psic, kappa, invDz2, Mx, My, Mz, K0hi, K0lo,
+        kbin;
+    int gint;
+};
+
+__device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
+    const float4 a = s.a, b = s.b, c = s.c, d = s.d, e = s.e;
+    SampleF k;
+    k.t = a.x; k.Dx = a.y; k.Dy = a.z; k.Dz = a.w;
+    k.ux = b.x; k.uy = b.y; k.uz = b.z; k.h = b.w;
+    k.invRc = c.x; k.gfrac = c.y; k.psic = c.z; k.kappa = c.w;
+    k.invDz2 = d.x; k.Mx = d.y; k.My = d.z; k.Mz = d.w;
+    k.K0hi = e.x; k.K0lo = e.y; k.gint = __float_as_int(e.z); k.kbin = e.w;
+    return k;
+}
 
 __device__ __forceinline__ SplitConst make_split_const(const Model& m, int64_t pulse, float cx,
                                                        float cy) {
-    SplitConst k;
     const double t = (double)pulse * m.inv_prf;
     const double Dx = platform_coord(m, 0, t) - (double)cx;
     const double Dy = platform_coord(m, 1, t) - (double)cy;
@@ -197,43 +210,24 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, int64_t p
     const double epx = m.v[0] * dt, epy = m.v[1] * dt, epz = m.v[2] * dt;
     const double Mx = Dx + 0.5 * epx, My = Dy + 0.5 * epy, Mz = Dz + 0.5 * epz;
     const double K0 = Mx * epx + My * epy + Mz * epz;
-    k.t = (float)t;
-    k.Dx = (float)Dx; k.Dy = (float)Dy; k.Dz = (float)Dz;
-    k.ux = (float)(Dx * inv); k.uy = (float)(Dy * inv); k.uz = (float)(Dz * inv);
-    k.h = (float)(0.5 * inv);
-    k.invRc = (float)inv;
-    k.gint = (int)fmax(fmin(Gi, 1.0e9), -1.0e9);
-    k.gfrac = (float)(G - Gi);
-    k.psic = (float)psi;
-    k.kappa = (float)((rref * inv) * (rref * inv));
-    k.invDz = (float)(1.0 / Dz);
-    k.invDz2 = (float)(1.0 / (Dz * Dz));
-    k.Mx = (float)Mx; k.My = (float)My; k.Mz = (float)Mz;
-    k.K0hi = (float)K0;
-    k.K0lo = (float)(K0 - (double)k.K0hi);
-    k.pad = 0.f;
+    const float K0hi = (float)K0;
+    SplitConst k;
+    k.a = make_float4((float)t, (float)Dx, (float)Dy, (float)Dz);
+    k.b = make_float4((float)(Dx * inv), (float)(Dy * inv), (float)(Dz * inv), (float)(0.5 * inv));
+    k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, (float)((rref * inv) * (rref * inv)));
+    k.d = make_float4((float)(1.0 / (Dz * Dz)), (float)Mx, (float)My, (float)Mz);
+    k.e = make_float4(K0hi, (float)(K0 - (double)K0hi),
+                      __int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)),
+                      (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
     return k;
 }
 
-// Squared off-nadir angle from q^2 = (rho / d_z)^2: atan(q)^2 as a series for small q.
-__device__ __forceinline__ float theta2_f(float q2, float rho2, float dz) {
-    if (q2 < 1e-2f) return q2 * fmaf(q2, fmaf(q2, 23.0f / 45.0f, -2.0f / 3.0f), 1.0f);
-    const float th = atan2f(sqrtf(rho2), dz);
-    return th * th;
-}
-
-__device__ __forceinline__ double theta2_d(double rho2, double dz) {
-    const double q2 = rho2 / (dz * dz);
-    if (q2 < 1e-3) {
-        return q2 * fma(q2, fma(q2, fma(q2, -44.0 / 105.0, 23.0 / 45.0), -2.0 / 3.0), 1.0);
-    }
-    const double th = atan2(sqrt(rho2), dz);
-    return th * th;
-}
-
 // Scatterer registers of the split path (positions relative to the CTA reference point).
+// c1 = dt (e_p . v) / 2 - dt^2 |v|^2 / 2 is the part of the pulse-pair range change that
+// depends on the scatterer alone.
 struct ItemF {
-    float lx0, ly0, z, vx, vy, vz, amp0;
+    float lx0, ly0, z, vx, vy, vz, amp0, c1;
+    int ok;  // 1 for a real scatterer, 0 for padding past the end of the set
 };
 
 // Quantities the adjoint needs besides C.
@@ -242,14 +236,39 @@ struct DerivF {
     float dphi;  // d arg C / dz  [rad / m]
 };
 
-// Split-path evaluation of one scatterer at the sample described by k.  Returns the
-// cell key g * n_doppler + bin, or -1 when out of the range window or not a scatterer.
-// gc_out / bc_out (optional) receive the pre-floor coordinates behind the decision.
-template <bool DOPPLER, bool DERIV>
-__device__ __forceinline__ int eval_split(const Model& m, const SplitConst& k, const ItemF& it,
-                                          const Scat& sc, int64_t n, int64_t pulse, float& re,
-                                          float& im, DerivF* dv, int* g_out = nullptr,
-                                          double* gc_out = nullptr, double* bc_out = nullptr) {
+// Result flags of the fast evaluation.
+constexpr int kFlagRefine = 1;  // gate or bin coordinate within rounding of a cell edge
+constexpr int kFlagWide = 2;    // off-nadir angle beyond the series' range (q^2 >= 0.01)
+
+// FP64 re-decision of the gate and bin of one scatterer (kept out of line so that none of
+// its FP64 work is hoisted into the common path).
+static __device__ __noinline__ void refine_fp64(const Model& m, const Fp64Const& k64, double x, double y,
+                                         double z, double vx, double vy, double vz, bool doppler,
+                                         int* g, int* kb, double* gc, double* bc) {
+    const GeomD gd = geom_fp64(k64.t, k64.Px, k64.Py, k64.Pz, k64.rref, x, y, z, vx, vy, vz);
+    *gc = fma(gd.dR, m.inv_gw, m.half_gates);
+    *g = clamp_floor(*gc);
+    *kb = 0;
+    *bc = 0.5;
+    if (doppler) {
+        *bc = bin_coord_fp64(m, gd, vx, vy, vz);
+        *kb = clamp_floor(*bc) & (m.n_doppler - 1);
+    }
+}
+
+// Split-path evaluation of one scatterer at one sample.  Returns the cell key
+// g * n_doppler + bin, or -1 when out of the range window or not a scatterer.
+// GENERAL = false: straight-line code; items that need the FP64 re-decision or the exact
+//   off-nadir angle are only flagged (the caller re-evaluates them with GENERAL = true).
+// GENERAL = true: takes those branches (tab64 and the scatterer's original x, y needed).
+// For unflagged items both give bit-identical results.
+template <bool DOPPLER, bool GENERAL, bool DERIV>
+__device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, const ItemF& it,
+                                          float& re, float& im, int& flags,
+                                          const Fp64Const* k64 = nullptr, float x_orig = 0.f,
+                                          float y_orig = 0.f, DerivF* dv = nullptr,
+                                          int* g_out = nullptr, double* gc_out = nullptr,
+                                          double* bc_out = nullptr) {
     const float lx = fmaf(it.vx, k.t, it.lx0);
     const float ly = fmaf(it.vy, k.t, it.ly0);
     const float lz = fmaf(it.vz, k.t, it.z);
@@ -258,19 +277,30 @@ __device__ __forceinline__ int eval_split(const Model& m, const SplitConst& k, c
     const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
     const float dR0 = fmaf(ll, k.h, -ul);
     const float dR = dR0 * fmaf(-dR0, k.h, 1.0f);
+    // gate
     const float gcf = fmaf(dR, m.inv_gw_f, k.gfrac);
-    int g = k.gint + (int)floorf(gcf);
-    bool refine = fabsf(gcf - rintf(gcf)) < kGateEps;
-    // antenna: theta^2 with 1 / d_z^2 ~ (1 / D_z^2)(1 + 2 l_z / D_z)
+    const float gfl = floorf(gcf);
+    const float gfr = gcf - gfl;
+    int g = k.gint + (int)gfl;
+    const float eg = fmaf(fabsf(gcf), kEpsSlope, kGateEps);
+    int fl = (gfr < eg || gfr > 1.0f - eg) ? kFlagRefine : 0;
+    // antenna: q = rho / d_z, theta^2 = atan(q)^2 (series for q^2 < 0.01)
     const float dx = k.Dx - lx, dy = k.Dy - ly;
     const float rho2 = fmaf(dx, dx, dy * dy);
-    const float q2 = rho2 * (k.invDz2 * fmaf(2.0f * lz, k.invDz, 1.0f));
-    const float th2 = theta2_f(q2, rho2, k.Dz - lz);
+    const float q2 = rho2 * k.invDz2;
+    float th2 = q2 * fmaf(q2, fmaf(q2, 23.0f / 45.0f, -2.0f / 3.0f), 1.0f);
+    if (q2 >= 1e-2f) {
+        fl |= kFlagWide;
+        if (GENERAL) {
+            const float th = atan2f(sqrtf(rho2), k.Dz - lz);
+            th2 = th * th;
+        }
+    }
     // |C| = sqrt(sigma A) 2^(-2 theta^2 / theta_b^2) (r_ref / R_c)^2 (1 + dR / R_c)^-2
     const float xr = dR * k.invRc;
     const float E = fmaf(th2, m.beam_k_f, xr * fmaf(xr, kInvLn2F, -2.0f * kInvLn2F));
-    const float a = it.amp0 * k.kappa * ex2_approx(E);
-    // phase in cycles: psi_c + dR * 2 / lambda (2/lambda as hi + lo, product error-free)
+    const float a = (it.amp0 * k.kappa) * ex2_approx(E);
+    // phase in cycles: psi_c + dR 2/lambda (2/lambda as hi + lo, the product error-free)
     const float p = dR * m.chi_hi;
     const float perr = fmaf(dR, m.chi_hi, -p);
     float f = (p - rintf(p)) + (k.psic + fmaf(dR, m.chi_lo, perr));
@@ -282,29 +312,28 @@ __device__ __forceinline__ int eval_split(const Model& m, const SplitConst& k, c
     int kb = 0;
     float bc = 0.5f;
     if (DOPPLER) {
-        // D = R(t + dt) - R(t) = 2 (d + e/2).e / (R + R'),  d = D - l,  e = e_p - v dt,
-        // (d + e/2).e = K0 - dt (M.v) - (l + v dt / 2).e
+        // pulse-pair range change D = 2 (d + e/2).e / (R + R'), d = D - l, e = e_p - v dt:
+        // (d + e/2).e = K0 - dt (M.v) - c1 - l.e ;  bin coordinate -n_doppler 2 D / lambda + 1/2
         const float ex = fmaf(-it.vx, m.dt_f, m.ep[0]);
         const float ey = fmaf(-it.vy, m.dt_f, m.ep[1]);
         const float ez = fmaf(-it.vz, m.dt_f, m.ep[2]);
-        const float mx = fmaf(it.vx, m.hdt_f, lx);
-        const float my = fmaf(it.vy, m.hdt_f, ly);
-        const float mz = fmaf(it.vz, m.hdt_f, lz);
         const float Mv = fmaf(k.Mx, it.vx, fmaf(k.My, it.vy, k.Mz * it.vz));
-        const float me = fmaf(mx, ex, fmaf(my, ey, mz * ez));
-        const float hn2 = (fmaf(-m.dt_f, Mv, k.K0hi) - me) + k.K0lo;
-        const float D = hn2 * k.invRc * fmaf(-dR, k.invRc, 1.0f);
-        float nu = -D * m.chi_hi;
-        nu -= rintf(nu);
-        bc = fmaf(nu, (float)m.n_doppler, 0.5f);
-        kb = ((int)floorf(bc)) & (m.n_doppler - 1);
-        refine |= fabsf(bc - rintf(bc)) < kBinEps;
+        const float le = fmaf(lx, ex, fmaf(ly, ey, lz * ez));
+        const float hn2 = ((fmaf(-m.dt_f, Mv, k.K0hi) - le) - it.c1) + k.K0lo;
+        float b = (hn2 * k.kbin) * (1.0f - xr);     // nu n_doppler, unwrapped
+        b = fmaf(-(float)m.n_doppler, rintf(b * m.inv_nd), b);
+        bc = b + 0.5f;
+        const float bfl = floorf(bc);
+        const float bfr = bc - bfl;
+        kb = ((int)bfl) & (m.n_doppler - 1);
+        const float eb = fmaf(fabsf(b), kEpsSlope, kBinEps);
+        if (bfr < eb || bfr > 1.0f - eb) fl |= kFlagRefine;
     }
     if (DERIV) {
         // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
         // d ln a / dz = 2 d_z / R^2 - 4 ln2 theta rho / (theta_b^2 R^2), d phi / dz = 4 pi d_z / (lambda R)
         const float dz = k.Dz - lz;
-        const float invR = k.invRc * fmaf(-dR, k.invRc, 1.0f);
+        const float invR = k.invRc * (1.0f - xr);
         const float invR2 = invR * invR;
         float rho_theta;
         if (q2 < 1e-2f) {
@@ -317,18 +346,28 @@ __device__ __forceinline__ int eval_split(const Model& m, const SplitConst& k, c
         dv->dphi = kTwoPiF * (m.chi_hi + m.chi_lo) * dz * invR;  // chi = 2 / lambda
     }
     double gcd = (double)k.gint + (double)gcf, bcd = (double)bc;
-    if (refine && n < sc.n) {
+    if (GENERAL && (fl & kFlagRefine) && it.ok) {
         int g2, kb2;
-        decide_fp64(m, (double)pulse * m.inv_prf, (double)__ldg(sc.x + n), (double)__ldg(sc.y + n),
-                    (double)it.z, (double)it.vx, (double)it.vy, (double)it.vz, DOPPLER, g2, kb2,
-                    gcd, bcd);
+        refine_fp64(m, *k64, (double)x_orig, (double)y_orig, (double)it.z, (double)it.vx,
+                    (double)it.vy, (double)it.vz, DOPPLER, &g2, &kb2, &gcd, &bcd);
         g = g2;
         kb = kb2;
     }
+    flags = fl;
     if (g_out) *g_out = g;
     if (gc_out) *gc_out = gcd;
     if (bc_out) *bc_out = bcd;
-    return (n < sc.n && g >= 0 && g < m.n_gates) ? g * m.n_doppler + kb : -1;
+    return (it.ok && g >= 0 && g < m.n_gates) ? g * m.n_doppler + kb : -1;
+}
+
+// Squared off-nadir angle atan(rho / d_z)^2 in FP64 (series for small angles).
+__device__ __forceinline__ double theta2_d(double rho2, double dz) {
+    const double q2 = rho2 / (dz * dz);
+    if (q2 < 1e-3) {
+        return q2 * fma(q2, fma(q2, fma(q2, -44.0 / 105.0, 23.0 / 45.0), -2.0 / 3.0), 1.0);
+    }
+    const double th = atan2(sqrt(rho2), dz);
+    return th * th;
 }
 
 // Scatterer registers of the FP64 path (positions relative to the origin).
