@@ -148,9 +148,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
                 for (int q = 0; q < kItems; ++q) {
                     if ((fl >> (2 * q)) & 3) {
                         int f;
+                        const bool in = it[q].ok != 0;  // padding items read nothing
                         key[q] = eval_split<DOPPLER, true, false>(
-                            m, k, it[q], re[q], im[q], f, &tab64[j], __ldg(sc.x + base + q),
-                            __ldg(sc.y + base + q));
+                            m, k, it[q], re[q], im[q], f, &tab64[j],
+                            in ? __ldg(sc.x + base + q) : 0.0f, in ? __ldg(sc.y + base + q) : 0.0f);
                     }
                 }
             }

@@ -283,7 +283,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float gfr = gcf - gfl;
     int g = k.gint + (int)gfl;
     const float eg = fmaf(fabsf(gcf), kEpsSlope, kGateEps);
-    int fl = (gfr < eg || gfr > 1.0f - eg) ? kFlagRefine : 0;
+    int fl = (fabsf(gfr - 0.5f) > 0.5f - eg) ? kFlagRefine : 0;
     // antenna: q = rho / d_z, theta^2 = atan(q)^2 (series for q^2 < 0.01)
     const float dx = k.Dx - lx, dy = k.Dy - ly;
     const float rho2 = fmaf(dx, dx, dy * dy);
@@ -327,7 +327,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         const float bfr = bc - bfl;
         kb = ((int)bfl) & (m.n_doppler - 1);
         const float eb = fmaf(fabsf(b), kEpsSlope, kBinEps);
-        if (bfr < eb || bfr > 1.0f - eb) fl |= kFlagRefine;
+        if (fabsf(bfr - 0.5f) > 0.5f - eb) fl |= kFlagRefine;
     }
     if (DERIV) {
         // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
@@ -357,7 +357,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     if (g_out) *g_out = g;
     if (gc_out) *gc_out = gcd;
     if (bc_out) *bc_out = bcd;
-    return (it.ok && g >= 0 && g < m.n_gates) ? g * m.n_doppler + kb : -1;
+    // padding items (past the end of the set) carry zero amplitude: harmless in any cell
+    return ((unsigned)g < (unsigned)m.n_gates) ? g * m.n_doppler + kb : -1;
 }
 
 // Squared off-nadir angle atan(rho / d_z)^2 in FP64 (series for small angles).
@@ -429,27 +430,21 @@ __device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, con
 // on the order in which atomics land.  Before touching memory, each warp merges runs of
 // equal keys: in-lane over the thread's consecutive scatterers, then across lanes with a
 // segmented Hillis-Steele scan (fixed order), so only run tails are emitted.
-// rint(v * 2^32) with integer operations only.  The hardware float -> int64 conversions
-// issue on the FP64 pipe, which runs at 1/64 of the FP32 rate on this GPU; one per
-// emitted run made that pipe the bottleneck of the whole summation.  Exact for the
-// left-shift range; the right-shift range rounds half away from zero on the magnitude.
-// Valid for |v| < 2^30 (per-cell sums are limited to |sum| < 2^31 anyway).
+// v * 2^32 as a 64-bit integer (2^-31 resolution, |v| < 2^30), branch-free.  The hardware
+// float -> int64 conversion issues on the FP64 pipe, which runs at 1/64 of the FP32 rate
+// on this GPU; one per emitted run made that pipe the bottleneck of the whole summation.
+// Here v = t + r with t = trunc(v) and |r| < 1 (both exact in FP32), and only 32-bit
+// conversions are used.
 __device__ __forceinline__ long long fixed_from_f32(float v) {
-    const unsigned b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xffu);                       // biased exponent
-    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
-    const int sh = e - 118;                                       // v 2^32 = m 2^(e - 118)
-    unsigned long long q;
-    if (sh >= 0) {
-        q = m << (sh > 39 ? 39 : sh);
-    } else {
-        const int r = -sh;
-        q = r > 25 ? 0ull : ((m >> (r - 1)) + 1ull) >> 1;
-    }
-    if (e == 0) q = 0ull;                                         // zero / subnormal
-    return (b >> 31) ? -(long long)q : (long long)q;
+    const float t = truncf(v);
+    const float r = v - t;
+    const long long hi = (long long)__float2int_rz(t);
+    const long long lo = (long long)__float2int_rn(r * 2147483648.0f);
+    return (long long)((unsigned long long)hi << 32) + lo * 2;
 }
 
+// v * 2^32 rounded, with integer operations only (the FP64 path's values carry more bits
+// than two FP32 conversions keep).  Valid for |v| < 2^30.
 __device__ __forceinline__ long long fixed_from_f64(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ffull);
@@ -487,31 +482,28 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
                                                  unsigned long long* __restrict__ base) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    T rr = re[0], ri = im[0];
-    T first_r = T(0), first_i = T(0);
-    bool split = false;  // the lane holds more than one run
+    // in-lane inclusive run sums; bit q of tails: a run ends at item q
+    T sr[J], si[J];
+    sr[0] = re[0];
+    si[0] = im[0];
+    unsigned tails = 0u;
+    int first_end = J - 1;
 #pragma unroll
     for (int q = 1; q < J; ++q) {
-        if (key[q] != key[q - 1]) {
-            if (!split) {
-                first_r = rr;
-                first_i = ri;
-                split = true;
-            } else if (key[q - 1] >= 0) {
-                emit_cell(base, key[q - 1], rr, ri);  // interior run: complete
-            }
-            rr = re[q];
-            ri = im[q];
-        } else {
-            rr += re[q];
-            ri += im[q];
+        const bool same = key[q] == key[q - 1];
+        sr[q] = same ? sr[q - 1] + re[q] : re[q];
+        si[q] = same ? si[q - 1] + im[q] : im[q];
+        if (!same) {
+            tails |= 1u << (q - 1);
+            first_end = min(first_end, q - 1);
         }
     }
-    const int kfirst = key[0], klast = key[J - 1];
-    const int prev_last = __shfl_up_sync(kFull, klast, 1);
-    const bool link = lane > 0 && prev_last == kfirst;  // first run continues lane-1's last run
-    T cr = rr, ci = ri;
-    int head = (split || !link) ? 1 : 0;
+    const bool uniform = tails == 0u;
+    const int prev_last = __shfl_up_sync(kFull, key[J - 1], 1);
+    const bool link = lane > 0 && prev_last == key[0];  // first run continues lane-1's last run
+    // segmented inclusive scan (fixed order) of the lanes' last-run sums
+    T cr = sr[J - 1], ci = si[J - 1];
+    int head = (!uniform || !link) ? 1 : 0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const T ur = __shfl_up_sync(kFull, cr, d);
@@ -524,16 +516,37 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
         }
     }
     T in_r = __shfl_up_sync(kFull, cr, 1), in_i = __shfl_up_sync(kFull, ci, 1);
+    if (!link) {
+        in_r = T(0);
+        in_i = T(0);
+    }
     const int next_link = __shfl_down_sync(kFull, link ? 1 : 0, 1);
-    const bool tail = (lane == 31) || !next_link;
-    if (split) {
-        if (kfirst >= 0) {
-            if (!link) { in_r = T(0); in_i = T(0); }
-            emit_cell(base, kfirst, in_r + first_r, in_i + first_i);
+    if (lane == 31 || !next_link) tails |= 1u << (J - 1);
+    // runs of out-of-window items (key -1) are not emitted
+#pragma unroll
+    for (int q = 0; q < J; ++q)
+        if (key[q] < 0) tails &= ~(1u << q);
+    // emit the pending run tails, one per lane per round
+    while (__any_sync(kFull, tails != 0u)) {
+        if (tails) {
+            const int q = __ffs(tails) - 1;
+            tails &= tails - 1u;
+            int k = key[0];
+            T vr = sr[0], vi = si[0];
+#pragma unroll
+            for (int j = 1; j < J; ++j) {
+                if (q == j) {
+                    k = key[j];
+                    vr = sr[j];
+                    vi = si[j];
+                }
+            }
+            if (q <= first_end) {  // the lane's first run: add the carry from the left
+                vr += in_r;
+                vi += in_i;
+            }
+            emit_cell(base, k, vr, vi);
         }
-        if (tail && klast >= 0) emit_cell(base, klast, rr, ri);
-    } else if (tail && klast >= 0) {
-        emit_cell(base, klast, cr, ci);
     }
 }
 
