@@ -116,6 +116,10 @@ rsim::Model make_model(const rsim_radar* r, const rsim_platform* p, const rsim_s
     m.hdt_f = (float)(0.5 * m.inv_prf);
     for (int i = 0; i < 3; ++i) m.ep[i] = (float)(p->v[i] * m.inv_prf);
     m.inv_nd = (float)(1.0 / (double)n_doppler);
+    m.s1 = (float)(-2.0 / (3.0 * m.beam_k));
+    m.s2 = (float)(23.0 / (45.0 * m.beam_k * m.beam_k));
+    m.qb_wide = (float)(1e-2 * m.beam_k);
+    m.inv_beam_k = (float)(1.0 / m.beam_k);
     return m;
 }
 

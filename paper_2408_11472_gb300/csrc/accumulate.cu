@@ -77,7 +77,7 @@ __device__ __forceinline__ void items_split(const Model& m, const Raw& r, float 
         it[q].amp0 = sqrtf(r.s[q] * (float)m.area);
         const float epv = fmaf(m.ep[0], r.vx[q], fmaf(m.ep[1], r.vy[q], m.ep[2] * r.vz[q]));
         const float vv = fmaf(r.vx[q], r.vx[q], fmaf(r.vy[q], r.vy[q], r.vz[q] * r.vz[q]));
-        it[q].c1 = m.hdt_f * fmaf(-m.dt_f, vv, epv);
+        it[q].c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
         it[q].ok = (base + q < n) ? 1 : 0;
     }
 }

@@ -56,6 +56,8 @@ struct Model {
     int n_doppler;          // 1 in regular mode
     // FP32 copies for the split path
     float inv_gw_f, beam_k_f, chi_hi, chi_lo, dt_f, hdt_f, ep[3], inv_nd;
+    // off-nadir series in qb = beam_k rho^2 / D_z^2: beam_k atan(q)^2 = qb (1 + qb (s1 + qb s2))
+    float s1, s2, qb_wide, inv_beam_k;
 };
 
 // Sample schedule: sample s is pulse pulse_base + s * pulse_stride.
@@ -170,26 +172,25 @@ __device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, int64_t pul
 struct __align__(16) SplitConst {
     float4 a;   // t, D_x, D_y, D_z
     float4 b;   // D / R_c (x, y, z), 1 / (2 R_c)
-    float4 c;   // 1 / R_c, frac of the gate coordinate of c, 2 R_c / lambda - rint(.), (r_ref/R_c)^2
-    float4 d;   // 1 / D_z^2, M = D + e_p / 2 (x, y, z)
-    float4 e;   // K0 = M . e_p as hi + lo, floor of the gate coordinate of c (int bits), -n_doppler 2/(lambda R_c)
+    float4 c;   // 1 / R_c, frac of the gate coordinate of c, 2 R_c / lambda - rint(.), log2 (r_ref/R_c)^2
+    float4 d;   // beam_k / D_z^2, K0 = M . e_p as hi + lo (M = D + e_p/2), -n_doppler 2 / (lambda R_c)
+    float4 e;   // floor of the gate coordinate of c (int bits), unused x 3
 };
 
 // Register copy of one table entry.
 struct SampleF {
-    float t, Dx, Dy, Dz, ux, uy, uz, h, invRc, gfrac, psic, kappa, invDz2, Mx, My, Mz, K0hi, K0lo,
-        kbin;
+    float t, Dx, Dy, Dz, ux, uy, uz, h, invRc, gfrac, psic, l2kappa, kq, K0hi, K0lo, kbin;
     int gint;
 };
 
 __device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
-    const float4 a = s.a, b = s.b, c = s.c, d = s.d, e = s.e;
+    const float4 a = s.a, b = s.b, c = s.c, d = s.d;
     SampleF k;
     k.t = a.x; k.Dx = a.y; k.Dy = a.z; k.Dz = a.w;
     k.ux = b.x; k.uy = b.y; k.uz = b.z; k.h = b.w;
-    k.invRc = c.x; k.gfrac = c.y; k.psic = c.z; k.kappa = c.w;
-    k.invDz2 = d.x; k.Mx = d.y; k.My = d.z; k.Mz = d.w;
-    k.K0hi = e.x; k.K0lo = e.y; k.gint = __float_as_int(e.z); k.kbin = e.w;
+    k.invRc = c.x; k.gfrac = c.y; k.psic = c.z; k.l2kappa = c.w;
+    k.kq = d.x; k.K0hi = d.y; k.K0lo = d.z; k.kbin = d.w;
+    k.gint = __float_as_int(s.e.x);
     return k;
 }
 
@@ -208,23 +209,21 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, int64_t p
     const double inv = 1.0 / Rc;
     const double dt = m.inv_prf;
     const double epx = m.v[0] * dt, epy = m.v[1] * dt, epz = m.v[2] * dt;
-    const double Mx = Dx + 0.5 * epx, My = Dy + 0.5 * epy, Mz = Dz + 0.5 * epz;
-    const double K0 = Mx * epx + My * epy + Mz * epz;
+    const double K0 = (Dx + 0.5 * epx) * epx + (Dy + 0.5 * epy) * epy + (Dz + 0.5 * epz) * epz;
     const float K0hi = (float)K0;
     SplitConst k;
     k.a = make_float4((float)t, (float)Dx, (float)Dy, (float)Dz);
     k.b = make_float4((float)(Dx * inv), (float)(Dy * inv), (float)(Dz * inv), (float)(0.5 * inv));
-    k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, (float)((rref * inv) * (rref * inv)));
-    k.d = make_float4((float)(1.0 / (Dz * Dz)), (float)Mx, (float)My, (float)Mz);
-    k.e = make_float4(K0hi, (float)(K0 - (double)K0hi),
-                      __int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)),
+    k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, (float)(2.0 * log2(rref * inv)));
+    k.d = make_float4((float)(m.beam_k / (Dz * Dz)), K0hi, (float)(K0 - (double)K0hi),
                       (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
+    k.e = make_float4(__int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)), 0.f, 0.f, 0.f);
     return k;
 }
 
 // Scatterer registers of the split path (positions relative to the CTA reference point).
-// c1 = dt (e_p . v) / 2 - dt^2 |v|^2 / 2 is the part of the pulse-pair range change that
-// depends on the scatterer alone.
+// c1 = dt (e_p . v) - dt^2 |v|^2 / 2 is the part of the pulse-pair range change that depends
+// on the scatterer alone.
 struct ItemF {
     float lx0, ly0, z, vx, vy, vz, amp0, c1;
     int ok;  // 1 for a real scatterer, 0 for padding past the end of the set
@@ -277,29 +276,28 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
     const float dR0 = fmaf(ll, k.h, -ul);
     const float dR = dR0 * fmaf(-dR0, k.h, 1.0f);
-    // gate
+    // gate: floor of the coordinate; re-decided in FP64 within the band of an edge
     const float gcf = fmaf(dR, m.inv_gw_f, k.gfrac);
     const float gfl = floorf(gcf);
-    const float gfr = gcf - gfl;
     int g = k.gint + (int)gfl;
-    const float eg = fmaf(fabsf(gcf), kEpsSlope, kGateEps);
-    int fl = (fabsf(gfr - 0.5f) > 0.5f - eg) ? kFlagRefine : 0;
-    // antenna: q = rho / d_z, theta^2 = atan(q)^2 (series for q^2 < 0.01)
+    int fl = (fabsf((gcf - gfl) - 0.5f) > fmaf(-fabsf(gcf), kEpsSlope, 0.5f - kGateEps))
+                 ? kFlagRefine : 0;
+    // |C| = sqrt(sigma A) 2^E, E = beam_k atan(q)^2 + log2 (r_ref/R_c)^2 - 2 log2(1 + dR/R_c),
+    // q = rho / d_z (series in qb = beam_k q^2 below 0.01 q^2; the exact angle beyond)
     const float dx = k.Dx - lx, dy = k.Dy - ly;
     const float rho2 = fmaf(dx, dx, dy * dy);
-    const float q2 = rho2 * k.invDz2;
-    float th2 = q2 * fmaf(q2, fmaf(q2, 23.0f / 45.0f, -2.0f / 3.0f), 1.0f);
-    if (q2 >= 1e-2f) {
+    const float qb = rho2 * k.kq;
+    float T = fmaf(qb, fmaf(qb, fmaf(qb, m.s2, m.s1), 1.0f), k.l2kappa);
+    if (qb < m.qb_wide) {
         fl |= kFlagWide;
         if (GENERAL) {
             const float th = atan2f(sqrtf(rho2), k.Dz - lz);
-            th2 = th * th;
+            T = fmaf(th * th, m.beam_k_f, k.l2kappa);
         }
     }
-    // |C| = sqrt(sigma A) 2^(-2 theta^2 / theta_b^2) (r_ref / R_c)^2 (1 + dR / R_c)^-2
     const float xr = dR * k.invRc;
-    const float E = fmaf(th2, m.beam_k_f, xr * fmaf(xr, kInvLn2F, -2.0f * kInvLn2F));
-    const float a = (it.amp0 * k.kappa) * ex2_approx(E);
+    const float E = fmaf(xr, fmaf(xr, kInvLn2F, -2.0f * kInvLn2F), T);
+    const float a = it.amp0 * ex2_approx(E);
     // phase in cycles: psi_c + dR 2/lambda (2/lambda as hi + lo, the product error-free)
     const float p = dR * m.chi_hi;
     const float perr = fmaf(dR, m.chi_hi, -p);
@@ -310,24 +308,20 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     re = a * cs;
     im = -a * sn;
     int kb = 0;
-    float bc = 0.5f;
+    float b = 0.0f;
     if (DOPPLER) {
         // pulse-pair range change D = 2 (d + e/2).e / (R + R'), d = D - l, e = e_p - v dt:
-        // (d + e/2).e = K0 - dt (M.v) - c1 - l.e ;  bin coordinate -n_doppler 2 D / lambda + 1/2
-        const float ex = fmaf(-it.vx, m.dt_f, m.ep[0]);
-        const float ey = fmaf(-it.vy, m.dt_f, m.ep[1]);
-        const float ez = fmaf(-it.vz, m.dt_f, m.ep[2]);
-        const float Mv = fmaf(k.Mx, it.vx, fmaf(k.My, it.vy, k.Mz * it.vz));
-        const float le = fmaf(lx, ex, fmaf(ly, ey, lz * ez));
-        const float hn2 = ((fmaf(-m.dt_f, Mv, k.K0hi) - le) - it.c1) + k.K0lo;
-        float b = (hn2 * k.kbin) * (1.0f - xr);     // nu n_doppler, unwrapped
-        b = fmaf(-(float)m.n_doppler, rintf(b * m.inv_nd), b);
-        bc = b + 0.5f;
-        const float bfl = floorf(bc);
-        const float bfr = bc - bfl;
-        kb = ((int)bfl) & (m.n_doppler - 1);
-        const float eb = fmaf(fabsf(b), kEpsSlope, kBinEps);
-        if (fabsf(bfr - 0.5f) > 0.5f - eb) fl |= kFlagRefine;
+        // (d + e/2).e = K0 - l.e_p - dt (d.v) - c1;  b = nu n_doppler = -n_doppler 2 D / lambda
+        // (unwrapped: the bin is taken mod n_doppler); bin = nearest integer to b
+        const float dz = k.Dz - lz;
+        const float dv_ = fmaf(dx, it.vx, fmaf(dy, it.vy, dz * it.vz));
+        const float lep = fmaf(lx, m.ep[0], fmaf(ly, m.ep[1], lz * m.ep[2]));
+        const float hn2 = ((fmaf(-m.dt_f, dv_, k.K0hi) - lep) - it.c1) + k.K0lo;
+        b = hn2 * k.kbin;
+        b = fmaf(-b, xr, b);                       // 1 / (R_c + dR) = (1 / R_c)(1 - dR / R_c)
+        const float br = rintf(b);
+        kb = __float2int_rn(b) & (m.n_doppler - 1);
+        if (fabsf(b - br) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps)) fl |= kFlagRefine;
     }
     if (DERIV) {
         // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
@@ -335,6 +329,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         const float dz = k.Dz - lz;
         const float invR = k.invRc * (1.0f - xr);
         const float invR2 = invR * invR;
+        const float q2 = qb * m.inv_beam_k;
         float rho_theta;
         if (q2 < 1e-2f) {
             rho_theta = rho2 / dz * fmaf(q2, fmaf(q2, 0.2f, -1.0f / 3.0f), 1.0f);
@@ -345,7 +340,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         dv->dlna = (2.0f * dz + 1.38629436111989061883f * m.beam_k_f * rho_theta) * invR2;
         dv->dphi = kTwoPiF * (m.chi_hi + m.chi_lo) * dz * invR;  // chi = 2 / lambda
     }
-    double gcd = (double)k.gint + (double)gcf, bcd = (double)bc;
+    double gcd = (double)k.gint + (double)gcf;
+    double bcd = (double)b - (double)m.n_doppler * rint((double)b / (double)m.n_doppler) + 0.5;
     if (GENERAL && (fl & kFlagRefine) && it.ok) {
         int g2, kb2;
         refine_fp64(m, *k64, (double)x_orig, (double)y_orig, (double)it.z, (double)it.vx,
