@@ -2,7 +2,7 @@
 //
 //  * accumulate_*: regular mode (Section II.A, one sample per pulse, cells = gates) and
 //    the fast-mode Doppler pass (Algorithm 1 of Section III.B, one sample per update,
-//    cells = gate x Doppler bin).  Each CTA owns 1024 consecutive scatterers held in
+//    cells = gate x Doppler bin).  Each CTA owns 512 consecutive scatterers (128 threads x 4) held in
 //    registers for ALL of its samples, so the 28 B of input per scatterer are read from
 //    HBM once per launch however many samples there are.  Per (CTA, sample) FP64 constants
 //    of a CTA reference point are computed by one thread per sample into shared memory.

@@ -15,13 +15,13 @@ namespace rsim {
 
 // Launch shape of the summation kernels (compile-time; the defaults are the tuned values).
 #ifndef RSIM_THREADS
-#define RSIM_THREADS 256
+#define RSIM_THREADS 128
 #endif
 #ifndef RSIM_ITEMS
 #define RSIM_ITEMS 4
 #endif
 #ifndef RSIM_MIN_BLOCKS
-#define RSIM_MIN_BLOCKS 2
+#define RSIM_MIN_BLOCKS 5
 #endif
 constexpr int kThreads = RSIM_THREADS;        // summation CTA size
 constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (1, 2, 4, 8)
