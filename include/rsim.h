@@ -213,6 +213,26 @@ rsim_status rsim_direct_sum_backward(const rsim_radar *radar, const rsim_platfor
                                      const void *grad_iq, float *grad_z, float *grad_nrcs,
                                      cudaStream_t stream);
 
+/* rsim_doppler_accumulate without a caller workspace, for callers that cannot allocate
+ * device memory where they run (allocation-free real-time loops, plug-ins inside a host
+ * process whose allocator they do not own, tenants of a pre-partitioned GPU).  The paper
+ * has no counterpart: this is a deployment variant of the same computation.
+ * Same arguments and results as rsim_doppler_accumulate minus the workspace; the
+ * fixed-point scratch is a 16 MiB device array built into the library (held by every GPU
+ * that loads the library until the process exits), so
+ * rsim_workspace_size(n_updates, n_gates, n_doppler) must be <= 16 MiB, else
+ * RSIM_ERR_WORKSPACE.  Nothing is allocated: no cudaMalloc/cudaFree or allocating library
+ * call.  The first call on each device looks the array's device address up
+ * (cudaGetSymbolAddress, with that device current): make that first call before any
+ * stream capture.  All calls on a device share the array and each clears it on entry, so
+ * calls that may overlap on the GPU race; order them (one stream, or events). */
+rsim_status rsim_doppler_accumulate_noalloc(const rsim_radar *radar,
+                                            const rsim_platform *platform,
+                                            const rsim_scatterers *scat, int64_t update0,
+                                            int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                            rsim_precision precision, void *spectra,
+                                            cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

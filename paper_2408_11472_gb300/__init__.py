@@ -25,7 +25,7 @@ from ._lib import PRECISIONS, WINDOWS, RsimError
 
 __all__ = [
     "Radar", "Platform", "Scatterers", "RsimError", "workspace_size", "direct_sum",
-    "doppler_accumulate", "synth_pulses", "scatterer_cells", "synth_pulses_backward",
+    "doppler_accumulate", "doppler_accumulate_noalloc", "synth_pulses", "scatterer_cells", "synth_pulses_backward",
     "doppler_accumulate_backward", "direct_sum_backward", "spectra_range", "simulate_fast",
     "FastMode", "RegularMode", "version", "PRECISIONS", "WINDOWS",
 ]
@@ -169,6 +169,24 @@ def doppler_accumulate(radar, platform, scat: Scatterers, update0: int, n_update
         ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(update0), int(n_updates),
         int(n_fast), int(n_doppler), _prec(precision), _ptr(out), _ptr(ws),
         ws.numel() * ws.element_size(), _stream(stream)))
+    return out
+
+
+def doppler_accumulate_noalloc(radar, platform, scat: Scatterers, update0: int, n_updates: int,
+                               n_fast: int, n_doppler: int, precision: str = "split",
+                               out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """doppler_accumulate without a workspace, for callers that cannot allocate device
+    memory where they run: the scratch is the library's built-in 16 MiB device array (calls
+    that overlap on the GPU race on it).  ``out`` should be passed by such callers; without
+    it a zeroed tensor is created here for convenience."""
+    shape = (n_updates, radar.n_gates, n_doppler)
+    if out is None:
+        out = torch.zeros(shape, dtype=_cdtype(precision), device=scat.device)
+    _need(out, _cdtype(precision), shape, scat.device, "out")
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_doppler_accumulate_noalloc(
+        ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(update0), int(n_updates),
+        int(n_fast), int(n_doppler), _prec(precision), _ptr(out), _stream(stream)))
     return out
 
 

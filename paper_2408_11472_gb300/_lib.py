@@ -67,6 +67,8 @@ PROTOTYPES = {
                                           _P, _P, _P, _P], ctypes.c_int),
     "rsim_direct_sum_backward": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P],
                                  ctypes.c_int),
+    "rsim_doppler_accumulate_noalloc": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
+                                         _P, _P], ctypes.c_int),
 }
 
 

@@ -244,6 +244,21 @@ rsim::SynthArgs make_synth_args(const rsim_radar* radar, int32_t n_spectra, int6
 
 }  // namespace
 
+namespace rsim {
+
+// Sets the calling thread's rsim_last_error() message (for entry points in other
+// translation units).
+void set_last_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+}  // namespace rsim
+
 extern "C" {
 
 int rsim_version(void) { return RSIM_ABI_VERSION; }

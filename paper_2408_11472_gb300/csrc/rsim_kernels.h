@@ -22,6 +22,9 @@ cudaError_t launch_backward(const Model& m, const Schedule& sch, const Scat& sc,
                             bool doppler, const void* G, float* grad_z, float* grad_nrcs,
                             cudaStream_t stream);
 
+// Sets the calling thread's rsim_last_error() message (abi.cu).
+void set_last_error(const char* fmt, ...);
+
 // Post-processing (synth.cu).
 struct SynthArgs {
     int n_gates, n_doppler, log2_nd, n_fast, n_spectra, n_pulses;
