@@ -128,6 +128,11 @@ typedef struct {
 /* Library version (RSIM_ABI_VERSION). */
 int rsim_version(void);
 
+/* Number of consecutive scatterers that share one FP64 reference point in RSIM_SPLIT
+ * (the scatterer block of one CTA).  Splitting a scatterer set at multiples of it keeps every
+ * scatterer's arithmetic, and so its index decisions, identical to an unsplit call. */
+int rsim_block_scatterers(void);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *rsim_last_error(void);
 

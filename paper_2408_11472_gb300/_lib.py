@@ -52,6 +52,7 @@ _I32, _I64 = ctypes.c_int32, ctypes.c_int64
 PROTOTYPES = {
     "rsim_version": ([], ctypes.c_int),
     "rsim_last_error": ([], ctypes.c_char_p),
+    "rsim_block_scatterers": ([], ctypes.c_int),
     "rsim_workspace_size": ([_I32, _I32, _I32], ctypes.c_size_t),
     "rsim_direct_sum": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, ctypes.c_size_t, _P],
                         ctypes.c_int),

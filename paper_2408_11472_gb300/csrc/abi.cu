@@ -265,6 +265,8 @@ int rsim_version(void) { return RSIM_ABI_VERSION; }
 
 const char* rsim_last_error(void) { return g_last_error.c_str(); }
 
+int rsim_block_scatterers(void) { return rsim::kChunk; }
+
 size_t rsim_workspace_size(int32_t n_samples, int32_t n_gates, int32_t n_doppler) {
     if (n_samples < 0 || n_gates < 1 || n_gates > 4096 || !is_pow2(n_doppler) || n_doppler > 4096)
         return 0;

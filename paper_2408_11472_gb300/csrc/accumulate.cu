@@ -193,12 +193,29 @@ __global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
     }
 }
 
+// Fixed point (q 2^-32) to float without the FP64 pipe: |q| = hi 2^32 + lo, both unsigned
+// 32-bit, so small values keep their full relative precision.
+__device__ __forceinline__ float fixed_to_f32(long long q) {
+    const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
+    const unsigned hi = (unsigned)(a >> 32);
+    const unsigned lo = (unsigned)(a & 0xffffffffull);
+    const float v = fmaf(__uint2float_rn(lo), 2.3283064365386963e-10f, __uint2float_rn(hi));
+    return q < 0 ? -v : v;
+}
+
+template <typename T>
+__device__ __forceinline__ T fixed_to(long long q);
+template <>
+__device__ __forceinline__ float fixed_to<float>(long long q) { return fixed_to_f32(q); }
+template <>
+__device__ __forceinline__ double fixed_to<double>(long long q) { return (double)q * (1.0 / kFixScale); }
+
 template <typename T>
 __global__ void finalize_kernel(const long long* __restrict__ ws, T* __restrict__ out,
                                 int64_t n_vals) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vals; i += stride) {
-        out[i] += (T)((double)ws[i] * (1.0 / kFixScale));
+        out[i] += fixed_to<T>(__ldcs(ws + i));
     }
 }
 
