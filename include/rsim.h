@@ -163,6 +163,30 @@ rsim_status rsim_doppler_accumulate(const rsim_radar *radar, const rsim_platform
                                     rsim_precision precision, void *spectra, void *workspace,
                                     size_t workspace_bytes, cudaStream_t stream);
 
+/* Workspace bytes of rsim_doppler_accumulate_batched: n_real regions of
+ * rsim_workspace_size(n_samples, n_gates, n_doppler) rounded up to 256 bytes. */
+size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_gates,
+                                   int32_t n_doppler);
+
+/* rsim_doppler_accumulate for n_real independent scatterer sets -- realizations of the same
+ * track, as the ~100 realizations behind each SWH/SSH spectrum of Section IV.D -- in one
+ * launch per group of up to 96 sets: every CTA of the launch takes a block of scatterers of
+ * one set (sets of uneven size share the grid), and samples whose range window no scatterer
+ * of a block can reach are skipped by that block.  Each set's spectra are bit-identical to
+ * a rsim_doppler_accumulate call of its own.
+ * scats   : HOST array [n_real] of scatterer sets (device arrays; each its own origin/area);
+ * spectra : HOST array [n_real] of DEVICE pointers, each [n_updates][n_gates][n_doppler]
+ *           complex, accumulated (+=);
+ * workspace >= rsim_batched_workspace_size(n_real, n_updates, n_gates, n_doppler), 256-byte
+ * aligned.  Capturable in a CUDA graph (memset + kernels only). */
+rsim_status rsim_doppler_accumulate_batched(const rsim_radar *radar,
+                                            const rsim_platform *platform, int32_t n_real,
+                                            const rsim_scatterers *scats, int64_t update0,
+                                            int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                            rsim_precision precision, void *const *spectra,
+                                            void *workspace, size_t workspace_bytes,
+                                            cudaStream_t stream);
+
 /* Fast-mode post-processing (Section III.B steps 2-4 with Eq. (1)): batched
  * n_doppler-point inverse FFT per gate of each spectrum, blend window, sum into
  * the pulses x in [pulse0, pulse0 + n_pulses).

@@ -25,7 +25,8 @@ from ._lib import PRECISIONS, WINDOWS, RsimError
 
 __all__ = [
     "Radar", "Platform", "Scatterers", "RsimError", "workspace_size", "direct_sum",
-    "doppler_accumulate", "doppler_accumulate_noalloc", "synth_pulses", "scatterer_cells", "synth_pulses_backward",
+    "doppler_accumulate", "doppler_accumulate_noalloc", "doppler_accumulate_batched",
+    "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "synth_pulses_backward",
     "doppler_accumulate_backward", "direct_sum_backward", "spectra_range", "simulate_fast",
     "FastMode", "RegularMode", "version", "PRECISIONS", "WINDOWS",
 ]
@@ -188,6 +189,35 @@ def doppler_accumulate_noalloc(radar, platform, scat: Scatterers, update0: int, 
         ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(update0), int(n_updates),
         int(n_fast), int(n_doppler), _prec(precision), _ptr(out), _stream(stream)))
     return out
+
+
+def batched_workspace_size(n_real: int, n_samples: int, n_gates: int, n_doppler: int) -> int:
+    return int(_lib.lib.rsim_batched_workspace_size(int(n_real), int(n_samples), int(n_gates),
+                                                    int(n_doppler)))
+
+
+def doppler_accumulate_batched(radar, platform, scats, update0: int, n_updates: int, n_fast: int,
+                               n_doppler: int, precision: str = "split", outs=None,
+                               workspace: Optional[torch.Tensor] = None, stream=None):
+    """doppler_accumulate for a list of independent scatterer sets (realizations of the same
+    track) in one launch per group of 96.  Returns the list of spectra (+= into ``outs``)."""
+    n_real = len(scats)
+    shape = (n_updates, radar.n_gates, n_doppler)
+    dev = scats[0].device if n_real else torch.device("cuda")
+    if outs is None:
+        outs = [torch.zeros(shape, dtype=_cdtype(precision), device=dev) for _ in range(n_real)]
+    for o in outs:
+        _need(o, _cdtype(precision), shape, dev, "out")
+    need = batched_workspace_size(n_real, n_updates, radar.n_gates, n_doppler)
+    ws = _workspace(workspace, need, dev)
+    arr = (_lib.Scatterers * max(n_real, 1))(*[s.c_struct() for s in scats])
+    ptrs = (ctypes.c_void_p * max(n_real, 1))(*[o.data_ptr() for o in outs])
+    rd, pf = _lib.make_radar(radar), _lib.make_platform(platform)
+    _lib.check(_lib.lib.rsim_doppler_accumulate_batched(
+        ctypes.byref(rd), ctypes.byref(pf), n_real, arr, int(update0), int(n_updates), int(n_fast),
+        int(n_doppler), _prec(precision), ptrs, _ptr(ws), ws.numel() * ws.element_size(),
+        _stream(stream)))
+    return outs
 
 
 def _prec_of(t: torch.Tensor) -> str:
@@ -359,3 +389,70 @@ class RegularMode(torch.autograd.Function):
         s, radar, platform, pulse0 = ctx.args
         gz, gs = direct_sum_backward(radar, platform, s, pulse0, grad_y.contiguous())
         return gz, gs, None, None, None, None, None, None
+
+
+class BatchedFastMode:
+    """Fast mode for many independent realizations of the same track (e.g. the ~100 surface
+    realizations averaged per SWH/SSH spectrum, Section IV.D).
+
+    Per block of ``update_block`` updates one batched spectrum launch covers every
+    realization (rsim_doppler_accumulate_batched: one CTA grid shared by sets of uneven
+    size, out-of-window samples culled per block); then each realization's post-processing
+    runs.  All buffers are allocated up front, so the whole sequence can be captured once
+    into a CUDA graph (``capture()``) and replayed (``replay()``).  ``spectra[r]`` and
+    ``iq[r]`` hold realization r's results."""
+
+    def __init__(self, radar, platform, scats, pulse0: int, n_pulses: int, n_fast: int,
+                 n_doppler: int, window: str = "sqrt_raised_cosine", precision: str = "split",
+                 update_block: int = 64):
+        self.radar, self.platform, self.scats = radar, platform, list(scats)
+        self.pulse0, self.n_pulses, self.n_fast, self.n_doppler = pulse0, n_pulses, n_fast, n_doppler
+        self.window, self.precision = window, precision
+        self.u0, self.S = spectra_range(pulse0, n_pulses, n_fast)
+        self.block = max(1, min(int(update_block), self.S))
+        dev = self.scats[0].device
+        cdt = _cdtype(precision)
+        G = radar.n_gates
+        self.spectra = [torch.zeros((self.S, G, n_doppler), dtype=cdt, device=dev) for _ in self.scats]
+        self.iq = [torch.empty((n_pulses, G), dtype=cdt, device=dev) for _ in self.scats]
+        self.workspace = torch.empty(
+            max(16, batched_workspace_size(len(self.scats), self.block, G, n_doppler)),
+            dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def _run(self):
+        for T in self.spectra:
+            T.zero_()
+        for b0 in range(0, self.S, self.block):
+            b1 = min(self.S, b0 + self.block)
+            doppler_accumulate_batched(self.radar, self.platform, self.scats, self.u0 + b0, b1 - b0,
+                                       self.n_fast, self.n_doppler, self.precision,
+                                       outs=[T[b0:b1] for T in self.spectra],
+                                       workspace=self.workspace)
+        for T, Y in zip(self.spectra, self.iq):
+            synth_pulses(self.radar, T, self.u0, self.n_fast, self.pulse0, self.n_pulses,
+                         self.window, out=Y)
+
+    def run(self):
+        """Run eagerly on the current stream."""
+        self._run()
+        return self.iq
+
+    def capture(self):
+        """Record the whole update loop into a CUDA graph (after one eager warm-up run)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._run()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._run()
+        self.graph = g
+        return self
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+        return self.iq

@@ -68,6 +68,10 @@ PROTOTYPES = {
                                           _P, _P, _P, _P], ctypes.c_int),
     "rsim_direct_sum_backward": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P],
                                  ctypes.c_int),
+    "rsim_batched_workspace_size": ([_I32, _I32, _I32, _I32], ctypes.c_size_t),
+    "rsim_doppler_accumulate_batched": ([_RP, _PP, _I32, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p), _P, ctypes.c_size_t, _P],
+                                        ctypes.c_int),
     "rsim_doppler_accumulate_noalloc": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
                                          _P, _P], ctypes.c_int),
 }

@@ -140,6 +140,31 @@ size_t ws_bytes(int64_t n_samples, int n_gates, int n_doppler) {
     return (size_t)n_samples * (size_t)n_gates * (size_t)n_doppler * 16u;
 }
 
+// Sample schedule of a summation launch.  The samples are split over gridDim.y only when the
+// scatterer chunks alone cannot fill the GPU (about 8 resident CTAs' worth per SM).
+// Returns the number of sample groups (gridDim.y).
+int64_t plan_samples(int64_t chunks, int64_t pulse_base, int32_t stride, int32_t n_samples,
+                     rsim::Schedule* sch) {
+    const int64_t target = (int64_t)device_sms() * 8;
+    int64_t groups = (target + chunks - 1) / chunks;
+    if (groups < 1) groups = 1;
+    if (groups > n_samples) groups = n_samples;
+    int64_t spg = (n_samples + groups - 1) / groups;
+    if (spg < (n_samples + 65534) / 65535) spg = (n_samples + 65534) / 65535;
+    groups = (n_samples + spg - 1) / spg;
+    sch->pulse_base = pulse_base;
+    sch->pulse_stride = stride;
+    sch->n_samples = n_samples;
+    sch->samples_per_group = (int32_t)spg;
+    sch->pad = 0;
+    return groups;
+}
+
+size_t batch_stride(int32_t n_samples, int32_t n_gates, int32_t n_doppler) {
+    const size_t b = ws_bytes(n_samples, n_gates, n_doppler);
+    return (b + 255u) & ~(size_t)255u;
+}
+
 // Shared body of rsim_direct_sum and rsim_doppler_accumulate.
 rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platform,
                            const rsim_scatterers* scat, int64_t pulse_base, int32_t stride,
@@ -169,21 +194,8 @@ rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platfor
     const rsim::Scat sc = make_scat(scat);
     const int64_t chunks = (scat->n + rsim::kChunk - 1) / rsim::kChunk;
     if (chunks > 0x7fffffff) return fail(RSIM_ERR_INVALID_ARG, "too many scatterers");
-    // Split the samples over gridDim.y only when the scatterer chunks alone cannot fill the
-    // GPU (about 8 resident CTAs' worth per SM).
-    const int64_t target = (int64_t)device_sms() * 8;
-    int64_t groups = (target + chunks - 1) / chunks;
-    if (groups < 1) groups = 1;
-    if (groups > n_samples) groups = n_samples;
-    int64_t spg = (n_samples + groups - 1) / groups;
-    if (spg < (n_samples + 65534) / 65535) spg = (n_samples + 65534) / 65535;
-    groups = (n_samples + spg - 1) / spg;
     rsim::Schedule sch;
-    sch.pulse_base = pulse_base;
-    sch.pulse_stride = stride;
-    sch.n_samples = n_samples;
-    sch.samples_per_group = (int32_t)spg;
-    sch.pad = 0;
+    const int64_t groups = plan_samples(chunks, pulse_base, stride, n_samples, &sch);
 
     cudaError_t e = cudaMemsetAsync(workspace, 0, need, stream);
     if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
@@ -402,6 +414,86 @@ rsim_status rsim_doppler_accumulate_backward(const rsim_radar* radar,
         return fail(RSIM_ERR_INVALID_ARG, "update0 out of range");
     return run_backward(radar, platform, scat, update0 * (int64_t)n_fast, n_fast, n_updates,
                         n_doppler, true, precision, grad_spectra, grad_z, grad_nrcs, stream);
+}
+
+size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_gates,
+                                   int32_t n_doppler) {
+    if (n_real < 0 || rsim_workspace_size(n_samples, n_gates, n_doppler) == 0) return 0;
+    return (size_t)n_real * batch_stride(n_samples, n_gates, n_doppler);
+}
+
+rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_platform* platform,
+                                            int32_t n_real, const rsim_scatterers* scats,
+                                            int64_t update0, int32_t n_updates, int32_t n_fast,
+                                            int32_t n_doppler, rsim_precision precision,
+                                            void* const* spectra, void* workspace,
+                                            size_t workspace_bytes, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_platform(platform)) != RSIM_OK) return st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (n_fast < 1) return fail(RSIM_ERR_INVALID_ARG, "n_fast=%d < 1", n_fast);
+    if (!is_pow2(n_doppler) || n_doppler > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [1, 4096]", n_doppler);
+    if ((int64_t)radar->n_gates * n_doppler > ((int64_t)1 << 24))
+        return fail(RSIM_ERR_INVALID_ARG, "n_gates * n_doppler > 2^24");
+    if (n_real < 0 || n_updates < 0 || update0 < 0)
+        return fail(RSIM_ERR_INVALID_ARG, "negative count or index");
+    if (update0 > (((int64_t)1 << 52) / n_fast) - n_updates)
+        return fail(RSIM_ERR_INVALID_ARG, "update index out of range");
+    if (n_real == 0 || n_updates == 0) return RSIM_OK;
+    if (!scats || !spectra) return fail(RSIM_ERR_INVALID_ARG, "scatterer / spectra arrays are NULL");
+    const bool fp64 = precision == RSIM_FP64;
+    for (int r = 0; r < n_real; ++r) {
+        if ((st = check_scat(&scats[r])) != RSIM_OK)
+            return fail(st, "realization %d: %s", r, g_last_error.c_str());
+        if (scats[r].n > 0 && (!spectra[r] || !aligned(spectra[r], fp64 ? 16 : 8)))
+            return fail(RSIM_ERR_INVALID_ARG, "realization %d: spectra NULL or misaligned", r);
+    }
+    const size_t stride_b = batch_stride(n_updates, radar->n_gates, n_doppler);
+    const size_t need = (size_t)n_real * stride_b;
+    if (!workspace) return fail(RSIM_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
+    if (!aligned(workspace, 256)) return fail(RSIM_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    if (workspace_bytes < need)
+        return fail(RSIM_ERR_WORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, need);
+
+    const rsim::Model m = make_model(radar, platform, &scats[0], n_doppler);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, need, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    const int64_t n_vals = (int64_t)(ws_bytes(n_updates, radar->n_gates, n_doppler) / 8);
+    static thread_local rsim::BatchParams bp;       // 11.5 KB: kept off the host stack
+    static thread_local rsim::FinalizeBatch fb;
+    int r = 0;
+    while (r < n_real) {
+        int k = 0;
+        int64_t chunks = 0;
+        for (; r < n_real && k < rsim::kMaxBatch; ++r) {
+            if (scats[r].n == 0) continue;
+            rsim::BatchEntry& be = bp.e[k];
+            be.sc = make_scat(&scats[r]);
+            for (int i = 0; i < 3; ++i) be.p0[i] = platform->p0[i] - scats[r].origin[i];
+            be.chunk_begin = chunks;
+            be.ws = reinterpret_cast<unsigned long long*>(static_cast<char*>(workspace) + (size_t)r * stride_b);
+            be.area = (float)scats[r].facet_area_m2;
+            be.pad = 0;
+            fb.ws[k] = be.ws;
+            fb.out[k] = spectra[r];
+            chunks += (scats[r].n + rsim::kChunk - 1) / rsim::kChunk;
+            ++k;
+        }
+        if (k == 0) break;
+        if (chunks > 0x7fffffff) return fail(RSIM_ERR_INVALID_ARG, "too many scatterers in one batch");
+        bp.n_real = k;
+        bp.pad = 0;
+        rsim::Schedule sch;
+        const int64_t groups = plan_samples(chunks, update0 * (int64_t)n_fast, n_fast, n_updates, &sch);
+        e = rsim::launch_accumulate_batched(m, sch, bp, fp64, true, dim3((unsigned)chunks, (unsigned)groups),
+                                            stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batched summation kernel launch");
+        e = rsim::launch_finalize_batched(fb, k, n_vals, fp64, device_sms(), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batched finalize kernel launch");
+    }
+    return RSIM_OK;
 }
 
 rsim_status rsim_direct_sum_backward(const rsim_radar* radar, const rsim_platform* platform,

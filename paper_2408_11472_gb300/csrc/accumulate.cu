@@ -2,12 +2,17 @@
 //
 //  * accumulate_*: regular mode (Section II.A, one sample per pulse, cells = gates) and
 //    the fast-mode Doppler pass (Algorithm 1 of Section III.B, one sample per update,
-//    cells = gate x Doppler bin).  Each CTA owns 512 consecutive scatterers (128 threads x 4) held in
-//    registers for ALL of its samples, so the 28 B of input per scatterer are read from
-//    HBM once per launch however many samples there are.  Per (CTA, sample) FP64 constants
-//    of a CTA reference point are computed by one thread per sample into shared memory.
-//    Contributions leave a warp as merged runs and are added with 64-bit integer atomics
-//    into a fixed-point workspace (exact, order-independent sums).
+//    cells = gate x Doppler bin).  Each CTA owns kChunk consecutive scatterers (kThreads x
+//    kItems) held in registers for ALL of its samples, so the 28 B of input per scatterer
+//    are read from HBM once per launch however many samples there are.  Per (CTA, sample)
+//    FP64 constants of a CTA reference point are computed by one thread per sample into
+//    shared memory, together with a culling flag: a sample none of whose scatterers can
+//    reach the range window is skipped by the whole CTA.  Contributions leave a warp as
+//    merged runs and are added with 64-bit integer atomics into a fixed-point workspace
+//    (exact, order-independent sums).
+//    The batched variants run many independent scatterer sets (realizations of the same
+//    track) in one launch; every realization keeps its own chunking, so its result is
+//    bit-identical to a launch of its own.
 //  * finalize: fixed-point workspace -> complex output (+=).
 //  * cells: per-scatterer gate / bin decisions (same arithmetic as accumulate).
 //  * backward_*: adjoint gather -- per scatterer, recompute C and its z-derivative at every
@@ -65,7 +70,8 @@ __device__ __forceinline__ void chunk_ref(const Scat& sc, int64_t chunk0, float&
 }
 
 __device__ __forceinline__ void items_split(const Model& m, const Raw& r, float cx, float cy,
-                                            int64_t base, int64_t n, ItemF (&it)[kItems]) {
+                                            float area, int64_t base, int64_t n,
+                                            ItemF (&it)[kItems]) {
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
         it[q].lx0 = r.x[q] - cx;
@@ -74,7 +80,7 @@ __device__ __forceinline__ void items_split(const Model& m, const Raw& r, float 
         it[q].vx = r.vx[q];
         it[q].vy = r.vy[q];
         it[q].vz = r.vz[q];
-        it[q].amp0 = sqrtf(r.s[q] * (float)m.area);
+        it[q].amp0 = sqrtf(r.s[q] * area);
         const float epv = fmaf(m.ep[0], r.vx[q], fmaf(m.ep[1], r.vy[q], m.ep[2] * r.vz[q]));
         const float vv = fmaf(r.vx[q], r.vx[q], fmaf(r.vy[q], r.vy[q], r.vz[q] * r.vz[q]));
         it[q].c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
@@ -82,7 +88,7 @@ __device__ __forceinline__ void items_split(const Model& m, const Raw& r, float 
     }
 }
 
-__device__ __forceinline__ void items_fp64(const Model& m, const Raw& r, ItemD (&it)[kItems]) {
+__device__ __forceinline__ void items_fp64(const Raw& r, double area, ItemD (&it)[kItems]) {
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
         it[q].x = r.x[q];
@@ -91,46 +97,82 @@ __device__ __forceinline__ void items_fp64(const Model& m, const Raw& r, ItemD (
         it[q].vx = r.vx[q];
         it[q].vy = r.vy[q];
         it[q].vz = r.vz[q];
-        it[q].amp0 = sqrt((double)r.s[q] * m.area);
+        it[q].amp0 = sqrt((double)r.s[q] * area);
     }
+}
+
+// Culling bounds of the CTA's scatterers around its reference point (cx, cy, 0):
+// lmax >= max |r - c|, vmax >= max |v| over the real (non-padding) items, enlarged so that
+// FP32 rounding of the norms cannot make the bound too tight.
+__device__ __forceinline__ void chunk_bounds(const Raw& r, float cx, float cy, int64_t base,
+                                             int64_t n, float* s_red, float& lmax, float& vmax) {
+    float l = 0.f, v = 0.f;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        if (base + q < n) {
+            const float dx = r.x[q] - cx, dy = r.y[q] - cy;
+            l = fmaxf(l, sqrtf(fmaf(dx, dx, fmaf(dy, dy, r.z[q] * r.z[q]))));
+            v = fmaxf(v, sqrtf(fmaf(r.vx[q], r.vx[q], fmaf(r.vy[q], r.vy[q], r.vz[q] * r.vz[q]))));
+        }
+    }
+    // non-negative floats order like their bit patterns
+    const unsigned lb = __reduce_max_sync(0xffffffffu, __float_as_uint(l));
+    const unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+    if (threadIdx.x == 0) { s_red[0] = 0.f; s_red[1] = 0.f; }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned*>(s_red), lb);
+        atomicMax(reinterpret_cast<unsigned*>(s_red + 1), vb);
+    }
+    __syncthreads();
+    lmax = s_red[0] * (1.0f + 1e-6f) + 1e-3f;
+    vmax = s_red[1] * (1.0f + 1e-6f);
 }
 
 __device__ __forceinline__ int64_t sample_pulse(const Schedule& sch, int s) {
     return sch.pulse_base + (int64_t)s * sch.pulse_stride;
 }
 
-}  // namespace
+// One CTA's work on one scatterer set: chunk starting at chunk0, samples [s_begin, s_end).
+struct ChunkCtx {
+    Scat sc;
+    const double* p0;   // platform at t = 0 relative to this set's origin
+    float area;
+    int64_t chunk0;
+    unsigned long long* ws;
+};
 
-// ------------------------------------------------------------------------------- forward
 template <bool DOPPLER>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
-    Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
+__device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Schedule& sch,
+                                                       const ChunkCtx& cx_, int s_begin,
+                                                       int s_end) {
     __shared__ SplitConst tab[kTab];
     __shared__ Fp64Const tab64[kTab];
+    __shared__ float s_red[2];
     constexpr unsigned kFull = 0xffffffffu;
-    const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
-    const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
-    float cx, cy;
-    chunk_ref(sc, chunk0, cx, cy);
+    const Scat& sc = cx_.sc;
+    const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * kItems;
+    float cx, cy, lmax, vmax;
+    chunk_ref(sc, cx_.chunk0, cx, cy);
     ItemF it[kItems];
     {
         Raw r;
         load_raw(sc, base, r);
-        items_split(m, r, cx, cy, base, sc.n, it);
+        items_split(m, r, cx, cy, cx_.area, base, sc.n, it);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
     }
     const int cells = m.n_gates * m.n_doppler;
-    const int s_begin = blockIdx.y * sch.samples_per_group;
-    const int s_end = min(sch.n_samples, s_begin + sch.samples_per_group);
     for (int sb = s_begin; sb < s_end; sb += kTab) {
         const int nb = min(kTab, s_end - sb);
         __syncthreads();
         if (threadIdx.x < nb) {
             const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
-            tab[threadIdx.x] = make_split_const(m, pulse, cx, cy);
-            tab64[threadIdx.x] = make_fp64_const(m, pulse);
+            tab[threadIdx.x] = make_split_const(m, cx_.p0, pulse, cx, cy, lmax, vmax);
+            tab64[threadIdx.x] = make_fp64_const(m, cx_.p0, pulse);
         }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
+            if (!sample_active(tab[j])) continue;  // CTA-uniform
             const int s = sb + j;
             const SampleF k = load_sample(tab[j]);
             int key[kItems];
@@ -155,32 +197,49 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
                     }
                 }
             }
-            warp_reduce_emit<float, kItems>(key, re, im, ws + (int64_t)s * cells * 2);
+            warp_reduce_emit<float, kItems>(key, re, im, cx_.ws + (int64_t)s * cells * 2);
         }
     }
 }
 
+// FP64 path: culling uses the same bound around the chunk's middle scatterer.
+__device__ __forceinline__ int fp64_active(const Model& m, const Fp64Const& k, float cx, float cy,
+                                           float lmax, float vmax) {
+    const double dx = k.Px - (double)cx, dy = k.Py - (double)cy, dz = k.Pz;
+    const double Rc = sqrt(dx * dx + dy * dy + dz * dz);
+    const double G = (Rc - k.rref) * m.inv_gw + m.half_gates;
+    return window_reachable(m, G, k.t, lmax, vmax);
+}
+
 template <bool DOPPLER>
-__global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
-    Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
+__device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Schedule& sch,
+                                                      const ChunkCtx& cx_, int s_begin,
+                                                      int s_end) {
     __shared__ Fp64Const tab[kTab];
-    const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
-    const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
+    __shared__ float s_red[2];
+    const Scat& sc = cx_.sc;
+    const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * kItems;
+    float cx, cy, lmax, vmax;
+    chunk_ref(sc, cx_.chunk0, cx, cy);
     ItemD it[kItems];
     {
         Raw r;
         load_raw(sc, base, r);
-        items_fp64(m, r, it);
+        items_fp64(r, (double)cx_.area, it);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
     }
     const int cells = m.n_gates * m.n_doppler;
-    const int s_begin = blockIdx.y * sch.samples_per_group;
-    const int s_end = min(sch.n_samples, s_begin + sch.samples_per_group);
     for (int sb = s_begin; sb < s_end; sb += kTab) {
         const int nb = min(kTab, s_end - sb);
         __syncthreads();
-        if (threadIdx.x < nb) tab[threadIdx.x] = make_fp64_const(m, sample_pulse(sch, sb + threadIdx.x));
+        if (threadIdx.x < nb) {
+            Fp64Const k = make_fp64_const(m, cx_.p0, sample_pulse(sch, sb + threadIdx.x));
+            k.active = fp64_active(m, k, cx, cy, lmax, vmax);
+            tab[threadIdx.x] = k;
+        }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
+            if (!tab[j].active) continue;  // CTA-uniform
             const int s = sb + j;
             const Fp64Const& k = tab[j];
             int key[kItems];
@@ -188,9 +247,87 @@ __global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
 #pragma unroll
             for (int q = 0; q < kItems; ++q)
                 key[q] = eval_fp64<DOPPLER, false>(m, k, it[q], base + q, sc.n, re[q], im[q], nullptr);
-            warp_reduce_emit<double, kItems>(key, re, im, ws + (int64_t)s * cells * 2);
+            warp_reduce_emit<double, kItems>(key, re, im, cx_.ws + (int64_t)s * cells * 2);
         }
     }
+}
+
+__device__ __forceinline__ void sample_range(const Schedule& sch, int& s_begin, int& s_end) {
+    s_begin = blockIdx.y * sch.samples_per_group;
+    s_end = min(sch.n_samples, s_begin + sch.samples_per_group);
+}
+
+// Realization of a global chunk index in a batch (binary search over chunk_begin).
+__device__ __forceinline__ int batch_find(const BatchParams& bp, int64_t chunk) {
+    int lo = 0, hi = bp.n_real - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bp.e[mid].chunk_begin <= chunk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ ChunkCtx batch_ctx(const BatchParams& bp, int r, int64_t chunk) {
+    const BatchEntry& e = bp.e[r];
+    ChunkCtx c;
+    c.sc = e.sc;
+    c.p0 = e.p0;
+    c.area = e.area;
+    c.chunk0 = (chunk - e.chunk_begin) * kChunk;
+    c.ws = e.ws;
+    return c;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------- forward
+template <bool DOPPLER>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
+    Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
+    ChunkCtx c;
+    c.sc = sc;
+    c.p0 = m.p0;
+    c.area = (float)m.area;
+    c.chunk0 = (int64_t)blockIdx.x * kChunk;
+    c.ws = ws;
+    int s0, s1;
+    sample_range(sch, s0, s1);
+    accumulate_split_chunk<DOPPLER>(m, sch, c, s0, s1);
+}
+
+template <bool DOPPLER>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_batched_kernel(
+    Model m, Schedule sch, BatchParams bp) {
+    const int r = batch_find(bp, blockIdx.x);
+    const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);
+    int s0, s1;
+    sample_range(sch, s0, s1);
+    accumulate_split_chunk<DOPPLER>(m, sch, c, s0, s1);
+}
+
+template <bool DOPPLER>
+__global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
+    Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
+    ChunkCtx c;
+    c.sc = sc;
+    c.p0 = m.p0;
+    c.area = (float)m.area;
+    c.chunk0 = (int64_t)blockIdx.x * kChunk;
+    c.ws = ws;
+    int s0, s1;
+    sample_range(sch, s0, s1);
+    accumulate_fp64_chunk<DOPPLER>(m, sch, c, s0, s1);
+}
+
+template <bool DOPPLER>
+__global__ void __launch_bounds__(kThreads) accumulate_fp64_batched_kernel(
+    Model m, Schedule sch, BatchParams bp) {
+    const int r = batch_find(bp, blockIdx.x);
+    const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);
+    int s0, s1;
+    sample_range(sch, s0, s1);
+    accumulate_fp64_chunk<DOPPLER>(m, sch, c, s0, s1);
 }
 
 // Fixed point (q 2^-32) to float without the FP64 pipe: |q| = hi 2^32 + lo, both unsigned
@@ -219,6 +356,17 @@ __global__ void finalize_kernel(const long long* __restrict__ ws, T* __restrict_
     }
 }
 
+// Batched finalize: gridDim.y indexes the realization.
+template <typename T>
+__global__ void finalize_batched_kernel(FinalizeBatch fb, int64_t n_vals) {
+    const long long* __restrict__ ws = static_cast<const long long*>(fb.ws[blockIdx.y]);
+    T* __restrict__ out = static_cast<T*>(fb.out[blockIdx.y]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vals; i += stride) {
+        out[i] += fixed_to<T>(__ldcs(ws + i));
+    }
+}
+
 // ------------------------------------------------------------------------------- cells
 __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse, int fp64,
                                                          int doppler, Scat sc, int32_t* gate,
@@ -234,9 +382,9 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
         float cx, cy;
         chunk_ref(sc, chunk0, cx, cy);
         ItemF it[kItems];
-        items_split(m, r, cx, cy, base, sc.n, it);
-        const SampleF k = load_sample(make_split_const(m, pulse, cx, cy));
-        const Fp64Const k64 = make_fp64_const(m, pulse);
+        items_split(m, r, cx, cy, (float)m.area, base, sc.n, it);
+        const SampleF k = load_sample(make_split_const(m, m.p0, pulse, cx, cy, 0.f, 0.f));
+        const Fp64Const k64 = make_fp64_const(m, m.p0, pulse);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) {
             float re, im;
@@ -247,8 +395,8 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
         }
     } else {
         ItemD it[kItems];
-        items_fp64(m, r, it);
-        const Fp64Const k = make_fp64_const(m, pulse);
+        items_fp64(r, m.area, it);
+        const Fp64Const k = make_fp64_const(m, m.p0, pulse);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) {
             double re, im;
@@ -275,16 +423,18 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     float* __restrict__ grad_nrcs) {
     __shared__ SplitConst tab[kTab];
     __shared__ Fp64Const tab64[kTab];
+    __shared__ float s_red[2];
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
     const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
-    float cx, cy;
+    float cx, cy, lmax, vmax;
     chunk_ref(sc, chunk0, cx, cy);
     ItemF it[kItems];
     float sig[kItems], xo[kItems], yo[kItems];
     {
         Raw r;
         load_raw(sc, base, r);
-        items_split(m, r, cx, cy, base, sc.n, it);
+        items_split(m, r, cx, cy, (float)m.area, base, sc.n, it);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) { sig[q] = r.s[q]; xo[q] = r.x[q]; yo[q] = r.y[q]; }
     }
@@ -297,11 +447,12 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
         __syncthreads();
         if (threadIdx.x < nb) {
             const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
-            tab[threadIdx.x] = make_split_const(m, pulse, cx, cy);
-            tab64[threadIdx.x] = make_fp64_const(m, pulse);
+            tab[threadIdx.x] = make_split_const(m, m.p0, pulse, cx, cy, lmax, vmax);
+            tab64[threadIdx.x] = make_fp64_const(m, m.p0, pulse);
         }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
+            if (!sample_active(tab[j])) continue;
             const int s = sb + j;
             const SampleF k = load_sample(tab[j]);
 #pragma unroll
@@ -335,14 +486,18 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
     Model m, Schedule sch, Scat sc, const double2* __restrict__ G, float* __restrict__ grad_z,
     float* __restrict__ grad_nrcs) {
     __shared__ Fp64Const tab[kTab];
+    __shared__ float s_red[2];
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
     const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
+    float cx, cy, lmax, vmax;
+    chunk_ref(sc, chunk0, cx, cy);
     ItemD it[kItems];
     float sig[kItems];
     {
         Raw r;
         load_raw(sc, base, r);
-        items_fp64(m, r, it);
+        items_fp64(r, m.area, it);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) sig[q] = r.s[q];
     }
@@ -353,9 +508,14 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
     for (int sb = 0; sb < sch.n_samples; sb += kTab) {
         const int nb = min(kTab, sch.n_samples - sb);
         __syncthreads();
-        if (threadIdx.x < nb) tab[threadIdx.x] = make_fp64_const(m, sample_pulse(sch, sb + threadIdx.x));
+        if (threadIdx.x < nb) {
+            Fp64Const k = make_fp64_const(m, m.p0, sample_pulse(sch, sb + threadIdx.x));
+            k.active = fp64_active(m, k, cx, cy, lmax, vmax);
+            tab[threadIdx.x] = k;
+        }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
+            if (!tab[j].active) continue;
             const int s = sb + j;
             const Fp64Const& k = tab[j];
 #pragma unroll
@@ -396,6 +556,18 @@ cudaError_t launch_accumulate(const Model& m, const Schedule& sch, const Scat& s
     return cudaGetLastError();
 }
 
+cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const BatchParams& bp,
+                                      bool fp64, bool doppler, dim3 grid, cudaStream_t stream) {
+    if (fp64) {
+        if (doppler) accumulate_fp64_batched_kernel<true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        else accumulate_fp64_batched_kernel<false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+    } else {
+        if (doppler) accumulate_split_batched_kernel<true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        else accumulate_split_batched_kernel<false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const void* ws, void* out, int64_t n_vals, bool fp64,
                             int n_sms, cudaStream_t stream) {
     const int threads = 256;
@@ -407,6 +579,20 @@ cudaError_t launch_finalize(const void* ws, void* out, int64_t n_vals, bool fp64
         static_cast<const long long*>(ws), static_cast<double*>(out), n_vals);
     else finalize_kernel<float><<<(unsigned)blocks, threads, 0, stream>>>(
         static_cast<const long long*>(ws), static_cast<float*>(out), n_vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t n_vals, bool fp64,
+                                    int n_sms, cudaStream_t stream) {
+    const int threads = 256;
+    int64_t blocks = (n_vals + threads - 1) / threads;
+    int64_t cap = ((int64_t)n_sms * 8 + n_real - 1) / n_real;
+    if (cap < 1) cap = 1;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    const dim3 grid((unsigned)blocks, (unsigned)n_real);
+    if (fp64) finalize_batched_kernel<double><<<grid, threads, 0, stream>>>(fb, n_vals);
+    else finalize_batched_kernel<float><<<grid, threads, 0, stream>>>(fb, n_vals);
     return cudaGetLastError();
 }
 

@@ -76,6 +76,30 @@ struct Scat {
     int pad;
 };
 
+// Many scatterer sets (realizations of the same track) in one launch.  Per-set data ride
+// in the kernel parameters (up to kMaxBatch sets per launch, 11.5 KB).
+constexpr int kMaxBatch = 96;
+
+struct BatchEntry {
+    Scat sc;
+    double p0[3];              // platform at t = 0 relative to this set's origin
+    int64_t chunk_begin;       // first global chunk (CTA) index of this set
+    unsigned long long* ws;    // this set's fixed-point workspace
+    float area;                // facet area
+    int pad;
+};
+
+struct BatchParams {
+    int n_real;
+    int pad;
+    BatchEntry e[kMaxBatch];
+};
+
+struct FinalizeBatch {
+    const void* ws[kMaxBatch];
+    void* out[kMaxBatch];
+};
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -86,8 +110,9 @@ __device__ __forceinline__ int clamp_floor(double v) {
     return (int)floor(fmax(fmin(v, 1.0e9), -1.0e9));
 }
 
-__device__ __forceinline__ double platform_coord(const Model& m, int i, double t) {
-    return fma(m.v[i], t, m.p0[i]);
+// Platform coordinate i at time t, p0 = platform at t = 0 relative to the scatterers' origin.
+__device__ __forceinline__ double platform_coord(const Model& m, const double* p0, int i, double t) {
+    return fma(m.v[i], t, p0[i]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -127,42 +152,38 @@ __device__ __forceinline__ double bin_coord_fp64(const Model& m, const GeomD& g,
     return fma(nu, (double)m.n_doppler, 0.5);
 }
 
-// FP64 index decisions (gate and pulse-pair Doppler bin) of one scatterer at time t.
-// Used by the FP64 path and to re-decide near-edge split-path items, so both paths take
-// bit-identical decisions.
-__device__ __forceinline__ void decide_fp64(const Model& m, double t, double x, double y, double z,
-                                            double vx, double vy, double vz, bool doppler,
-                                            int& g, int& kb, double& gc, double& bc) {
-    const double rref = fma(m.r_ref_rate, t, m.r_ref0);
-    const GeomD gd = geom_fp64(t, platform_coord(m, 0, t), platform_coord(m, 1, t),
-                               platform_coord(m, 2, t), rref, x, y, z, vx, vy, vz);
-    gc = fma(gd.dR, m.inv_gw, m.half_gates);
-    g = clamp_floor(gc);
-    kb = 0;
-    bc = 0.5;
-    if (doppler) {
-        bc = bin_coord_fp64(m, gd, vx, vy, vz);
-        kb = clamp_floor(bc) & (m.n_doppler - 1);
-    }
-}
-
 // Per-sample constants of the FP64 path.
 struct Fp64Const {
     double t, Px, Py, Pz;    // platform relative to the origin
     double rref;             // r_ref(t)
     double psiref;           // 2 r_ref / lambda - rint(.)  [cycles]
+    int active;              // 0: no scatterer of the CTA can fall in the range window
+    int pad;
 };
 
-__device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, int64_t pulse) {
+__device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, const double* p0,
+                                                     int64_t pulse) {
     Fp64Const k;
     k.t = (double)pulse * m.inv_prf;
-    k.Px = platform_coord(m, 0, k.t);
-    k.Py = platform_coord(m, 1, k.t);
-    k.Pz = platform_coord(m, 2, k.t);
+    k.Px = platform_coord(m, p0, 0, k.t);
+    k.Py = platform_coord(m, p0, 1, k.t);
+    k.Pz = platform_coord(m, p0, 2, k.t);
     k.rref = fma(m.r_ref_rate, k.t, m.r_ref0);
     const double psi = k.rref * m.two_over_lambda;
     k.psiref = psi - rint(psi);
+    k.active = 1;
+    k.pad = 0;
     return k;
+}
+
+// Culling bound of a CTA: every scatterer of the chunk lies within |l(t)| <= lmax + vmax |t|
+// of the reference point c, and |R - R_c| <= |l(t)| (triangle inequality), so its gate
+// coordinate lies within that distance / gate width of c's.  A sample whose band misses
+// the window [0, n_gates) has no contribution from the CTA.  G = gate coordinate of c.
+__device__ __forceinline__ int window_reachable(const Model& m, double G, double t, float lmax,
+                                                float vmax) {
+    const double B = ((double)lmax + (double)vmax * fabs(t)) * m.inv_gw + 2.0;
+    return (G + B >= 0.0 && G - B < (double)m.n_gates) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -174,7 +195,7 @@ struct __align__(16) SplitConst {
     float4 b;   // D / R_c (x, y, z), 1 / (2 R_c)
     float4 c;   // 1 / R_c, frac of the gate coordinate of c, 2 R_c / lambda - rint(.), log2 (r_ref/R_c)^2
     float4 d;   // beam_k / D_z^2, K0 = M . e_p as hi + lo (M = D + e_p/2), -n_doppler 2 / (lambda R_c)
-    float4 e;   // floor of the gate coordinate of c (int bits), unused x 3
+    float4 e;   // floor of the gate coordinate of c (int bits), active flag (int bits), unused x 2
 };
 
 // Register copy of one table entry.
@@ -182,6 +203,8 @@ struct SampleF {
     float t, Dx, Dy, Dz, ux, uy, uz, h, invRc, gfrac, psic, l2kappa, kq, K0hi, K0lo, kbin;
     int gint;
 };
+
+__device__ __forceinline__ int sample_active(const SplitConst& s) { return __float_as_int(s.e.y); }
 
 __device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
     const float4 a = s.a, b = s.b, c = s.c, d = s.d;
@@ -194,12 +217,13 @@ __device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
     return k;
 }
 
-__device__ __forceinline__ SplitConst make_split_const(const Model& m, int64_t pulse, float cx,
-                                                       float cy) {
+__device__ __forceinline__ SplitConst make_split_const(const Model& m, const double* p0,
+                                                       int64_t pulse, float cx, float cy,
+                                                       float lmax, float vmax) {
     const double t = (double)pulse * m.inv_prf;
-    const double Dx = platform_coord(m, 0, t) - (double)cx;
-    const double Dy = platform_coord(m, 1, t) - (double)cy;
-    const double Dz = platform_coord(m, 2, t);
+    const double Dx = platform_coord(m, p0, 0, t) - (double)cx;
+    const double Dy = platform_coord(m, p0, 1, t) - (double)cy;
+    const double Dz = platform_coord(m, p0, 2, t);
     const double Rc = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
     const double rref = fma(m.r_ref_rate, t, m.r_ref0);
     const double G = (Rc - rref) * m.inv_gw + m.half_gates;
@@ -217,7 +241,8 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, int64_t p
     k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, (float)(2.0 * log2(rref * inv)));
     k.d = make_float4((float)(m.beam_k / (Dz * Dz)), K0hi, (float)(K0 - (double)K0hi),
                       (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
-    k.e = make_float4(__int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)), 0.f, 0.f, 0.f);
+    k.e = make_float4(__int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)),
+                      __int_as_float(window_reachable(m, G, t, lmax, vmax)), 0.f, 0.f);
     return k;
 }
 

@@ -10,12 +10,18 @@ namespace rsim {
 struct Model;
 struct Schedule;
 struct Scat;
+struct BatchParams;
+struct FinalizeBatch;
 
 cudaError_t launch_accumulate(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
                               bool doppler, unsigned long long* ws, dim3 grid,
                               cudaStream_t stream);
 cudaError_t launch_finalize(const void* ws, void* out, int64_t n_vals, bool fp64, int n_sms,
                             cudaStream_t stream);
+cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const BatchParams& bp,
+                                      bool fp64, bool doppler, dim3 grid, cudaStream_t stream);
+cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t n_vals, bool fp64,
+                                    int n_sms, cudaStream_t stream);
 cudaError_t launch_cells(const Model& m, int64_t pulse, bool fp64, bool doppler, const Scat& sc,
                          int32_t* gate, int32_t* bin, double* gc, double* bc, cudaStream_t stream);
 cudaError_t launch_backward(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
