@@ -17,7 +17,7 @@
  *     scatterer heights and NRCS)                            -> rsim_*_backward
  *
  * Model (every function uses the same one):
- *   t_p = p / PRF; scatterer n at s(t) = origin + r_n + v_n t; platform at
+ *   t_p = p / PRF; scatterer n at s(t) = origin + r_n + v_n (t - t0); platform at
  *   P(t) = p0 + v t; d = P - s; R = |d|; range-window reference
  *   r_ref(t) = r_ref0 + r_ref_rate t;
  *   gate = floor((R - r_ref) / gate_width + n_gates / 2), dropped unless
@@ -117,12 +117,16 @@ typedef struct {
 } rsim_platform;
 
 /* Scatterer set, structure of arrays of n float32 DEVICE arrays: positions relative
- * to origin (m), velocities (m/s), NRCS (linear, >= 0).  facet_area_m2 > 0. */
+ * to origin (m) at the epoch t0 (s), velocities (m/s), NRCS (linear, >= 0); the scatterer
+ * moves as s(t) = origin + r + v (t - t0).  facet_area_m2 > 0.  Give the state at an epoch
+ * near the pulses simulated (the surface of Algorithm 1's update_simulation at that time):
+ * RSIM_SPLIT carries |r - c + v (t - t0)| in FP32. */
 typedef struct {
     int64_t n;
     const float *x, *y, *z, *vx, *vy, *vz, *nrcs;
     double origin[3];
     double facet_area_m2;
+    double t0;
 } rsim_scatterers;
 
 /* Library version (RSIM_ABI_VERSION). */

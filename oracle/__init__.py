@@ -68,7 +68,7 @@ _IP = ctypes.POINTER(ctypes.c_int32)
 class _Scene(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("x", _FP), ("y", _FP), ("z", _FP), ("vx", _FP),
                 ("vy", _FP), ("vz", _FP), ("nrcs", _FP), ("origin", ctypes.c_double * 3),
-                ("area", ctypes.c_double)]
+                ("area", ctypes.c_double), ("t0", ctypes.c_double)]
 
 
 def _radar(r) -> _Radar:
@@ -91,7 +91,8 @@ def _scene(s):
         if a.size != n:
             raise ValueError("scene arrays differ in length")
     sc = _Scene(n, *[a.ctypes.data_as(_FP) for a in arrs],
-                (ctypes.c_double * 3)(*s.get("origin", (0.0, 0.0, 0.0))), float(s.get("area", 1.0)))
+                (ctypes.c_double * 3)(*s.get("origin", (0.0, 0.0, 0.0))), float(s.get("area", 1.0)),
+                float(s.get("t0", 0.0)))
     return sc, arrs  # keep arrays alive
 
 

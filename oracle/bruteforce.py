@@ -26,8 +26,9 @@ def _scene_arrays(scene):
 def echo(radar, platform, scene, t):
     """Complex amplitude, range excess and range of every scatterer at time t."""
     f, o, area = _scene_arrays(scene)
-    pos = np.stack([o[0] + f["x"] + f["vx"] * t, o[1] + f["y"] + f["vy"] * t,
-                    o[2] + f["z"] + f["vz"] * t])
+    ts = t - float(scene.get("t0", 0.0))   # the state is given at epoch t0
+    pos = np.stack([o[0] + f["x"] + f["vx"] * ts, o[1] + f["y"] + f["vy"] * ts,
+                    o[2] + f["z"] + f["vz"] * ts])
     plat = np.asarray(platform.p0, dtype=np.float64) + np.asarray(platform.v, dtype=np.float64) * t
     d = plat[:, None] - pos
     horiz = np.hypot(d[0], d[1])

@@ -16,7 +16,8 @@
  * Definitions (paper section / equation, and the reading taken where the paper
  * is silent):
  *   t_p      = p / PRF                                   (stop-and-hop)
- *   s(t)     = O + r + v t,  P(t) = p0 + V t,  d = P - s   (Alg. 1 update_simulation, linear kinematics)
+ *   s(t)     = O + r + v (t - t0),  P(t) = p0 + V t,  d = P - s   (Alg. 1 update_simulation, linear
+ *              kinematics from the state given at epoch t0)
  *   R        = |d|,  dR = R - r_ref(t)
  *   theta    = atan2(|d_xy|, d_z)                          (nadir-pointing antenna)
  *   a        = sqrt(sigma A) exp(-2 ln2 theta^2/theta_b^2) (r_ref/R)^2   (radar equation at facet level, Sec. II.A)
@@ -62,6 +63,7 @@ typedef struct {
     const float *x, *y, *z, *vx, *vy, *vz, *nrcs;
     double origin[3];
     double area;
+    double t0;   /* epoch of the state: s(t) = O + r + v (t - t0) */
 } or_scene;
 
 typedef struct {
@@ -90,9 +92,10 @@ int or_get_threads(void) {
  * scatterers_range() and scatterers_complex_amplitudes() of Algorithm 1). */
 static void echo_at(const or_radar *rd, const or_platform *pf, const or_scene *sc,
                     int64_t n, double t, or_echo *e) {
-    double sx = sc->origin[0] + (double)sc->x[n] + (double)sc->vx[n] * t;
-    double sy = sc->origin[1] + (double)sc->y[n] + (double)sc->vy[n] * t;
-    double sz = sc->origin[2] + (double)sc->z[n] + (double)sc->vz[n] * t;
+    double ts = t - sc->t0;
+    double sx = sc->origin[0] + (double)sc->x[n] + (double)sc->vx[n] * ts;
+    double sy = sc->origin[1] + (double)sc->y[n] + (double)sc->vy[n] * ts;
+    double sz = sc->origin[2] + (double)sc->z[n] + (double)sc->vz[n] * ts;
     double px = pf->p0[0] + pf->v[0] * t;
     double py = pf->p0[1] + pf->v[1] * t;
     double pz = pf->p0[2] + pf->v[2] * t;

@@ -57,9 +57,12 @@ class Platform:
 
 
 class Scatterers:
-    """Structure-of-arrays scatterer set on a CUDA device (float32, contiguous)."""
+    """Structure-of-arrays scatterer set on a CUDA device (float32, contiguous).
 
-    def __init__(self, x, y, z, vx, vy, vz, nrcs, origin=(0.0, 0.0, 0.0), area=1.0):
+    Positions are relative to ``origin`` at the epoch ``t0`` (seconds); a scatterer moves as
+    origin + r + v (t - t0)."""
+
+    def __init__(self, x, y, z, vx, vy, vz, nrcs, origin=(0.0, 0.0, 0.0), area=1.0, t0=0.0):
         arrs = [x, y, z, vx, vy, vz, nrcs]
         n = arrs[0].numel()
         for a in arrs:
@@ -70,17 +73,19 @@ class Scatterers:
         self.x, self.y, self.z, self.vx, self.vy, self.vz, self.nrcs = arrs
         self.origin = tuple(float(o) for o in origin)
         self.area = float(area)
+        self.t0 = float(t0)
 
     @classmethod
     def from_arrays(cls, d, device="cuda") -> "Scatterers":
         """Copy a dict of arrays (numpy or torch; keys x, y, z, vx, vy, vz, nrcs,
         optional origin and area) to ``device``."""
         t = [torch.as_tensor(d[k]).to(device=device, dtype=torch.float32).contiguous() for k in _KEYS]
-        return cls(*t, origin=d.get("origin", (0.0, 0.0, 0.0)), area=d.get("area", 1.0))
+        return cls(*t, origin=d.get("origin", (0.0, 0.0, 0.0)), area=d.get("area", 1.0),
+                   t0=d.get("t0", 0.0))
 
     def replace(self, **kw) -> "Scatterers":
         arrs = {k: kw.get(k, getattr(self, k)) for k in _KEYS}
-        return Scatterers(**arrs, origin=self.origin, area=self.area)
+        return Scatterers(**arrs, origin=self.origin, area=self.area, t0=self.t0)
 
     @property
     def n(self) -> int:
@@ -92,7 +97,7 @@ class Scatterers:
 
     def c_struct(self) -> _lib.Scatterers:
         return _lib.Scatterers(self.n, *[getattr(self, k).data_ptr() for k in _KEYS],
-                               (ctypes.c_double * 3)(*self.origin), self.area)
+                               (ctypes.c_double * 3)(*self.origin), self.area, self.t0)
 
 
 def version() -> int:

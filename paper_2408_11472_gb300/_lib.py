@@ -40,7 +40,8 @@ class Platform(ctypes.Structure):
 class Scatterers(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
                                           ("x", "y", "z", "vx", "vy", "vz", "nrcs")] + [
-        ("origin", ctypes.c_double * 3), ("facet_area_m2", ctypes.c_double)]
+        ("origin", ctypes.c_double * 3), ("facet_area_m2", ctypes.c_double),
+        ("t0", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

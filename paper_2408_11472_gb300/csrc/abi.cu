@@ -79,6 +79,7 @@ rsim_status check_scat(const rsim_scatterers* s) {
         }
     }
     if (!finite_pos(s->facet_area_m2)) return fail(RSIM_ERR_INVALID_ARG, "facet_area_m2 must be > 0");
+    if (!std::isfinite(s->t0)) return fail(RSIM_ERR_INVALID_ARG, "t0 must be finite");
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(s->origin[i])) return fail(RSIM_ERR_INVALID_ARG, "origin must be finite");
     return RSIM_OK;
@@ -128,6 +129,7 @@ rsim::Scat make_scat(const rsim_scatterers* s) {
     sc.x = s->x; sc.y = s->y; sc.z = s->z;
     sc.vx = s->vx; sc.vy = s->vy; sc.vz = s->vz; sc.nrcs = s->nrcs;
     sc.n = s->n;
+    sc.t0 = s->t0;
     const float* p[7] = {s->x, s->y, s->z, s->vx, s->vy, s->vz, s->nrcs};
     int vec = 1;
     for (int i = 0; i < 7; ++i) vec &= aligned(p[i], 16) ? 1 : 0;

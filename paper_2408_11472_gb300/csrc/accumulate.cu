@@ -167,8 +167,8 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
         __syncthreads();
         if (threadIdx.x < nb) {
             const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
-            tab[threadIdx.x] = make_split_const(m, cx_.p0, pulse, cx, cy, lmax, vmax);
-            tab64[threadIdx.x] = make_fp64_const(m, cx_.p0, pulse);
+            tab[threadIdx.x] = make_split_const(m, cx_.p0, sc.t0, pulse, cx, cy, lmax, vmax);
+            tab64[threadIdx.x] = make_fp64_const(m, cx_.p0, sc.t0, pulse);
         }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
@@ -233,7 +233,7 @@ __device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Sche
         const int nb = min(kTab, s_end - sb);
         __syncthreads();
         if (threadIdx.x < nb) {
-            Fp64Const k = make_fp64_const(m, cx_.p0, sample_pulse(sch, sb + threadIdx.x));
+            Fp64Const k = make_fp64_const(m, cx_.p0, sc.t0, sample_pulse(sch, sb + threadIdx.x));
             k.active = fp64_active(m, k, cx, cy, lmax, vmax);
             tab[threadIdx.x] = k;
         }
@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
         chunk_ref(sc, chunk0, cx, cy);
         ItemF it[kItems];
         items_split(m, r, cx, cy, (float)m.area, base, sc.n, it);
-        const SampleF k = load_sample(make_split_const(m, m.p0, pulse, cx, cy, 0.f, 0.f));
-        const Fp64Const k64 = make_fp64_const(m, m.p0, pulse);
+        const SampleF k = load_sample(make_split_const(m, m.p0, sc.t0, pulse, cx, cy, 0.f, 0.f));
+        const Fp64Const k64 = make_fp64_const(m, m.p0, sc.t0, pulse);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) {
             float re, im;
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
     } else {
         ItemD it[kItems];
         items_fp64(r, m.area, it);
-        const Fp64Const k = make_fp64_const(m, m.p0, pulse);
+        const Fp64Const k = make_fp64_const(m, m.p0, sc.t0, pulse);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) {
             double re, im;
@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
         __syncthreads();
         if (threadIdx.x < nb) {
             const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
-            tab[threadIdx.x] = make_split_const(m, m.p0, pulse, cx, cy, lmax, vmax);
-            tab64[threadIdx.x] = make_fp64_const(m, m.p0, pulse);
+            tab[threadIdx.x] = make_split_const(m, m.p0, sc.t0, pulse, cx, cy, lmax, vmax);
+            tab64[threadIdx.x] = make_fp64_const(m, m.p0, sc.t0, pulse);
         }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
         const int nb = min(kTab, sch.n_samples - sb);
         __syncthreads();
         if (threadIdx.x < nb) {
-            Fp64Const k = make_fp64_const(m, m.p0, sample_pulse(sch, sb + threadIdx.x));
+            Fp64Const k = make_fp64_const(m, m.p0, sc.t0, sample_pulse(sch, sb + threadIdx.x));
             k.active = fp64_active(m, k, cx, cy, lmax, vmax);
             tab[threadIdx.x] = k;
         }

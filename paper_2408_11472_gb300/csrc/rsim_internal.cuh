@@ -72,7 +72,8 @@ struct Schedule {
 struct Scat {
     const float *x, *y, *z, *vx, *vy, *vz, *nrcs;
     int64_t n;
-    int vec4;  // all arrays 16-byte aligned: load 4 consecutive scatterers as float4
+    double t0;  // epoch of the state: s(t) = origin + r + v (t - t0)
+    int vec4;   // all arrays 16-byte aligned: load 4 consecutive scatterers as float4
     int pad;
 };
 
@@ -154,21 +155,23 @@ __device__ __forceinline__ double bin_coord_fp64(const Model& m, const GeomD& g,
 
 // Per-sample constants of the FP64 path.
 struct Fp64Const {
-    double t, Px, Py, Pz;    // platform relative to the origin
-    double rref;             // r_ref(t)
+    double t;                // scatterer time since the set's epoch, t_pulse - t0
+    double Px, Py, Pz;       // platform at t_pulse relative to the origin
+    double rref;             // r_ref(t_pulse)
     double psiref;           // 2 r_ref / lambda - rint(.)  [cycles]
     int active;              // 0: no scatterer of the CTA can fall in the range window
     int pad;
 };
 
-__device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, const double* p0,
+__device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, const double* p0, double t0,
                                                      int64_t pulse) {
     Fp64Const k;
-    k.t = (double)pulse * m.inv_prf;
-    k.Px = platform_coord(m, p0, 0, k.t);
-    k.Py = platform_coord(m, p0, 1, k.t);
-    k.Pz = platform_coord(m, p0, 2, k.t);
-    k.rref = fma(m.r_ref_rate, k.t, m.r_ref0);
+    const double tp = (double)pulse * m.inv_prf;
+    k.t = tp - t0;
+    k.Px = platform_coord(m, p0, 0, tp);
+    k.Py = platform_coord(m, p0, 1, tp);
+    k.Pz = platform_coord(m, p0, 2, tp);
+    k.rref = fma(m.r_ref_rate, tp, m.r_ref0);
     const double psi = k.rref * m.two_over_lambda;
     k.psiref = psi - rint(psi);
     k.active = 1;
@@ -177,6 +180,7 @@ __device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, const doubl
 }
 
 // Culling bound of a CTA: every scatterer of the chunk lies within |l(t)| <= lmax + vmax |t|
+// (t counted from the set's epoch)
 // of the reference point c, and |R - R_c| <= |l(t)| (triangle inequality), so its gate
 // coordinate lies within that distance / gate width of c's.  A sample whose band misses
 // the window [0, n_gates) has no contribution from the CTA.  G = gate coordinate of c.
@@ -191,7 +195,7 @@ __device__ __forceinline__ int window_reachable(const Model& m, double G, double
 // CTA and sample, rounded to FP32 and packed for 128-bit shared-memory loads.
 // D = P(t) - origin - c, R_c = |D|, e_p = platform displacement over one PRI.
 struct __align__(16) SplitConst {
-    float4 a;   // t, D_x, D_y, D_z
+    float4 a;   // t - t0 (scatterer time since the set's epoch), D_x, D_y, D_z
     float4 b;   // D / R_c (x, y, z), 1 / (2 R_c)
     float4 c;   // 1 / R_c, frac of the gate coordinate of c, 2 R_c / lambda - rint(.), log2 (r_ref/R_c)^2
     float4 d;   // beam_k / D_z^2, K0 = M . e_p as hi + lo (M = D + e_p/2), -n_doppler 2 / (lambda R_c)
@@ -218,9 +222,10 @@ __device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
 }
 
 __device__ __forceinline__ SplitConst make_split_const(const Model& m, const double* p0,
-                                                       int64_t pulse, float cx, float cy,
-                                                       float lmax, float vmax) {
+                                                       double t0, int64_t pulse, float cx,
+                                                       float cy, float lmax, float vmax) {
     const double t = (double)pulse * m.inv_prf;
+    const double ts = t - t0;
     const double Dx = platform_coord(m, p0, 0, t) - (double)cx;
     const double Dy = platform_coord(m, p0, 1, t) - (double)cy;
     const double Dz = platform_coord(m, p0, 2, t);
@@ -236,13 +241,13 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, const dou
     const double K0 = (Dx + 0.5 * epx) * epx + (Dy + 0.5 * epy) * epy + (Dz + 0.5 * epz) * epz;
     const float K0hi = (float)K0;
     SplitConst k;
-    k.a = make_float4((float)t, (float)Dx, (float)Dy, (float)Dz);
+    k.a = make_float4((float)ts, (float)Dx, (float)Dy, (float)Dz);
     k.b = make_float4((float)(Dx * inv), (float)(Dy * inv), (float)(Dz * inv), (float)(0.5 * inv));
     k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, (float)(2.0 * log2(rref * inv)));
     k.d = make_float4((float)(m.beam_k / (Dz * Dz)), K0hi, (float)(K0 - (double)K0hi),
                       (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
     k.e = make_float4(__int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)),
-                      __int_as_float(window_reachable(m, G, t, lmax, vmax)), 0.f, 0.f);
+                      __int_as_float(window_reachable(m, G, ts, lmax, vmax)), 0.f, 0.f);
     return k;
 }
 

@@ -64,6 +64,7 @@ def test_culling_on_a_long_track(rsim, orc, precision):
     P = 257_143
     pf = sg.nadir_track(P)
     sc = sg.sea_surface(96, 17)
+    sc["t0"] = P / (2 * rd.prf_hz)     # surface state given at the nadir crossing
     dev = rsim.Scatterers.from_arrays(sc)
     nf, nd = 64, 64
     # the scene enters the range window about 350 updates (1.2 s, 8.7 km) before nadir:

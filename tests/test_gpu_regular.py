@@ -139,6 +139,7 @@ def test_long_track_and_moving_window(rsim, orc):
     pf0 = sg.nadir_track(P)
     pf = sg.PlatformParams(p0=pf0.p0, v=pf0.v, r_ref0=pf0.r_ref0 - 0.3, r_ref_rate=0.05)
     sc = sg.sea_surface(96, 6)
+    sc["t0"] = P / (2 * rd.prf_hz) - 0.25   # surface state given a quarter second before
     dev = rsim.Scatterers.from_arrays(sc)
     p0 = P // 2 - 3
     for precision in PRECISIONS:
