@@ -69,23 +69,29 @@ __device__ __forceinline__ void chunk_ref(const Scat& sc, int64_t chunk0, float&
     cy = __ldg(sc.y + mid);
 }
 
+__device__ __forceinline__ ItemF item_split(const Model& m, float x, float y, float z, float vx,
+                                            float vy, float vz, float nrcs, float cx, float cy,
+                                            float area) {
+    ItemF it;
+    it.lx0 = x - cx;
+    it.ly0 = y - cy;
+    it.z = z;
+    it.vx = vx;
+    it.vy = vy;
+    it.vz = vz;
+    it.amp0 = sqrtf(nrcs * area);
+    const float epv = fmaf(m.ep[0], vx, fmaf(m.ep[1], vy, m.ep[2] * vz));
+    const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    it.c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
+    return it;
+}
+
 __device__ __forceinline__ void items_split(const Model& m, const Raw& r, float cx, float cy,
-                                            float area, int64_t base, int64_t n,
-                                            ItemF (&it)[kItems]) {
+                                            float area, ItemF (&it)[kItems]) {
 #pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-        it[q].lx0 = r.x[q] - cx;
-        it[q].ly0 = r.y[q] - cy;
-        it[q].z = r.z[q];
-        it[q].vx = r.vx[q];
-        it[q].vy = r.vy[q];
-        it[q].vz = r.vz[q];
-        it[q].amp0 = sqrtf(r.s[q] * area);
-        const float epv = fmaf(m.ep[0], r.vx[q], fmaf(m.ep[1], r.vy[q], m.ep[2] * r.vz[q]));
-        const float vv = fmaf(r.vx[q], r.vx[q], fmaf(r.vy[q], r.vy[q], r.vz[q] * r.vz[q]));
-        it[q].c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
-        it[q].ok = (base + q < n) ? 1 : 0;
-    }
+    for (int q = 0; q < kItems; ++q)
+        it[q] = item_split(m, r.x[q], r.y[q], r.z[q], r.vx[q], r.vy[q], r.vz[q], r.s[q], cx, cy,
+                           area);
 }
 
 __device__ __forceinline__ void items_fp64(const Raw& r, double area, ItemD (&it)[kItems]) {
@@ -105,7 +111,7 @@ __device__ __forceinline__ void items_fp64(const Raw& r, double area, ItemD (&it
 // lmax >= max |r - c|, vmax >= max |v| over the real (non-padding) items, enlarged so that
 // FP32 rounding of the norms cannot make the bound too tight.
 __device__ __forceinline__ void chunk_bounds(const Raw& r, float cx, float cy, int64_t base,
-                                             int64_t n, float* s_red, float& lmax, float& vmax) {
+                                             int64_t n, float* s_red) {
     float l = 0.f, v = 0.f;
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
@@ -125,22 +131,79 @@ __device__ __forceinline__ void chunk_bounds(const Raw& r, float cx, float cy, i
         atomicMax(reinterpret_cast<unsigned*>(s_red + 1), vb);
     }
     __syncthreads();
-    lmax = s_red[0] * (1.0f + 1e-6f) + 1e-3f;
-    vmax = s_red[1] * (1.0f + 1e-6f);
+    if (threadIdx.x == 0) {
+        s_red[0] = s_red[0] * (1.0f + 1e-6f) + 1e-3f;
+        s_red[1] = s_red[1] * (1.0f + 1e-6f);
+    }
+    // the table builders read s_red after the next barrier
 }
 
 __device__ __forceinline__ int64_t sample_pulse(const Schedule& sch, int s) {
     return sch.pulse_base + (int64_t)s * sch.pulse_stride;
 }
 
+// Compaction of one block of samples: thread j < nb holds sample j and whether the CTA's
+// scatterers can reach the range window there.  Returns how many can (CTA-uniform) and sets
+// slot to this thread's place among them, in sample order.  s_cnt: one int per warp.
+// Every thread of the CTA calls this (it holds a barrier).
+__device__ __forceinline__ int compact_samples(bool act, int* s_cnt, int& slot) {
+    constexpr int kWarps = kThreads / 32;
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) s_cnt[w] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) {
+        const int c = s_cnt[i];
+        before += (i < w) ? c : 0;
+        total += c;
+    }
+    slot = before + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+    return total;
+}
+
 // One CTA's work on one scatterer set: chunk starting at chunk0, samples [s_begin, s_end).
+// sc points into kernel-parameter space (a single set's parameter, or a batch entry), so the
+// set's pointers are read from the constant bank where needed instead of held in registers.
 struct ChunkCtx {
-    Scat sc;
+    const Scat* sc;
     const double* p0;   // platform at t = 0 relative to this set's origin
     float area;
     int64_t chunk0;
     unsigned long long* ws;
 };
+
+// Deferred exact evaluations.  An item whose fast evaluation is flagged (coordinate within
+// rounding of a cell edge, or far off nadir) leaves the warp's merged sum and is queued
+// (chunk item index | table slot << 16) in its warp's shared-memory queue; the warp later
+// re-evaluates each queued item exactly and adds it to the workspace on its own.  Keeping
+// that rare, register-hungry path out of the per-sample loop keeps the loop within the
+// register budget.  Every contribution is added in fixed point, so the split between
+// merged and single additions does not change the result's determinism.
+constexpr int kQueue = 256;  // entries per warp; flushed before it can overflow
+
+template <bool DOPPLER>
+__device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t chunk0, float cx,
+                                         float cy, float area, const SplitConst* tab,
+                                         const Fp64Const* tab64, const int* queue, int n) {
+    for (int e = threadIdx.x & 31; e < n; e += 32) {
+        const int code = queue[e];
+        const int i = code & 0xffff, j = code >> 16;
+        const int64_t idx = chunk0 + i;
+        if (idx >= sc.n) continue;  // padding items carry no amplitude
+        const float x = __ldg(sc.x + idx), y = __ldg(sc.y + idx);
+        const ItemF it = item_split(m, x, y, __ldg(sc.z + idx), __ldg(sc.vx + idx),
+                                    __ldg(sc.vy + idx), __ldg(sc.vz + idx), __ldg(sc.nrcs + idx),
+                                    cx, cy, area);
+        const SampleF k = load_sample(tab[j]);
+        float re, im;
+        int f;
+        const int key = eval_split<DOPPLER, true, false>(m, k, it, re, im, f, &tab64[j], x, y);
+        if (key >= 0) emit_cell(sample_out(tab[j]), key, re, im);
+    }
+    __syncwarp();
+}
 
 template <bool DOPPLER>
 __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Schedule& sch,
@@ -149,31 +212,42 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
     __shared__ SplitConst tab[kTab];
     __shared__ Fp64Const tab64[kTab];
     __shared__ float s_red[2];
+    __shared__ int s_cnt[kThreads / 32];
+    __shared__ int s_queue[kThreads / 32][kQueue];
     constexpr unsigned kFull = 0xffffffffu;
-    const Scat& sc = cx_.sc;
-    const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * kItems;
-    float cx, cy, lmax, vmax;
+    const Scat& sc = *cx_.sc;
+    const int lane = threadIdx.x & 31;
+    int* const queue = s_queue[threadIdx.x >> 5];
+    float cx, cy;
     chunk_ref(sc, cx_.chunk0, cx, cy);
     ItemF it[kItems];
     {
+        const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * kItems;
         Raw r;
         load_raw(sc, base, r);
-        items_split(m, r, cx, cy, cx_.area, base, sc.n, it);
-        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
+        items_split(m, r, cx, cy, cx_.area, it);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red);
     }
     const int cells = m.n_gates * m.n_doppler;
     for (int sb = s_begin; sb < s_end; sb += kTab) {
         const int nb = min(kTab, s_end - sb);
         __syncthreads();
-        if (threadIdx.x < nb) {
-            const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
-            tab[threadIdx.x] = make_split_const(m, cx_.p0, sc.t0, pulse, cx, cy, lmax, vmax);
-            tab64[threadIdx.x] = make_fp64_const(m, cx_.p0, sc.t0, pulse);
+        // the table keeps only the samples the CTA can contribute to
+        const int s = sb + threadIdx.x;
+        const int64_t pulse = sample_pulse(sch, s);
+        const bool act = threadIdx.x < nb &&
+                         cta_reaches_window(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+        int slot;
+        const int na = compact_samples(act, s_cnt, slot);
+        if (act) {
+            SplitConst kc = make_split_const(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+            set_sample_slot(kc, s, cx_.ws + (int64_t)s * cells * 2);
+            tab[slot] = kc;
+            tab64[slot] = make_fp64_const(m, cx_.p0, sc.t0, pulse);
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            if (!sample_active(tab[j])) continue;  // CTA-uniform
-            const int s = sb + j;
+        int nq = 0;  // entries in this warp's queue (warp-uniform)
+        for (int j = 0; j < na; ++j) {
             const SampleF k = load_sample(tab[j]);
             int key[kItems];
             float re[kItems], im[kItems];
@@ -182,33 +256,32 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             for (int q = 0; q < kItems; ++q) {
                 int f;
                 key[q] = eval_split<DOPPLER, false, false>(m, k, it[q], re[q], im[q], f);
-                fl |= f << (2 * q);
+                if (f) key[q] = -1;  // deferred to the exact evaluation
+                fl |= (f != 0) << q;
             }
-            // rare: items near a cell edge or far off nadir, re-evaluated exactly
-            if (__any_sync(kFull, fl != 0)) {
+            if (__any_sync(kFull, fl != 0)) {  // rare: queue the flagged items
 #pragma unroll
                 for (int q = 0; q < kItems; ++q) {
-                    if ((fl >> (2 * q)) & 3) {
-                        int f;
-                        const bool in = it[q].ok != 0;  // padding items read nothing
-                        key[q] = eval_split<DOPPLER, true, false>(
-                            m, k, it[q], re[q], im[q], f, &tab64[j],
-                            in ? __ldg(sc.x + base + q) : 0.0f, in ? __ldg(sc.y + base + q) : 0.0f);
-                    }
+                    const bool mine = (fl >> q) & 1;
+                    const unsigned b = __ballot_sync(kFull, mine);
+                    if (mine)
+                        queue[nq + __popc(b & ((1u << lane) - 1u))] =
+                            (threadIdx.x * kItems + q) | (j << 16);
+                    nq += __popc(b);
                 }
             }
-            warp_reduce_emit<float, kItems>(key, re, im, cx_.ws + (int64_t)s * cells * 2);
+            warp_reduce_emit<float, kItems>(key, re, im, sample_out(tab[j]));
+            if (nq > kQueue - 32 * kItems) {  // room for one more sample's worth
+                __syncwarp();
+                flush_queue<DOPPLER>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
+                nq = 0;
+            }
+        }
+        if (nq > 0) {  // before the table is rebuilt
+            __syncwarp();
+            flush_queue<DOPPLER>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
         }
     }
-}
-
-// FP64 path: culling uses the same bound around the chunk's middle scatterer.
-__device__ __forceinline__ int fp64_active(const Model& m, const Fp64Const& k, float cx, float cy,
-                                           float lmax, float vmax) {
-    const double dx = k.Px - (double)cx, dy = k.Py - (double)cy, dz = k.Pz;
-    const double Rc = sqrt(dx * dx + dy * dy + dz * dz);
-    const double G = (Rc - k.rref) * m.inv_gw + m.half_gates;
-    return window_reachable(m, G, k.t, lmax, vmax);
 }
 
 template <bool DOPPLER>
@@ -217,31 +290,36 @@ __device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Sche
                                                       int s_end) {
     __shared__ Fp64Const tab[kTab];
     __shared__ float s_red[2];
-    const Scat& sc = cx_.sc;
+    __shared__ int s_cnt[kThreads / 32];
+    const Scat& sc = *cx_.sc;
     const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * kItems;
-    float cx, cy, lmax, vmax;
+    float cx, cy;
     chunk_ref(sc, cx_.chunk0, cx, cy);
     ItemD it[kItems];
     {
         Raw r;
         load_raw(sc, base, r);
         items_fp64(r, (double)cx_.area, it);
-        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red);
     }
     const int cells = m.n_gates * m.n_doppler;
     for (int sb = s_begin; sb < s_end; sb += kTab) {
         const int nb = min(kTab, s_end - sb);
         __syncthreads();
-        if (threadIdx.x < nb) {
-            Fp64Const k = make_fp64_const(m, cx_.p0, sc.t0, sample_pulse(sch, sb + threadIdx.x));
-            k.active = fp64_active(m, k, cx, cy, lmax, vmax);
-            tab[threadIdx.x] = k;
+        const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
+        const bool act = threadIdx.x < nb &&
+                         cta_reaches_window(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+        int slot;
+        const int na = compact_samples(act, s_cnt, slot);
+        if (act) {
+            Fp64Const kd = make_fp64_const(m, cx_.p0, sc.t0, pulse);
+            kd.index = sb + threadIdx.x;
+            tab[slot] = kd;
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            if (!tab[j].active) continue;  // CTA-uniform
-            const int s = sb + j;
+        for (int j = 0; j < na; ++j) {
             const Fp64Const& k = tab[j];
+            const int s = k.index;
             int key[kItems];
             double re[kItems], im[kItems];
 #pragma unroll
@@ -271,7 +349,7 @@ __device__ __forceinline__ int batch_find(const BatchParams& bp, int64_t chunk) 
 __device__ __forceinline__ ChunkCtx batch_ctx(const BatchParams& bp, int r, int64_t chunk) {
     const BatchEntry& e = bp.e[r];
     ChunkCtx c;
-    c.sc = e.sc;
+    c.sc = &e.sc;
     c.p0 = e.p0;
     c.area = e.area;
     c.chunk0 = (chunk - e.chunk_begin) * kChunk;
@@ -284,9 +362,10 @@ __device__ __forceinline__ ChunkCtx batch_ctx(const BatchParams& bp, int r, int6
 // ------------------------------------------------------------------------------- forward
 template <bool DOPPLER>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
-    Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
+    unsigned long long* __restrict__ ws) {
     ChunkCtx c;
-    c.sc = sc;
+    c.sc = &sc;
     c.p0 = m.p0;
     c.area = (float)m.area;
     c.chunk0 = (int64_t)blockIdx.x * kChunk;
@@ -298,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
 
 template <bool DOPPLER>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_batched_kernel(
-    Model m, Schedule sch, BatchParams bp) {
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ BatchParams bp) {
     const int r = batch_find(bp, blockIdx.x);
     const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);
     int s0, s1;
@@ -308,9 +387,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_batched
 
 template <bool DOPPLER>
 __global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
-    Model m, Schedule sch, Scat sc, unsigned long long* __restrict__ ws) {
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
+    unsigned long long* __restrict__ ws) {
     ChunkCtx c;
-    c.sc = sc;
+    c.sc = &sc;
     c.p0 = m.p0;
     c.area = (float)m.area;
     c.chunk0 = (int64_t)blockIdx.x * kChunk;
@@ -322,7 +402,7 @@ __global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
 
 template <bool DOPPLER>
 __global__ void __launch_bounds__(kThreads) accumulate_fp64_batched_kernel(
-    Model m, Schedule sch, BatchParams bp) {
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ BatchParams bp) {
     const int r = batch_find(bp, blockIdx.x);
     const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);
     int s0, s1;
@@ -382,7 +462,7 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
         float cx, cy;
         chunk_ref(sc, chunk0, cx, cy);
         ItemF it[kItems];
-        items_split(m, r, cx, cy, (float)m.area, base, sc.n, it);
+        items_split(m, r, cx, cy, (float)m.area, it);
         const SampleF k = load_sample(make_split_const(m, m.p0, sc.t0, pulse, cx, cy, 0.f, 0.f));
         const Fp64Const k64 = make_fp64_const(m, m.p0, sc.t0, pulse);
 #pragma unroll
@@ -424,17 +504,18 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     __shared__ SplitConst tab[kTab];
     __shared__ Fp64Const tab64[kTab];
     __shared__ float s_red[2];
+    __shared__ int s_cnt[kThreads / 32];
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
     const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
-    float cx, cy, lmax, vmax;
+    float cx, cy;
     chunk_ref(sc, chunk0, cx, cy);
     ItemF it[kItems];
     float sig[kItems], xo[kItems], yo[kItems];
     {
         Raw r;
         load_raw(sc, base, r);
-        items_split(m, r, cx, cy, (float)m.area, base, sc.n, it);
-        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
+        items_split(m, r, cx, cy, (float)m.area, it);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) { sig[q] = r.s[q]; xo[q] = r.x[q]; yo[q] = r.y[q]; }
     }
@@ -445,15 +526,21 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     for (int sb = 0; sb < sch.n_samples; sb += kTab) {
         const int nb = min(kTab, sch.n_samples - sb);
         __syncthreads();
-        if (threadIdx.x < nb) {
-            const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
-            tab[threadIdx.x] = make_split_const(m, m.p0, sc.t0, pulse, cx, cy, lmax, vmax);
-            tab64[threadIdx.x] = make_fp64_const(m, m.p0, sc.t0, pulse);
+        const int s = sb + threadIdx.x;
+        const int64_t pulse = sample_pulse(sch, s);
+        const bool act = threadIdx.x < nb &&
+                         cta_reaches_window(m, m.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+        int slot;
+        const int na = compact_samples(act, s_cnt, slot);
+        if (act) {
+            SplitConst kc = make_split_const(m, m.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+            set_sample_slot(kc, s, nullptr);
+            tab[slot] = kc;
+            tab64[slot] = make_fp64_const(m, m.p0, sc.t0, pulse);
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            if (!sample_active(tab[j])) continue;
-            const int s = sb + j;
+        for (int j = 0; j < na; ++j) {
+            const int s = sample_index(tab[j]);
             const SampleF k = load_sample(tab[j]);
 #pragma unroll
             for (int q = 0; q < kItems; ++q) {
@@ -487,9 +574,10 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
     float* __restrict__ grad_nrcs) {
     __shared__ Fp64Const tab[kTab];
     __shared__ float s_red[2];
+    __shared__ int s_cnt[kThreads / 32];
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
     const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
-    float cx, cy, lmax, vmax;
+    float cx, cy;
     chunk_ref(sc, chunk0, cx, cy);
     ItemD it[kItems];
     float sig[kItems];
@@ -497,7 +585,7 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
         Raw r;
         load_raw(sc, base, r);
         items_fp64(r, m.area, it);
-        chunk_bounds(r, cx, cy, base, sc.n, s_red, lmax, vmax);
+        chunk_bounds(r, cx, cy, base, sc.n, s_red);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) sig[q] = r.s[q];
     }
@@ -508,16 +596,20 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
     for (int sb = 0; sb < sch.n_samples; sb += kTab) {
         const int nb = min(kTab, sch.n_samples - sb);
         __syncthreads();
-        if (threadIdx.x < nb) {
-            Fp64Const k = make_fp64_const(m, m.p0, sc.t0, sample_pulse(sch, sb + threadIdx.x));
-            k.active = fp64_active(m, k, cx, cy, lmax, vmax);
-            tab[threadIdx.x] = k;
+        const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
+        const bool act = threadIdx.x < nb &&
+                         cta_reaches_window(m, m.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+        int slot;
+        const int na = compact_samples(act, s_cnt, slot);
+        if (act) {
+            Fp64Const kd = make_fp64_const(m, m.p0, sc.t0, pulse);
+            kd.index = sb + threadIdx.x;
+            tab[slot] = kd;
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            if (!tab[j].active) continue;
-            const int s = sb + j;
+        for (int j = 0; j < na; ++j) {
             const Fp64Const& k = tab[j];
+            const int s = k.index;
 #pragma unroll
             for (int q = 0; q < kItems; ++q) {
                 double re, im;

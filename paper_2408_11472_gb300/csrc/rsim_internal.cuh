@@ -21,7 +21,7 @@ namespace rsim {
 #define RSIM_ITEMS 4
 #endif
 #ifndef RSIM_MIN_BLOCKS
-#define RSIM_MIN_BLOCKS 5
+#define RSIM_MIN_BLOCKS 6
 #endif
 constexpr int kThreads = RSIM_THREADS;        // summation CTA size
 constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (1, 2, 4, 8)
@@ -160,7 +160,7 @@ struct Fp64Const {
     double rref;             // r_ref(t_pulse)
     double psiref;           // 2 r_ref / lambda - rint(.)  [cycles]
     int active;              // 0: no scatterer of the CTA can fall in the range window
-    int pad;
+    int index;               // sample index (set when the table is compacted)
 };
 
 __device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, const double* p0, double t0,
@@ -175,7 +175,7 @@ __device__ __forceinline__ Fp64Const make_fp64_const(const Model& m, const doubl
     const double psi = k.rref * m.two_over_lambda;
     k.psiref = psi - rint(psi);
     k.active = 1;
-    k.pad = 0;
+    k.index = 0;
     return k;
 }
 
@@ -190,6 +190,21 @@ __device__ __forceinline__ int window_reachable(const Model& m, double G, double
     return (G + B >= 0.0 && G - B < (double)m.n_gates) ? 1 : 0;
 }
 
+// Window test of a CTA at one pulse: G is the gate coordinate of its reference point
+// (cx, cy, 0) (the same value make_split_const computes).
+__device__ __forceinline__ int cta_reaches_window(const Model& m, const double* p0, double t0,
+                                                  int64_t pulse, float cx, float cy, float lmax,
+                                                  float vmax) {
+    const double t = (double)pulse * m.inv_prf;
+    const double Dx = platform_coord(m, p0, 0, t) - (double)cx;
+    const double Dy = platform_coord(m, p0, 1, t) - (double)cy;
+    const double Dz = platform_coord(m, p0, 2, t);
+    const double Rc = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
+    const double rref = fma(m.r_ref_rate, t, m.r_ref0);
+    const double G = (Rc - rref) * m.inv_gw + m.half_gates;
+    return window_reachable(m, G, t - t0, lmax, vmax);
+}
+
 // ---------------------------------------------------------------------------------------
 // Per (reference point c, sample) constants of the split path, computed in FP64 once per
 // CTA and sample, rounded to FP32 and packed for 128-bit shared-memory loads.
@@ -199,7 +214,8 @@ struct __align__(16) SplitConst {
     float4 b;   // D / R_c (x, y, z), 1 / (2 R_c)
     float4 c;   // 1 / R_c, frac of the gate coordinate of c, 2 R_c / lambda - rint(.), log2 (r_ref/R_c)^2
     float4 d;   // beam_k / D_z^2, K0 = M . e_p as hi + lo (M = D + e_p/2), -n_doppler 2 / (lambda R_c)
-    float4 e;   // floor of the gate coordinate of c (int bits), active flag (int bits), unused x 2
+    float4 e;   // floor of the gate coordinate of c (int bits); active flag, then the sample
+                // index (int bits); the sample's workspace slice (pointer bits, lo + hi)
 };
 
 // Register copy of one table entry.
@@ -209,6 +225,24 @@ struct SampleF {
 };
 
 __device__ __forceinline__ int sample_active(const SplitConst& s) { return __float_as_int(s.e.y); }
+__device__ __forceinline__ int sample_index(const SplitConst& s) { return __float_as_int(s.e.y); }
+
+// After the activity test: the entry carries its sample index and output slice instead.
+__device__ __forceinline__ void set_sample_slot(SplitConst& s, int index,
+                                                unsigned long long* out) {
+    const unsigned long long u = reinterpret_cast<unsigned long long>(out);
+    s.e.y = __int_as_float(index);
+    s.e.z = __uint_as_float((unsigned)(u & 0xffffffffull));
+    s.e.w = __uint_as_float((unsigned)(u >> 32));
+}
+
+// Workspace slice of a table entry (read where it is used, so no register holds it
+// across the evaluation).
+__device__ __forceinline__ unsigned long long* sample_out(const SplitConst& s) {
+    const float2 p = *reinterpret_cast<const float2*>(&s.e.z);
+    return reinterpret_cast<unsigned long long*>(
+        ((unsigned long long)__float_as_uint(p.y) << 32) | __float_as_uint(p.x));
+}
 
 __device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
     const float4 a = s.a, b = s.b, c = s.c, d = s.d;
@@ -255,8 +289,7 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, const dou
 // c1 = dt (e_p . v) - dt^2 |v|^2 / 2 is the part of the pulse-pair range change that depends
 // on the scatterer alone.
 struct ItemF {
-    float lx0, ly0, z, vx, vy, vz, amp0, c1;
-    int ok;  // 1 for a real scatterer, 0 for padding past the end of the set
+    float lx0, ly0, z, vx, vy, vz, amp0, c1;  // padding past the end of a set: amp0 = 0
 };
 
 // Quantities the adjoint needs besides C.
@@ -372,7 +405,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     }
     double gcd = (double)k.gint + (double)gcf;
     double bcd = (double)b - (double)m.n_doppler * rint((double)b / (double)m.n_doppler) + 0.5;
-    if (GENERAL && (fl & kFlagRefine) && it.ok) {
+    if (GENERAL && (fl & kFlagRefine)) {
         int g2, kb2;
         refine_fp64(m, *k64, (double)x_orig, (double)y_orig, (double)it.z, (double)it.vx,
                     (double)it.vy, (double)it.vz, DOPPLER, &g2, &kb2, &gcd, &bcd);
@@ -494,18 +527,28 @@ __device__ __forceinline__ long long to_fixed<float>(float v) { return fixed_fro
 template <>
 __device__ __forceinline__ long long to_fixed<double>(double v) { return fixed_from_f64(v); }
 
+// Fire-and-forget global reduction (no return value, so the warp does not wait for it).
+// The workspace is global memory; the address space is stated explicitly because the
+// pointer may come out of a shared-memory table, where the compiler cannot infer it.
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.global.add.u64 [%0], %1;"
+                 :
+                 : "l"((unsigned long long)__cvta_generic_to_global(p)), "l"(v)
+                 : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ void emit_cell(unsigned long long* __restrict__ base, int key, T re,
                                           T im) {
     const long long qr = to_fixed(re), qi = to_fixed(im);
-    if (qr) atomicAdd(base + 2 * (int64_t)key, (unsigned long long)qr);
-    if (qi) atomicAdd(base + 2 * (int64_t)key + 1, (unsigned long long)qi);
+    if (qr) red_add_u64(base + 2 * (int64_t)key, (unsigned long long)qr);
+    if (qi) red_add_u64(base + 2 * (int64_t)key + 1, (unsigned long long)qi);
 }
 
 template <typename T, int J>
 __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&re)[J],
-                                                 const T (&im)[J],
-                                                 unsigned long long* __restrict__ base) {
+                                               const T (&im)[J],
+                                               unsigned long long* __restrict__ base) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     // in-lane inclusive run sums; bit q of tails: a run ends at item q
@@ -575,5 +618,6 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
         }
     }
 }
+
 
 }  // namespace rsim
