@@ -163,7 +163,14 @@ def main():
     ap.add_argument("--L", type=int, default=None, help="surface side (default: 2048)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e / regular / FP64 / oracle legs (profiling runs)")
+    ap.add_argument("--config", type=int, default=None, choices=[0, 2, 3, 4],
+                    help="run another measurement configuration instead (bench_configs.py)")
     args = ap.parse_args()
+
+    if args.config is not None:
+        import bench_configs
+        print(json.dumps(bench_configs.run(args.config, args)), flush=True)
+        return
 
     rank, world, local = dist_env()
     c = sg.config(1)

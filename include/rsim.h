@@ -172,6 +172,15 @@ rsim_status rsim_doppler_accumulate(const rsim_radar *radar, const rsim_platform
 size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_gates,
                                    int32_t n_doppler);
 
+/* Launch plan of the batched scatterer pass.  Every choice gives bit-identical results;
+ * only the speed differs (see rsim_autotune_batched). */
+typedef struct {
+    int32_t sets_per_launch;   /* scatterer sets per launch, 1..96; 0 = 96 */
+    int32_t samples_per_group; /* updates handled by one CTA (the rest of the updates go to
+                                  further CTAs over the same scatterers); 0 = library's choice */
+    int32_t reserved[6];       /* must be 0 */
+} rsim_tuning;
+
 /* rsim_doppler_accumulate for n_real independent scatterer sets -- realizations of the same
  * track, as the ~100 realizations behind each SWH/SSH spectrum of Section IV.D -- in one
  * launch per group of up to 96 sets: every CTA of the launch takes a block of scatterers of
@@ -181,6 +190,8 @@ size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_
  * scats   : HOST array [n_real] of scatterer sets (device arrays; each its own origin/area);
  * spectra : HOST array [n_real] of DEVICE pointers, each [n_updates][n_gates][n_doppler]
  *           complex, accumulated (+=);
+ * tuning  : launch plan, or NULL for the library's choice (RSIM_ERR_INVALID_ARG when a
+ *           field is out of range);
  * workspace >= rsim_batched_workspace_size(n_real, n_updates, n_gates, n_doppler), 256-byte
  * aligned.  Capturable in a CUDA graph (memset + kernels only). */
 rsim_status rsim_doppler_accumulate_batched(const rsim_radar *radar,
@@ -188,8 +199,25 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar *radar,
                                             const rsim_scatterers *scats, int64_t update0,
                                             int32_t n_updates, int32_t n_fast, int32_t n_doppler,
                                             rsim_precision precision, void *const *spectra,
-                                            void *workspace, size_t workspace_bytes,
-                                            cudaStream_t stream);
+                                            const rsim_tuning *tuning, void *workspace,
+                                            size_t workspace_bytes, cudaStream_t stream);
+
+/* Autotuner of the batched scatterer pass: runs rsim_doppler_accumulate_batched with the
+ * same arguments under candidate launch plans (sets per launch in {96, 32, 8}, samples per
+ * group in {library's choice, n_updates, n_updates/2, /4, /8}, limited to what the call can
+ * use), times each with CUDA events on `stream` (one untimed run, then the median of
+ * `reps` >= 1 runs) and writes the fastest plan to *best and its time in ms to *best_ms
+ * (may be NULL).  Tune on a representative part of the job (e.g. a few dozen updates):
+ * the plan then applies to any update range of the same sets.
+ * SYNCHRONOUS: blocks until the runs finish; RSIM_ERR_UNSUPPORTED while `stream` is being
+ * captured into a graph.  The spectra receive unspecified values (accumulated several
+ * times): pass scratch buffers or zero them afterwards. */
+rsim_status rsim_autotune_batched(const rsim_radar *radar, const rsim_platform *platform,
+                                  int32_t n_real, const rsim_scatterers *scats, int64_t update0,
+                                  int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                  rsim_precision precision, void *const *spectra,
+                                  void *workspace, size_t workspace_bytes, int32_t reps,
+                                  rsim_tuning *best, double *best_ms, cudaStream_t stream);
 
 /* Fast-mode post-processing (Section III.B steps 2-4 with Eq. (1)): batched
  * n_doppler-point inverse FFT per gate of each spectrum, blend window, sum into
@@ -213,6 +241,16 @@ rsim_status rsim_scatterer_cells(const rsim_radar *radar, const rsim_platform *p
                                  const rsim_scatterers *scat, int64_t pulse, int32_t n_doppler,
                                  rsim_precision precision, int32_t *gate, int32_t *bin,
                                  double *gate_coord, double *bin_coord, cudaStream_t stream);
+
+/* Per-scatterer complex amplitude C_n(t_pulse) of the radar equation and two-way phase
+ * (Section II.A, Fig. 1 step 4; the model above), with the arithmetic of `precision`
+ * exactly as the summation entry points evaluate it, for every scatterer whether or not
+ * it falls in the range window.  For precision studies (phase and amplitude error of the
+ * split path against RSIM_FP64).
+ * contrib : [n] complex (complex64 for RSIM_SPLIT, complex128 for RSIM_FP64), OVERWRITTEN. */
+rsim_status rsim_scatterer_echo(const rsim_radar *radar, const rsim_platform *platform,
+                                const rsim_scatterers *scat, int64_t pulse,
+                                rsim_precision precision, void *contrib, cudaStream_t stream);
 
 /* Adjoint of rsim_synth_pulses (gradient convention dL/dRe + j dL/dIm):
  *   grad_spectra[s][g][k] = sum_m exp(-j 2 pi k m / n_doppler)

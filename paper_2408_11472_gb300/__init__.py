@@ -26,7 +26,9 @@ from ._lib import PRECISIONS, WINDOWS, RsimError
 __all__ = [
     "Radar", "Platform", "Scatterers", "RsimError", "workspace_size", "direct_sum",
     "doppler_accumulate", "doppler_accumulate_noalloc", "doppler_accumulate_batched",
-    "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "synth_pulses_backward",
+    "autotune_batched", "Tuning",
+    "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "scatterer_echo",
+    "synth_pulses_backward",
     "doppler_accumulate_backward", "direct_sum_backward", "spectra_range", "simulate_fast",
     "FastMode", "RegularMode", "version", "PRECISIONS", "WINDOWS",
 ]
@@ -201,28 +203,61 @@ def batched_workspace_size(n_real: int, n_samples: int, n_gates: int, n_doppler:
                                                     int(n_doppler)))
 
 
-def doppler_accumulate_batched(radar, platform, scats, update0: int, n_updates: int, n_fast: int,
-                               n_doppler: int, precision: str = "split", outs=None,
-                               workspace: Optional[torch.Tensor] = None, stream=None):
-    """doppler_accumulate for a list of independent scatterer sets (realizations of the same
-    track) in one launch per group of 96.  Returns the list of spectra (+= into ``outs``)."""
+Tuning = _lib.Tuning
+
+
+def _batched_args(radar, scats, n_updates, n_doppler, precision, outs, workspace):
     n_real = len(scats)
     shape = (n_updates, radar.n_gates, n_doppler)
     dev = scats[0].device if n_real else torch.device("cuda")
     if outs is None:
         outs = [torch.zeros(shape, dtype=_cdtype(precision), device=dev) for _ in range(n_real)]
+    if len(outs) != n_real:
+        raise ValueError("one output per scatterer set")
     for o in outs:
         _need(o, _cdtype(precision), shape, dev, "out")
     need = batched_workspace_size(n_real, n_updates, radar.n_gates, n_doppler)
     ws = _workspace(workspace, need, dev)
     arr = (_lib.Scatterers * max(n_real, 1))(*[s.c_struct() for s in scats])
     ptrs = (ctypes.c_void_p * max(n_real, 1))(*[o.data_ptr() for o in outs])
+    return outs, ws, arr, ptrs
+
+
+def doppler_accumulate_batched(radar, platform, scats, update0: int, n_updates: int, n_fast: int,
+                               n_doppler: int, precision: str = "split", outs=None,
+                               workspace: Optional[torch.Tensor] = None, stream=None,
+                               tuning: Optional[Tuning] = None):
+    """doppler_accumulate for a list of independent scatterer sets (realizations of the same
+    track) in one launch per group of sets.  ``tuning``: launch plan (``autotune_batched``),
+    None for the library's choice; every plan gives bit-identical spectra.  Returns the list
+    of spectra (+= into ``outs``)."""
+    outs, ws, arr, ptrs = _batched_args(radar, scats, n_updates, n_doppler, precision, outs,
+                                        workspace)
     rd, pf = _lib.make_radar(radar), _lib.make_platform(platform)
     _lib.check(_lib.lib.rsim_doppler_accumulate_batched(
-        ctypes.byref(rd), ctypes.byref(pf), n_real, arr, int(update0), int(n_updates), int(n_fast),
-        int(n_doppler), _prec(precision), ptrs, _ptr(ws), ws.numel() * ws.element_size(),
-        _stream(stream)))
+        ctypes.byref(rd), ctypes.byref(pf), len(scats), arr, int(update0), int(n_updates),
+        int(n_fast), int(n_doppler), _prec(precision), ptrs,
+        ctypes.byref(tuning) if tuning is not None else None, _ptr(ws),
+        ws.numel() * ws.element_size(), _stream(stream)))
     return outs
+
+
+def autotune_batched(radar, platform, scats, update0: int, n_updates: int, n_fast: int,
+                     n_doppler: int, precision: str = "split", reps: int = 3, outs=None,
+                     workspace: Optional[torch.Tensor] = None, stream=None):
+    """Time candidate launch plans of ``doppler_accumulate_batched`` on these arguments
+    (rsim_autotune_batched; synchronous) and return ``(tuning, ms)`` of the fastest.  The
+    spectra in ``outs`` (allocated when None) receive unspecified values."""
+    outs, ws, arr, ptrs = _batched_args(radar, scats, n_updates, n_doppler, precision, outs,
+                                        workspace)
+    rd, pf = _lib.make_radar(radar), _lib.make_platform(platform)
+    best, ms = Tuning(), ctypes.c_double(0.0)
+    _lib.check(_lib.lib.rsim_autotune_batched(
+        ctypes.byref(rd), ctypes.byref(pf), len(scats), arr, int(update0), int(n_updates),
+        int(n_fast), int(n_doppler), _prec(precision), ptrs, _ptr(ws),
+        ws.numel() * ws.element_size(), int(reps), ctypes.byref(best), ctypes.byref(ms),
+        _stream(stream)))
+    return best, float(ms.value)
 
 
 def _prec_of(t: torch.Tensor) -> str:
@@ -270,6 +305,18 @@ def scatterer_cells(radar, platform, scat: Scatterers, pulse: int, n_doppler: in
                                              _ptr(gate), _ptr(bins), _ptr(gc), _ptr(bc),
                                              _stream(stream)))
     return gate, bins, gc, bc
+
+
+def scatterer_echo(radar, platform, scat: Scatterers, pulse: int, precision: str = "split",
+                   stream=None) -> torch.Tensor:
+    """Per-scatterer complex amplitude C_n at ``pulse`` (in or out of the range window), as
+    the summation evaluates it in ``precision``: complex64 (split) or complex128 (fp64) [n]."""
+    out = torch.empty(scat.n, dtype=_cdtype(precision), device=scat.device)
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_scatterer_echo(ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc),
+                                            int(pulse), _prec(precision), _ptr(out),
+                                            _stream(stream)))
+    return out
 
 
 def synth_pulses_backward(radar, grad_iq: torch.Tensor, n_spectra: int, update0: int,
@@ -409,8 +456,9 @@ class BatchedFastMode:
 
     def __init__(self, radar, platform, scats, pulse0: int, n_pulses: int, n_fast: int,
                  n_doppler: int, window: str = "sqrt_raised_cosine", precision: str = "split",
-                 update_block: int = 64):
+                 update_block: int = 64, tuning: Optional[Tuning] = None):
         self.radar, self.platform, self.scats = radar, platform, list(scats)
+        self.tuning = tuning
         self.pulse0, self.n_pulses, self.n_fast, self.n_doppler = pulse0, n_pulses, n_fast, n_doppler
         self.window, self.precision = window, precision
         self.u0, self.S = spectra_range(pulse0, n_pulses, n_fast)
@@ -433,7 +481,7 @@ class BatchedFastMode:
             doppler_accumulate_batched(self.radar, self.platform, self.scats, self.u0 + b0, b1 - b0,
                                        self.n_fast, self.n_doppler, self.precision,
                                        outs=[T[b0:b1] for T in self.spectra],
-                                       workspace=self.workspace)
+                                       workspace=self.workspace, tuning=self.tuning)
         for T, Y in zip(self.spectra, self.iq):
             synth_pulses(self.radar, T, self.u0, self.n_fast, self.pulse0, self.n_pulses,
                          self.window, out=Y)
@@ -442,6 +490,20 @@ class BatchedFastMode:
         """Run eagerly on the current stream."""
         self._run()
         return self.iq
+
+    def autotune(self, reps: int = 3, at_update: Optional[int] = None):
+        """Choose the launch plan by timing candidates on one block of updates, the one
+        starting at update ``at_update`` (default: the first; pick a block where the scenes
+        are in the range window), before ``capture()``.  Returns ``(tuning, ms)``."""
+        n = min(self.S, self.block)
+        b0 = 0 if at_update is None else min(max(int(at_update) - self.u0, 0), self.S - n)
+        self.tuning, ms = autotune_batched(
+            self.radar, self.platform, self.scats, self.u0 + b0, n, self.n_fast, self.n_doppler,
+            self.precision, reps=reps, outs=[T[b0:b0 + n] for T in self.spectra],
+            workspace=self.workspace)
+        for T in self.spectra:
+            T.zero_()
+        return self.tuning, ms
 
     def capture(self):
         """Record the whole update loop into a CUDA graph (after one eager warm-up run)."""

@@ -44,6 +44,15 @@ class Scatterers(ctypes.Structure):
         ("t0", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("sets_per_launch", ctypes.c_int32), ("samples_per_group", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+    def __repr__(self):
+        return "Tuning(sets_per_launch=%d, samples_per_group=%d)" % (self.sets_per_launch,
+                                                                     self.samples_per_group)
+
+
 _P = ctypes.c_void_p
 _RP = ctypes.POINTER(Radar)
 _PP = ctypes.POINTER(Platform)
@@ -63,6 +72,7 @@ PROTOTYPES = {
                            ctypes.c_int, _P, _P], ctypes.c_int),
     "rsim_scatterer_cells": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P, _P],
                              ctypes.c_int),
+    "rsim_scatterer_echo": ([_RP, _PP, _SP, _I64, ctypes.c_int, _P, _P], ctypes.c_int),
     "rsim_synth_pulses_backward": ([_RP, _P, _I32, _I64, _I32, _I32, _I64, _I32, ctypes.c_int,
                                     ctypes.c_int, _P, _P], ctypes.c_int),
     "rsim_doppler_accumulate_backward": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
@@ -71,8 +81,12 @@ PROTOTYPES = {
                                  ctypes.c_int),
     "rsim_batched_workspace_size": ([_I32, _I32, _I32, _I32], ctypes.c_size_t),
     "rsim_doppler_accumulate_batched": ([_RP, _PP, _I32, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
-                                         ctypes.POINTER(ctypes.c_void_p), _P, ctypes.c_size_t, _P],
-                                        ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Tuning),
+                                         _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "rsim_autotune_batched": ([_RP, _PP, _I32, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_void_p), _P, ctypes.c_size_t, _I32,
+                               ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_double), _P],
+                              ctypes.c_int),
     "rsim_doppler_accumulate_noalloc": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
                                          _P, _P], ctypes.c_int),
 }

@@ -1,12 +1,15 @@
 // abi.cu -- the C ABI of librsim (declared in include/rsim.h): argument validation,
-// workspace checks, model constants and kernel launches.  No allocation happens here;
-// every device buffer, including scratch, belongs to the caller.
+// workspace checks, model constants, kernel launches and the batched-pass autotuner.  No
+// device memory is allocated here; every device buffer, including scratch, belongs to the
+// caller.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "rsim.h"
 #include "rsim_internal.cuh"
@@ -145,13 +148,16 @@ size_t ws_bytes(int64_t n_samples, int n_gates, int n_doppler) {
 // Sample schedule of a summation launch.  The samples are split over gridDim.y only when the
 // scatterer chunks alone cannot fill the GPU (about 8 resident CTAs' worth per SM).
 // Returns the number of sample groups (gridDim.y).
+// Samples per CTA: spg_req > 0 forces it (clamped to what the grid allows), 0 = enough
+// groups for about 8 CTAs per SM.
 int64_t plan_samples(int64_t chunks, int64_t pulse_base, int32_t stride, int32_t n_samples,
-                     rsim::Schedule* sch) {
+                     rsim::Schedule* sch, int32_t spg_req = 0) {
     const int64_t target = (int64_t)device_sms() * 8;
     int64_t groups = (target + chunks - 1) / chunks;
     if (groups < 1) groups = 1;
     if (groups > n_samples) groups = n_samples;
     int64_t spg = (n_samples + groups - 1) / groups;
+    if (spg_req > 0) spg = spg_req < n_samples ? spg_req : n_samples;
     if (spg < (n_samples + 65534) / 65535) spg = (n_samples + 65534) / 65535;
     groups = (n_samples + spg - 1) / spg;
     sch->pulse_base = pulse_base;
@@ -346,7 +352,28 @@ rsim_status rsim_scatterer_cells(const rsim_radar* radar, const rsim_platform* p
     const rsim::Model m = make_model(radar, platform, scat, n_doppler);
     const rsim::Scat sc = make_scat(scat);
     const cudaError_t e = rsim::launch_cells(m, pulse, precision == RSIM_FP64, n_doppler > 1, sc,
-                                             gate, bin, gate_coord, bin_coord, stream);
+                                             gate, bin, gate_coord, bin_coord, nullptr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cells kernel launch");
+    return RSIM_OK;
+}
+
+rsim_status rsim_scatterer_echo(const rsim_radar* radar, const rsim_platform* platform,
+                                const rsim_scatterers* scat, int64_t pulse,
+                                rsim_precision precision, void* contrib, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_platform(platform)) != RSIM_OK) return st;
+    if ((st = check_scat(scat)) != RSIM_OK) return st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (pulse < 0 || pulse > ((int64_t)1 << 52)) return fail(RSIM_ERR_INVALID_ARG, "pulse out of range");
+    if (scat->n == 0) return RSIM_OK;
+    const bool fp64 = precision == RSIM_FP64;
+    if (!contrib || !aligned(contrib, fp64 ? 16 : 8))
+        return fail(RSIM_ERR_INVALID_ARG, "contrib is NULL or misaligned");
+    const rsim::Model m = make_model(radar, platform, scat, 1);
+    const rsim::Scat sc = make_scat(scat);
+    const cudaError_t e = rsim::launch_cells(m, pulse, fp64, false, sc, nullptr, nullptr, nullptr,
+                                             nullptr, contrib, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cells kernel launch");
     return RSIM_OK;
 }
@@ -428,9 +455,23 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
                                             int32_t n_real, const rsim_scatterers* scats,
                                             int64_t update0, int32_t n_updates, int32_t n_fast,
                                             int32_t n_doppler, rsim_precision precision,
-                                            void* const* spectra, void* workspace,
-                                            size_t workspace_bytes, cudaStream_t stream) {
+                                            void* const* spectra, const rsim_tuning* tuning,
+                                            void* workspace, size_t workspace_bytes,
+                                            cudaStream_t stream) {
     rsim_status st;
+    int sets_per_launch = rsim::kMaxBatch;
+    int32_t spg_req = 0;
+    if (tuning) {
+        for (int i = 0; i < 6; ++i)
+            if (tuning->reserved[i] != 0) return fail(RSIM_ERR_INVALID_ARG, "tuning.reserved must be 0");
+        if (tuning->sets_per_launch < 0 || tuning->sets_per_launch > rsim::kMaxBatch)
+            return fail(RSIM_ERR_INVALID_ARG, "tuning.sets_per_launch=%d not in [0, %d]",
+                        tuning->sets_per_launch, rsim::kMaxBatch);
+        if (tuning->samples_per_group < 0)
+            return fail(RSIM_ERR_INVALID_ARG, "tuning.samples_per_group < 0");
+        if (tuning->sets_per_launch > 0) sets_per_launch = tuning->sets_per_launch;
+        spg_req = tuning->samples_per_group;
+    }
     if ((st = check_radar(radar)) != RSIM_OK) return st;
     if ((st = check_platform(platform)) != RSIM_OK) return st;
     if ((st = check_precision(precision)) != RSIM_OK) return st;
@@ -469,7 +510,7 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
     while (r < n_real) {
         int k = 0;
         int64_t chunks = 0;
-        for (; r < n_real && k < rsim::kMaxBatch; ++r) {
+        for (; r < n_real && k < sets_per_launch; ++r) {
             if (scats[r].n == 0) continue;
             rsim::BatchEntry& be = bp.e[k];
             be.sc = make_scat(&scats[r]);
@@ -488,13 +529,87 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
         bp.n_real = k;
         bp.pad = 0;
         rsim::Schedule sch;
-        const int64_t groups = plan_samples(chunks, update0 * (int64_t)n_fast, n_fast, n_updates, &sch);
+        const int64_t groups = plan_samples(chunks, update0 * (int64_t)n_fast, n_fast, n_updates, &sch,
+                                            spg_req);
         e = rsim::launch_accumulate_batched(m, sch, bp, fp64, true, dim3((unsigned)chunks, (unsigned)groups),
                                             stream);
         if (e != cudaSuccess) return cuda_fail(e, "batched summation kernel launch");
         e = rsim::launch_finalize_batched(fb, k, n_vals, fp64, device_sms(), stream);
         if (e != cudaSuccess) return cuda_fail(e, "batched finalize kernel launch");
     }
+    return RSIM_OK;
+}
+
+rsim_status rsim_autotune_batched(const rsim_radar* radar, const rsim_platform* platform,
+                                  int32_t n_real, const rsim_scatterers* scats, int64_t update0,
+                                  int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                  rsim_precision precision, void* const* spectra, void* workspace,
+                                  size_t workspace_bytes, int32_t reps, rsim_tuning* best,
+                                  double* best_ms, cudaStream_t stream) {
+    if (!best) return fail(RSIM_ERR_INVALID_ARG, "best is NULL");
+    if (reps < 1 || reps > 1000) return fail(RSIM_ERR_INVALID_ARG, "reps=%d not in [1, 1000]", reps);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "stream query");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(RSIM_ERR_UNSUPPORTED, "autotuning times launches: not allowed during graph capture");
+    // candidate plans (duplicates after clamping are skipped)
+    const int sets_c[3] = {rsim::kMaxBatch, 32, 8};
+    int32_t spg_c[5] = {0, n_updates, (n_updates + 1) / 2, (n_updates + 3) / 4, (n_updates + 7) / 8};
+    std::vector<rsim_tuning> cand;
+    int nonempty = 0;
+    for (int r = 0; r < n_real; ++r) nonempty += (scats && scats[r].n > 0) ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        if (a > 0 && sets_c[a] >= nonempty) continue;  // same grouping as a larger value
+        for (int b = 0; b < 5; ++b) {
+            if (b > 0 && spg_c[b] < 1) continue;
+            rsim_tuning t;
+            memset(&t, 0, sizeof(t));
+            t.sets_per_launch = sets_c[a];
+            t.samples_per_group = spg_c[b];
+            bool dup = false;
+            for (const rsim_tuning& c : cand)
+                dup = dup || (c.sets_per_launch == t.sets_per_launch &&
+                              c.samples_per_group == t.samples_per_group);
+            if (!dup) cand.push_back(t);
+        }
+    }
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "event");
+    }
+    rsim_status st = RSIM_OK;
+    double best_t = -1.0;
+    std::vector<float> times;
+    for (const rsim_tuning& t : cand) {
+        times.clear();
+        for (int i = 0; i <= reps && st == RSIM_OK; ++i) {
+            if ((e = cudaEventRecord(e0, stream)) != cudaSuccess) { st = cuda_fail(e, "event record"); break; }
+            st = rsim_doppler_accumulate_batched(radar, platform, n_real, scats, update0, n_updates,
+                                                 n_fast, n_doppler, precision, spectra, &t,
+                                                 workspace, workspace_bytes, stream);
+            if (st != RSIM_OK) break;
+            if ((e = cudaEventRecord(e1, stream)) != cudaSuccess) { st = cuda_fail(e, "event record"); break; }
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_fail(e, "event sync"); break; }
+            float ms = 0.f;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) { st = cuda_fail(e, "event time"); break; }
+            if (i > 0) times.push_back(ms);  // the first run is untimed (warm-up)
+        }
+        if (st != RSIM_OK) break;
+        std::sort(times.begin(), times.end());
+        const double med = times[times.size() / 2];
+        if (best_t < 0.0 || med < best_t) {
+            best_t = med;
+            *best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RSIM_OK) return st;
+    if (best_ms) *best_ms = best_t < 0.0 ? 0.0 : best_t;
+    if (best_t < 0.0) memset(best, 0, sizeof(*best));  // nothing to run: the default plan
     return RSIM_OK;
 }
 

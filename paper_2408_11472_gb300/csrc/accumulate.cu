@@ -181,7 +181,7 @@ struct ChunkCtx {
 // that rare, register-hungry path out of the per-sample loop keeps the loop within the
 // register budget.  Every contribution is added in fixed point, so the split between
 // merged and single additions does not change the result's determinism.
-constexpr int kQueue = 256;  // entries per warp; flushed before it can overflow
+constexpr int kQueue = 64 * kItems;  // entries per warp; flushed before it can overflow
 
 template <bool DOPPLER>
 __device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t chunk0, float cx,
@@ -451,13 +451,13 @@ __global__ void finalize_batched_kernel(FinalizeBatch fb, int64_t n_vals) {
 __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse, int fp64,
                                                          int doppler, Scat sc, int32_t* gate,
                                                          int32_t* bin, double* gcoord,
-                                                         double* bcoord) {
+                                                         double* bcoord, void* contrib) {
     const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
     const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
     Raw r;
     load_raw(sc, base, r);
     int key[kItems], g[kItems];
-    double gc[kItems], bc[kItems];
+    double gc[kItems], bc[kItems], cre[kItems], cim[kItems];
     if (!fp64) {
         float cx, cy;
         chunk_ref(sc, chunk0, cx, cy);
@@ -472,6 +472,8 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
             key[q] = doppler
                 ? eval_split<true, true, false>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q])
                 : eval_split<false, true, false>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q]);
+            cre[q] = re;
+            cim[q] = im;
         }
     } else {
         ItemD it[kItems];
@@ -482,6 +484,8 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
             double re, im;
             key[q] = doppler ? eval_fp64<true, false>(m, k, it[q], base + q, sc.n, re, im, nullptr, &g[q], &gc[q], &bc[q])
                              : eval_fp64<false, false>(m, k, it[q], base + q, sc.n, re, im, nullptr, &g[q], &gc[q], &bc[q]);
+            cre[q] = re;
+            cim[q] = im;
         }
     }
 #pragma unroll
@@ -492,6 +496,10 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
         if (bin) bin[n] = doppler ? ((int)floor(bc[q]) & (m.n_doppler - 1)) : 0;
         if (gcoord) gcoord[n] = gc[q];
         if (bcoord) bcoord[n] = bc[q];
+        if (contrib) {
+            if (fp64) static_cast<double2*>(contrib)[n] = make_double2(cre[q], cim[q]);
+            else static_cast<float2*>(contrib)[n] = make_float2((float)cre[q], (float)cim[q]);
+        }
         (void)key[q];
     }
 }
@@ -689,11 +697,11 @@ cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t
 }
 
 cudaError_t launch_cells(const Model& m, int64_t pulse, bool fp64, bool doppler, const Scat& sc,
-                         int32_t* gate, int32_t* bin, double* gc, double* bc,
+                         int32_t* gate, int32_t* bin, double* gc, double* bc, void* contrib,
                          cudaStream_t stream) {
     const unsigned blocks = (unsigned)((sc.n + kChunk - 1) / kChunk);
     cells_kernel<<<blocks, kThreads, 0, stream>>>(m, pulse, fp64 ? 1 : 0, doppler ? 1 : 0, sc, gate,
-                                                  bin, gc, bc);
+                                                  bin, gc, bc, contrib);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,8 @@ cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const
 cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t n_vals, bool fp64,
                                     int n_sms, cudaStream_t stream);
 cudaError_t launch_cells(const Model& m, int64_t pulse, bool fp64, bool doppler, const Scat& sc,
-                         int32_t* gate, int32_t* bin, double* gc, double* bc, cudaStream_t stream);
+                         int32_t* gate, int32_t* bin, double* gc, double* bc, void* contrib,
+                         cudaStream_t stream);
 cudaError_t launch_backward(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
                             bool doppler, const void* G, float* grad_z, float* grad_nrcs,
                             cudaStream_t stream);

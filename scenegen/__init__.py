@@ -134,25 +134,36 @@ def sea_surface(L: int, seed: int, spacing: float = 1.0, height_std: float = 0.5
     ln_nrcs = rng.normal(nrcs_mu, nrcs_sigma, size=(L, L))
     if sigma_k is None:
         sigma_k = max(0.006, 3.0 * 2.0 * math.pi / (L * spacing))
-    k1 = 2.0 * math.pi * np.fft.fftfreq(L, d=spacing)
+    torch = _fft_backend(backend, device)
+    xp = np if torch is None else torch
+    dev = None if torch is None else (device if device is not None else "cpu")
+
+    def arr(a):
+        return a if torch is None else torch.from_numpy(a).to(dev)
+
+    # the same float64 arithmetic on either backend (numpy on the host, torch on `device`)
+    k1 = arr(2.0 * math.pi * np.fft.fftfreq(L, d=spacing))
     kx = k1[None, :]
     ky = k1[:, None]
-    spec = np.exp(-((kx - k_peak) ** 2 + ky ** 2) / (2.0 * sigma_k ** 2))
-    spec = np.where(kx > 0.0, spec, 0.0)  # one-sided: waves travel towards +x
-    amp = np.sqrt(spec) * (re + 1j * im) / math.sqrt(2.0)
-    kmag = np.sqrt(kx ** 2 + ky ** 2)
-    omega = np.sqrt(G_EARTH * kmag)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        ux = np.where(kmag > 0, kx / np.where(kmag > 0, kmag, 1.0), 0.0)
-        uy = np.where(kmag > 0, ky / np.where(kmag > 0, kmag, 1.0), 0.0)
-    coeffs = [amp, -1j * omega * amp, omega * ux * amp, omega * uy * amp]
-
-    torch = _fft_backend(backend, device)
+    spec = xp.exp(-((kx - k_peak) ** 2 + ky ** 2) / (2.0 * sigma_k ** 2))
+    spec = xp.where(kx > 0.0, spec, xp.zeros_like(spec))  # one-sided: waves travel towards +x
+    amp = xp.sqrt(spec) * (arr(re) + 1j * arr(im)) / math.sqrt(2.0)
+    del re, im
+    kmag = xp.sqrt(kx ** 2 + ky ** 2)
+    omega = xp.sqrt(G_EARTH * kmag)
+    safe = xp.where(kmag > 0, kmag, xp.ones_like(kmag))
+    ux = xp.where(kmag > 0, kx / safe, xp.zeros_like(kmag))
+    uy = xp.where(kmag > 0, ky / safe, xp.zeros_like(kmag))
+    ifft2 = np.fft.ifft2 if torch is None else torch.fft.ifft2
+    eta = ifft2(amp).real
+    wz = ifft2(-1j * omega * amp).real
+    wx = ifft2(omega * ux * amp).real
+    wy = ifft2(omega * uy * amp).real
+    del amp
+    xs = (np.arange(L, dtype=np.float64) - (L - 1) / 2.0) * spacing
+    nrcs = np.exp(ln_nrcs).astype(np.float32).ravel()
     if torch is None:
-        fields = [np.real(np.fft.ifft2(c)) for c in coeffs]
-        eta, wz, wx, wy = fields
         scale = height_std / float(np.std(eta))
-        xs = (np.arange(L, dtype=np.float64) - (L - 1) / 2.0) * spacing
         X = np.broadcast_to(xs[None, :], (L, L))
         Y = np.broadcast_to(xs[:, None], (L, L))
         out = {
@@ -162,22 +173,19 @@ def sea_surface(L: int, seed: int, spacing: float = 1.0, height_std: float = 0.5
             "vx": (wx * scale).astype(np.float32).ravel(),
             "vy": (wy * scale).astype(np.float32).ravel(),
             "vz": (wz * scale).astype(np.float32).ravel(),
-            "nrcs": np.exp(ln_nrcs).astype(np.float32).ravel(),
+            "nrcs": nrcs,
         }
     else:
-        dev = device if device is not None else "cpu"
-        fields = [torch.fft.ifft2(torch.from_numpy(c).to(dev)).real for c in coeffs]
-        eta, wz, wx, wy = fields
         scale = height_std / float(eta.std(unbiased=False))
-        xs = (torch.arange(L, dtype=torch.float64, device=dev) - (L - 1) / 2.0) * spacing
+        xt = torch.from_numpy(xs).to(dev)
         out = {
-            "x": xs[None, :].expand(L, L).reshape(-1).to(torch.float32),
-            "y": xs[:, None].expand(L, L).reshape(-1).to(torch.float32),
+            "x": xt[None, :].expand(L, L).reshape(-1).to(torch.float32),
+            "y": xt[:, None].expand(L, L).reshape(-1).to(torch.float32),
             "z": (eta * scale).to(torch.float32).reshape(-1),
             "vx": (wx * scale).to(torch.float32).reshape(-1),
             "vy": (wy * scale).to(torch.float32).reshape(-1),
             "vz": (wz * scale).to(torch.float32).reshape(-1),
-            "nrcs": torch.from_numpy(np.exp(ln_nrcs).astype(np.float32).ravel()).to(dev),
+            "nrcs": torch.from_numpy(nrcs).to(dev),
         }
     out["origin"] = (0.0, 0.0, 0.0)
     out["area"] = float(spacing * spacing)

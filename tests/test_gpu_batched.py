@@ -45,6 +45,55 @@ def test_batched_equals_individual_calls_bitwise(rsim, precision):
         assert torch.equal(T, T1)
 
 
+def test_every_launch_plan_gives_the_same_bits(rsim):
+    c = sg.config(1)
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    scats = _sets(rsim, [40, 0, 72, 33, 90, 16, 64, 25, 51, 12], seed0=700, shift=11.0)
+    u0, S = 30, 9
+    ref = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler)
+    for sets, spg in ((1, 0), (3, 1), (8, 4), (96, 9), (0, 2), (5, 100)):
+        t = rsim.Tuning(sets, spg)
+        outs = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler,
+                                               tuning=t)
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b), (sets, spg)
+
+
+def test_autotune_returns_a_valid_plan(rsim):
+    c = sg.config(1)
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    scats = _sets(rsim, [64, 100, 48, 80], seed0=710, shift=5.0)
+    u0, S = 30, 8
+    ref = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler)
+    t, ms = rsim.autotune_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler, reps=2)
+    assert ms > 0.0
+    assert 1 <= t.sets_per_launch <= 96 and t.samples_per_group >= 0
+    assert list(t.reserved) == [0] * 6
+    outs = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler, tuning=t)
+    for a, b in zip(outs, ref):
+        assert torch.equal(a, b)
+    # the batched driver tunes on its first block and keeps the results unchanged
+    bfm = rsim.BatchedFastMode(rd, pf, scats, u0 * fp.n_fast, 6 * fp.n_fast, fp.n_fast,
+                               fp.n_doppler, update_block=4)
+    y_default = [y.clone() for y in bfm.run()]
+    bfm.autotune(reps=1)
+    for a, b in zip(bfm.run(), y_default):
+        assert torch.equal(a, b)
+
+
+def test_bad_tuning_is_rejected(rsim):
+    c = sg.config(1)
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    scats = _sets(rsim, [16], seed0=720)
+    for t in (rsim.Tuning(97, 0), rsim.Tuning(-1, 0), rsim.Tuning(4, -2)):
+        with pytest.raises(rsim.RsimError):
+            rsim.doppler_accumulate_batched(rd, pf, scats, 0, 1, fp.n_fast, fp.n_doppler, tuning=t)
+    t = rsim.Tuning(4, 0)
+    t.reserved[2] = 1
+    with pytest.raises(rsim.RsimError):
+        rsim.doppler_accumulate_batched(rd, pf, scats, 0, 1, fp.n_fast, fp.n_doppler, tuning=t)
+
+
 def test_more_sets_than_one_launch_holds(rsim):
     c = sg.config(1)
     rd, pf, fp = c["radar"], c["platform"], c["fast"]

@@ -39,6 +39,22 @@ def test_cells_match_oracle_cfg0(rsim, orc, cfg0, precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+def test_scatterer_echo_matches_oracle(rsim, orc, cfg0, precision):
+    """Per-scatterer complex amplitude: FP64 path to rounding; split path within its FP32
+    phase error (a few 1e-6 cycles of two-way phase) and amplitude rounding."""
+    c, sc = cfg0
+    dev = rsim.Scatterers.from_arrays(sc)
+    rd, pf = c["radar"], c["platform"]
+    for p in (0, 40):
+        C_o = orc.echo(rd, pf, sc, p / rd.prf_hz)["C"]
+        C = np_(rsim.scatterer_echo(rd, pf, dev, p, precision)).astype(np.complex128)
+        assert C.dtype == np.complex128 and C.shape == C_o.shape
+        rel = np.abs(C - C_o) / np.abs(C_o)
+        assert rel.max() < (1e-6 if precision == "fp64" else 1e-3)
+        assert np.sqrt(np.mean(rel ** 2)) < (2e-7 if precision == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_direct_sum_parity_cfg0(rsim, orc, cfg0, precision):
     """cfg0 at full size: 65,536 scatterers x 64 pulses."""
     c, sc = cfg0
