@@ -14,6 +14,8 @@
     cfg 4  adjoint, 1024 x 1024 surface, 256 pulses: waveform-power loss against a seeded
            target, forward and backward through the autograd Function; gradient against the
            FP64 oracle's.
+    nfast  fast mode against regular mode over the update interval n_fast and the Doppler
+           bin count (N_d = n_fast, or 2 n_fast zero-padded), 2048 x 2048 surface.
 
 Every input is seeded and synthetic (the generator in ``scenegen``).  The FP64 oracle runs
 only inside each run's ``cpu_baseline`` leg, which times it on the host cores and returns
@@ -436,11 +438,74 @@ def run_cfg4(torch, rsim, args):
     return line
 
 
-RUNS = {0: run_cfg0, 2: run_cfg2, 3: run_cfg3, 4: run_cfg4}
+# ------------------------------------------------------------------------ n_fast sweep
+def run_nfast_sweep(torch, rsim, args):
+    """Fast mode against regular mode on the 2048 x 2048 surface over 4096 pulses, for
+    update intervals n_fast in {16 .. 256} and N_d = n_fast or 2 n_fast (the zero-padded
+    variant, whose segments hold the offsets -n_fast..n_fast without wrapping): time,
+    speed-up and the relative difference of the mean power waveform (mean over pulses of
+    |Y|^2 per gate, the comparison of the paper's Fig. 4 and Fig. 6)."""
+    c = sg.config(1)
+    rd, pf, P, L = c["radar"], c["platform"], c["n_pulses"], c["L"]
+    window = c["fast"].window
+    dev = rsim.Scatterers.from_arrays(sg.sea_surface(L, c["seed"]))
+    N, G = dev.n, rd.n_gates
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    Yr = torch.zeros((P, G), dtype=torch.complex64, device="cuda")
+    wsr = torch.empty(rsim.workspace_size(P, G, 1), dtype=torch.uint8, device="cuda")
+
+    def regular():
+        Yr.zero_()
+        rsim.direct_sum(rd, pf, dev, 0, P, "split", out=Yr, workspace=wsr)
+
+    t_reg = _timed(torch, regular, 3, flush)
+    regular()
+    torch.cuda.synchronize()
+    Yr64 = Yr.to(torch.complex128)
+    wf_reg = (Yr64.abs() ** 2).mean(0)
+    rows = []
+    for nf in (16, 32, 64, 128, 256):
+        for nd in (nf, 2 * nf):
+            S = (P - 1) // nf + 2
+            T = torch.zeros((S, G, nd), dtype=torch.complex64, device="cuda")
+            Y = torch.empty((P, G), dtype=torch.complex64, device="cuda")
+            ws = torch.empty(rsim.workspace_size(S, G, nd), dtype=torch.uint8, device="cuda")
+
+            def fast():
+                T.zero_()
+                rsim.doppler_accumulate(rd, pf, dev, 0, S, nf, nd, "split", out=T, workspace=ws)
+                rsim.synth_pulses(rd, T, 0, nf, 0, P, window, out=Y)
+
+            t = _timed(torch, fast, 5, flush)
+            fast()
+            torch.cuda.synchronize()
+            Y64 = Y.to(torch.complex128)
+            wf = (Y64.abs() ** 2).mean(0)
+            rows.append({
+                "n_fast": nf, "n_doppler": nd, "spectra": S, "ms": round(t, 3),
+                "speedup_vs_regular": round(t_reg / t, 2),
+                "mean_power_waveform_rel_diff": float(torch.linalg.vector_norm(wf - wf_reg) /
+                                                      torch.linalg.vector_norm(wf_reg)),
+                "mean_power_ratio": float(wf.sum() / wf_reg.sum()),
+                "iq_rel_l2_vs_regular": float(torch.linalg.vector_norm(Y64 - Yr64) /
+                                              torch.linalg.vector_norm(Yr64)),
+                "update_pulses_rel_l2": float(torch.linalg.vector_norm(Y64[::nf] - Yr64[::nf]) /
+                                              torch.linalg.vector_norm(Yr64[::nf]))})
+    line = _base_line("nfast_sweep_2048x2048_p4096", "fast vs regular mode over n_fast and N_d",
+                      "x speed-up at n_fast=64", next(r["speedup_vs_regular"] for r in rows
+                                                      if r["n_fast"] == 64 and r["n_doppler"] == 64))
+    line["config"].update({"scatterers": N, "pulses": P, "gates": G, "window": window,
+                           "precision": "split", "l2": "flushed before each timed call"})
+    line["regular_ms"] = round(t_reg, 3)
+    line["sweep"] = rows
+    return line
 
 
-def run(k: int, args):
+RUNS = {"0": run_cfg0, "2": run_cfg2, "3": run_cfg3, "4": run_cfg4, "nfast": run_nfast_sweep}
+
+
+def run(k: str, args):
     import torch
     import paper_2408_11472_gb300 as rsim
     torch.cuda.set_device(0)
-    return RUNS[k](torch, rsim, args)
+    return RUNS[str(k)](torch, rsim, args)
