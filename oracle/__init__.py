@@ -52,7 +52,10 @@ class _Radar(ctypes.Structure):
     _fields_ = [("carrier_hz", ctypes.c_double), ("prf_hz", ctypes.c_double),
                 ("c_mps", ctypes.c_double), ("gate_width_m", ctypes.c_double),
                 ("beamwidth_rad", ctypes.c_double), ("n_gates", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("ant_nu", ctypes.c_int32), ("ant", ctypes.POINTER(ctypes.c_double)),
+                ("ant_nv", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("ant_u0", ctypes.c_double), ("ant_du", ctypes.c_double),
+                ("ant_v0", ctypes.c_double), ("ant_dv", ctypes.c_double)]
 
 
 class _Platform(ctypes.Structure):
@@ -72,8 +75,22 @@ class _Scene(ctypes.Structure):
 
 
 def _radar(r) -> _Radar:
-    return _Radar(float(r.carrier_hz), float(r.prf_hz), float(r.c_mps), float(r.gate_width_m),
-                  float(r.beamwidth_rad), int(r.n_gates), 0)
+    """ctypes radar; a tabulated antenna pattern (``r.antenna``: complex ``gain[nv, nu]``,
+    grid ``u0, du, v0, dv``) rides along as float64 (re, im) pairs, kept alive by the struct."""
+    out = _Radar(float(r.carrier_hz), float(r.prf_hz), float(r.c_mps), float(r.gate_width_m),
+                 float(r.beamwidth_rad), int(r.n_gates), 0, None, 0, 0, 0.0, 1.0, 0.0, 1.0)
+    ant = getattr(r, "antenna", None)
+    if ant is not None:
+        g = np.asarray(ant.gain, dtype=np.complex128)
+        if g.ndim != 2 or min(g.shape) < 2:
+            raise ValueError("antenna gain must be [nv, nu] with nu, nv >= 2")
+        buf = np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))
+        out.ant = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        out.ant_nv, out.ant_nu = int(g.shape[0]), int(g.shape[1])
+        out.ant_u0, out.ant_du = float(ant.u0), float(ant.du)
+        out.ant_v0, out.ant_dv = float(ant.v0), float(ant.dv)
+        out._keep = buf
+    return out
 
 
 def _platform(p) -> _Platform:
@@ -143,6 +160,7 @@ class Oracle:
         L.or_doppler_spectra_cells.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_int32, _IP, _IP, _DP]
+        L.or_antenna_gain.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _DP, _DP, _DP]
         L.or_set_threads.argtypes = [ctypes.c_int]
         L.or_get_threads.restype = ctypes.c_int
         if threads:
@@ -165,6 +183,13 @@ class Oracle:
                                *[_d(o) for o in outs])
         R, dR, theta, amp, cr, ci = outs
         return {"R": R, "dR": dR, "theta": theta, "amp": amp, "C": cr + 1j * ci}
+
+    def antenna_gain(self, radar, u: float, v: float):
+        """Tabulated pattern of ``radar.antenna`` at (u, v): (G, dG/du, dG/dv), complex."""
+        rd = _radar(radar)
+        g, gu, gv = (np.zeros(2) for _ in range(3))
+        self.lib.or_antenna_gain(ctypes.byref(rd), float(u), float(v), _d(g), _d(gu), _d(gv))
+        return complex(*g), complex(*gu), complex(*gv)
 
     def cells(self, radar, platform, scene, pulse: int, n_doppler: int):
         sc, keep = _scene(scene)

@@ -23,6 +23,23 @@ def _scene_arrays(scene):
     return f, o, float(scene.get("area", 1.0))
 
 
+def pattern(antenna, u, v):
+    """Tabulated two-way pattern at direction cosines (u, v): bilinear in the real and
+    imaginary parts between the grid nodes, 0 outside [u0, u0 + (nu-1) du) x [v0, ...)."""
+    tab = np.asarray(antenna.gain, dtype=np.complex128)
+    nv, nu = tab.shape
+    x = (np.asarray(u, dtype=np.float64) - antenna.u0) / antenna.du
+    y = (np.asarray(v, dtype=np.float64) - antenna.v0) / antenna.dv
+    col, row = np.floor(x), np.floor(y)
+    inside = (col >= 0) & (col <= nu - 2) & (row >= 0) & (row <= nv - 2)
+    c = np.where(inside, col, 0).astype(np.int64)
+    r = np.where(inside, row, 0).astype(np.int64)
+    fx, fy = x - col, y - row
+    top = tab[r, c] + fx * (tab[r, c + 1] - tab[r, c])          # at v = v_row
+    bottom = tab[r + 1, c] + fx * (tab[r + 1, c + 1] - tab[r + 1, c])
+    return np.where(inside, top + fy * (bottom - top), 0.0)
+
+
 def echo(radar, platform, scene, t):
     """Complex amplitude, range excess and range of every scatterer at time t."""
     f, o, area = _scene_arrays(scene)
@@ -36,8 +53,12 @@ def echo(radar, platform, scene, t):
     r_ref = platform.r_ref0 + platform.r_ref_rate * t
     lam = radar.c_mps / radar.carrier_hz
     off_nadir = np.arctan2(horiz, d[2])
-    # Gaussian two-way pattern whose power is halved at theta = beamwidth / 2.
-    gain = 0.5 ** ((2.0 * off_nadir / radar.beamwidth_rad) ** 2 / 2.0)
+    if getattr(radar, "antenna", None) is not None:
+        # direction cosines of the line of sight platform -> scatterer
+        gain = pattern(radar.antenna, -d[0] / rng, -d[1] / rng)
+    else:
+        # Gaussian two-way pattern whose power is halved at theta = beamwidth / 2.
+        gain = 0.5 ** ((2.0 * off_nadir / radar.beamwidth_rad) ** 2 / 2.0)
     amp = np.sqrt(f["nrcs"] * area) * gain * (r_ref / rng) ** 2
     cycles = 2.0 * rng / lam
     frac = cycles - np.round(cycles)

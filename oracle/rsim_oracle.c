@@ -20,8 +20,12 @@
  *              kinematics from the state given at epoch t0)
  *   R        = |d|,  dR = R - r_ref(t)
  *   theta    = atan2(|d_xy|, d_z)                          (nadir-pointing antenna)
- *   a        = sqrt(sigma A) exp(-2 ln2 theta^2/theta_b^2) (r_ref/R)^2   (radar equation at facet level, Sec. II.A)
- *   psi      = 2 R / lambda  [cycles];  C = a exp(-j 2 pi (psi - rint psi))  (two-way phase)
+ *   w        = exp(-2 ln2 theta^2/theta_b^2)               (analytic two-way pattern), or
+ *            = the complex two-way pattern G(u, v) tabulated on a u-v grid and interpolated
+ *              bilinearly (real and imaginary parts) at the facet's direction cosines
+ *              u = (s - P)_x / R, v = (s - P)_y / R; zero outside the grid (Sec. II.A)
+ *   C        = sqrt(sigma A) w (r_ref/R)^2 exp(-j 2 pi (psi - rint psi)),  psi = 2 R / lambda
+ *              [cycles]                                   (radar equation at facet level, Sec. II.A)
  *   gate     = floor(dR / gate_width + N_g / 2), kept iff 0 <= gate < N_g  (complex sum per range gate, Sec. II.A)
  *   regular  : Y[p, g] = sum_n C_n(t_p) [gate_n(t_p) = g]                (Fig. 1 step 4)
  *   fast     : for each update i (pulse p_i = i n_fast), Algorithm 1:
@@ -50,7 +54,11 @@
 typedef struct {
     double carrier_hz, prf_hz, c_mps, gate_width_m, beamwidth_rad;
     int32_t n_gates;
+    int32_t ant_nu;      /* > 0: tabulated pattern with ant_nu x ant_nv nodes */
+    const double *ant;   /* [ant_nv][ant_nu][2] complex two-way gain, or NULL */
+    int32_t ant_nv;
     int32_t pad_;
+    double ant_u0, ant_du, ant_v0, ant_dv;
 } or_radar;
 
 typedef struct {
@@ -68,7 +76,35 @@ typedef struct {
 
 typedef struct {
     double R, dR, rho, dz, theta, amp, psi, re, im;
+    /* tabulated pattern only: base = sqrt(sigma A) (r_ref/R)^2, phase factor (cr, ci),
+     * direction cosines (u, v) and dG/du, dG/dv (complex) */
+    double base, cr, ci, u, v, gu_re, gu_im, gv_re, gv_im;
 } or_echo;
+
+/* Bilinear interpolation of the tabulated complex pattern at (u, v): nodes at
+ * u0 + i du (i < nu), v0 + j dv (j < nv); the cell (i, j) holds u0 + i du <= u < u0 + (i+1) du,
+ * likewise in v; outside the grid the gain and its derivatives are 0.  Also returns the
+ * partial derivatives dG/du, dG/dv of the interpolant inside the cell. */
+static void antenna_gain(const or_radar *rd, double u, double v, double g[2], double gu[2],
+                         double gv[2]) {
+    g[0] = g[1] = gu[0] = gu[1] = gv[0] = gv[1] = 0.0;
+    double fu = (u - rd->ant_u0) / rd->ant_du;
+    double fv = (v - rd->ant_v0) / rd->ant_dv;
+    double iu = floor(fu), iv = floor(fv);
+    if (!(iu >= 0.0 && iu <= (double)(rd->ant_nu - 2) && iv >= 0.0 && iv <= (double)(rd->ant_nv - 2)))
+        return;
+    double tu = fu - iu, tv = fv - iv;
+    int64_t i = (int64_t)iu, j = (int64_t)iv;
+    const double *g00 = rd->ant + ((size_t)j * rd->ant_nu + i) * 2;
+    const double *g10 = g00 + 2;                         /* u + du */
+    const double *g01 = g00 + (size_t)rd->ant_nu * 2;    /* v + dv */
+    const double *g11 = g01 + 2;
+    for (int c = 0; c < 2; ++c) {
+        g[c] = (1.0 - tv) * ((1.0 - tu) * g00[c] + tu * g10[c]) + tv * ((1.0 - tu) * g01[c] + tu * g11[c]);
+        gu[c] = ((1.0 - tv) * (g10[c] - g00[c]) + tv * (g11[c] - g01[c])) / rd->ant_du;
+        gv[c] = ((1.0 - tu) * (g01[c] - g00[c]) + tu * (g11[c] - g10[c])) / rd->ant_dv;
+    }
+}
 
 int or_version(void) { return 1; }
 
@@ -105,9 +141,7 @@ static void echo_at(const or_radar *rd, const or_platform *pf, const or_scene *s
     double rref = pf->r_ref0 + pf->r_ref_rate * t;
     double lambda = rd->c_mps / rd->carrier_hz;
     double theta = atan2(rho, dz);
-    double tb = rd->beamwidth_rad;
-    double w = exp(-2.0 * OR_LN2 * theta * theta / (tb * tb));
-    double amp = sqrt((double)sc->nrcs[n] * sc->area) * w * (rref / R) * (rref / R);
+    double base = sqrt((double)sc->nrcs[n] * sc->area) * (rref / R) * (rref / R);
     double psi = 2.0 * R / lambda;
     double phi = -2.0 * OR_PI * (psi - rint(psi));
     e->R = R;
@@ -115,10 +149,30 @@ static void echo_at(const or_radar *rd, const or_platform *pf, const or_scene *s
     e->rho = rho;
     e->dz = dz;
     e->theta = theta;
-    e->amp = amp;
     e->psi = psi;
-    e->re = amp * cos(phi);
-    e->im = amp * sin(phi);
+    e->base = base;
+    e->cr = cos(phi);
+    e->ci = sin(phi);
+    if (rd->ant_nu > 0) {
+        double g[2], gu[2], gv[2];
+        e->u = -dx / R;
+        e->v = -dy / R;
+        antenna_gain(rd, e->u, e->v, g, gu, gv);
+        e->gu_re = gu[0];
+        e->gu_im = gu[1];
+        e->gv_re = gv[0];
+        e->gv_im = gv[1];
+        e->amp = base * sqrt(g[0] * g[0] + g[1] * g[1]);
+        e->re = base * (g[0] * e->cr - g[1] * e->ci);
+        e->im = base * (g[0] * e->ci + g[1] * e->cr);
+    } else {
+        double tb = rd->beamwidth_rad;
+        double w = exp(-2.0 * OR_LN2 * theta * theta / (tb * tb));
+        e->u = e->v = e->gu_re = e->gu_im = e->gv_re = e->gv_im = 0.0;
+        e->amp = base * w;
+        e->re = e->amp * e->cr;
+        e->im = e->amp * e->ci;
+    }
 }
 
 static double gate_coord_of(const or_radar *rd, double dR) {
@@ -386,15 +440,33 @@ void or_synth_grad(int32_t n_gates, const double *G_Y, int32_t S, int64_t update
 }
 
 /* dC/dz of scatterer echo e (C = a exp(j phi)): C (dln a/dz + j dphi/dz) with
- * dR/dz = -d_z / R, dtheta/dz = rho / R^2. */
+ * dR/dz = -d_z / R, dtheta/dz = rho / R^2.  With the tabulated pattern, C = base G e^{j phi}
+ * and the pattern term is base e^{j phi} (dG/du du/dz + dG/dv dv/dz), where
+ * u = -d_x / R gives du/dz = u d_z / R^2 (likewise v). */
 static void dC_dz(const or_radar *rd, const or_echo *e, double *dre, double *dim) {
     double lambda = rd->c_mps / rd->carrier_hz;
-    double tb = rd->beamwidth_rad;
     double R2 = e->R * e->R;
-    double dlna = -4.0 * OR_LN2 * e->theta / (tb * tb) * (e->rho / R2) + 2.0 * e->dz / R2;
     double dphi = 4.0 * OR_PI * e->dz / (lambda * e->R);
+    if (rd->ant_nu > 0) {
+        double dlna = 2.0 * e->dz / R2;   /* (r_ref / R)^2 factor only */
+        *dre = e->re * dlna - e->im * dphi;
+        *dim = e->im * dlna + e->re * dphi;
+        double du = e->u * e->dz / R2, dv = e->v * e->dz / R2;
+        double dg_re = e->gu_re * du + e->gv_re * dv;
+        double dg_im = e->gu_im * du + e->gv_im * dv;
+        *dre += e->base * (dg_re * e->cr - dg_im * e->ci);
+        *dim += e->base * (dg_re * e->ci + dg_im * e->cr);
+        return;
+    }
+    double tb = rd->beamwidth_rad;
+    double dlna = -4.0 * OR_LN2 * e->theta / (tb * tb) * (e->rho / R2) + 2.0 * e->dz / R2;
     *dre = e->re * dlna - e->im * dphi;
     *dim = e->im * dlna + e->re * dphi;
+}
+
+/* The tabulated pattern and its partial derivatives at (u, v) (for the tests). */
+void or_antenna_gain(const or_radar *rd, double u, double v, double *g, double *gu, double *gv) {
+    antenna_gain(rd, u, v, g, gu, gv);
 }
 
 /* Adjoint of the fast-mode rasterisation: for each scatterer, the gradient of a

@@ -41,7 +41,9 @@ G_EARTH = 9.81
 
 __all__ = [
     "C_LIGHT",
+    "AntennaTable",
     "RadarParams",
+    "antenna_table",
     "PlatformParams",
     "FastParams",
     "WINDOWS",
@@ -60,9 +62,22 @@ __all__ = [
 WINDOWS = {"sqrt_linear": 0, "sqrt_raised_cosine": 1, "linear": 2}
 
 
+@dataclasses.dataclass(frozen=True, eq=False)
+class AntennaTable:
+    """Two-way complex antenna pattern on a u-v grid: ``gain[j, i]`` at direction cosines
+    u = u0 + i du, v = v0 + j dv (complex, shape [nv, nu])."""
+
+    gain: np.ndarray
+    u0: float
+    du: float
+    v0: float
+    dv: float
+
+
 @dataclasses.dataclass(frozen=True)
 class RadarParams:
-    """Instrument constants (SI units)."""
+    """Instrument constants (SI units).  ``antenna``: a tabulated two-way pattern, or None
+    for the analytic Gaussian pattern of beamwidth ``beamwidth_rad``."""
 
     carrier_hz: float = 13.575e9
     prf_hz: float = 18_000.0
@@ -70,6 +85,25 @@ class RadarParams:
     gate_width_m: float = 0.47
     beamwidth_rad: float = math.radians(1.3)
     n_gates: int = 128
+    antenna: Optional[AntennaTable] = None
+
+
+def antenna_table(seed: int, n: int = 129, half_width: float = 0.05,
+                  width: float = 0.0193, ripple: float = 0.3) -> AntennaTable:
+    """Seeded synthetic two-way pattern on an n x n grid over |u|, |v| <= half_width: an
+    elliptical main lobe exp(-(u/a)^2 - (v/b)^2) with a and b drawn within 15 % of
+    ``width``, a small seeded boresight offset and a smooth phase ripple of up to
+    ``ripple`` rad (the shape a measured pattern table has near the main lobe)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a, b = width * (1.0 + 0.15 * (2.0 * rng.random(2) - 1.0))
+    u_off, v_off = 0.05 * width * (2.0 * rng.random(2) - 1.0)
+    ku, kv, ph = rng.random(3) * np.array([2.0, 2.0, 2.0 * math.pi])
+    g = np.linspace(-half_width, half_width, n)
+    U, V = g[None, :], g[:, None]
+    amp = np.exp(-((U - u_off) / a) ** 2 - ((V - v_off) / b) ** 2)
+    phase = ripple * np.sin(ku * U / width + kv * V / width + ph)
+    d = float(g[1] - g[0])
+    return AntennaTable(gain=amp * np.exp(1j * phase), u0=float(g[0]), du=d, v0=float(g[0]), dv=d)
 
 
 @dataclasses.dataclass(frozen=True)
