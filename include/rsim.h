@@ -23,8 +23,9 @@
  *   gate = floor((R - r_ref) / gate_width + n_gates / 2), dropped unless
  *   0 <= gate < n_gates;
  *   off-nadir angle theta = atan2(|d_xy|, d_z);
- *   C = sqrt(nrcs * area) * exp(-2 ln2 theta^2 / beamwidth^2) * (r_ref / R)^2
- *       * exp(-j 4 pi R / lambda),  lambda = c / carrier;
+ *   C = sqrt(nrcs * area) * w * (r_ref / R)^2 * exp(-j 4 pi R / lambda),  lambda = c / carrier,
+ *   w = exp(-2 ln2 theta^2 / beamwidth^2), or the complex two-way gain of a tabulated
+ *   pattern at the facet's direction cosines (rsim_antenna);
  *   pulse-pair Doppler of the pair (p_i, p_i + 1): nu = phase advance of C per
  *   pulse in cycles, wrapped to [-1/2, 1/2); bin = floor(nu * n_doppler + 1/2)
  *   mod n_doppler (so bin k holds the tone exp(+j 2 pi k m / n_doppler));
@@ -97,6 +98,23 @@ typedef enum {
 } rsim_window;
 
 /* Instrument constants (SI).  1 <= n_gates <= 4096; all doubles finite and > 0. */
+/* Two-way antenna pattern tabulated on a u-v grid (Section II.A: every pattern a simulation
+ * needs is recorded on a u-v grid, and its complex value at each facet is obtained by
+ * interpolation in that grid).  (u, v) are the first two direction cosines of the line of
+ * sight from the platform to the facet in the scene frame, u = (s - P)_x / R,
+ * v = (s - P)_y / R.  Node (i, j) is at u = u0 + i du, v = v0 + j dv.  Between nodes the
+ * real and imaginary parts are interpolated bilinearly; outside
+ * [u0, u0 + (nu-1) du) x [v0, v0 + (nv-1) dv) the gain is 0.  The edge decision is taken
+ * in the precision of the call, so a table should fall to 0 at its border.
+ * gain : DEVICE [nv][nu] complex64 (re, im interleaved), 8-byte aligned, read during the
+ *        call's kernels (keep it alive until they finish). */
+typedef struct {
+    const void *gain;
+    int32_t nu, nv;        /* >= 2 each, nu * nv < 2^31 */
+    double u0, du;         /* du > 0 */
+    double v0, dv;         /* dv > 0 */
+} rsim_antenna;
+
 typedef struct {
     double carrier_hz;     /* carrier frequency f_c                               */
     double prf_hz;         /* pulse repetition frequency                          */
@@ -105,6 +123,8 @@ typedef struct {
     double beamwidth_rad;  /* two-way 3 dB full beamwidth of the Gaussian pattern */
     int32_t n_gates;       /* number of range gates N_g                           */
     int32_t reserved;      /* must be 0                                           */
+    const rsim_antenna *antenna;  /* tabulated two-way pattern (host struct, read during the
+                                     call), or NULL for the Gaussian pattern of beamwidth_rad */
 } rsim_radar;
 
 /* Platform track in the scene frame (metres, seconds): P(t) = p0 + v t;

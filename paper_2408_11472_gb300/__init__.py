@@ -24,7 +24,7 @@ from . import _lib
 from ._lib import PRECISIONS, WINDOWS, RsimError
 
 __all__ = [
-    "Radar", "Platform", "Scatterers", "RsimError", "workspace_size", "direct_sum",
+    "Antenna", "Radar", "Platform", "Scatterers", "RsimError", "workspace_size", "direct_sum",
     "doppler_accumulate", "doppler_accumulate_noalloc", "doppler_accumulate_batched",
     "autotune_batched", "Tuning",
     "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "scatterer_echo",
@@ -36,9 +36,24 @@ __all__ = [
 _KEYS = ("x", "y", "z", "vx", "vy", "vz", "nrcs")
 
 
+@dataclasses.dataclass(frozen=True, eq=False)
+class Antenna:
+    """Two-way complex antenna pattern on a u-v grid (rsim_antenna): ``gain[j, i]`` at the
+    direction cosines u = u0 + i du, v = v0 + j dv of the line of sight platform -> facet;
+    numpy or torch, complex, [nv, nu].  Copied to the device once per device."""
+
+    gain: object
+    u0: float
+    du: float
+    v0: float
+    dv: float
+
+
 @dataclasses.dataclass(frozen=True)
 class Radar:
-    """Instrument constants (SI).  Defaults: Sentinel-3 SRAL-like Ku-band altimeter."""
+    """Instrument constants (SI).  Defaults: Sentinel-3 SRAL-like Ku-band altimeter.
+    ``antenna``: tabulated two-way pattern (any object with gain, u0, du, v0, dv), or None
+    for the Gaussian pattern of ``beamwidth_rad``."""
 
     carrier_hz: float = 13.575e9
     prf_hz: float = 18_000.0
@@ -46,6 +61,7 @@ class Radar:
     gate_width_m: float = 0.47
     beamwidth_rad: float = math.radians(1.3)
     n_gates: int = 128
+    antenna: Optional[Antenna] = None
 
 
 @dataclasses.dataclass(frozen=True)

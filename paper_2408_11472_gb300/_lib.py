@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsim.so")
@@ -25,11 +26,17 @@ class RsimError(RuntimeError):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
 
 
+class Antenna(ctypes.Structure):
+    _fields_ = [("gain", ctypes.c_void_p), ("nu", ctypes.c_int32), ("nv", ctypes.c_int32),
+                ("u0", ctypes.c_double), ("du", ctypes.c_double),
+                ("v0", ctypes.c_double), ("dv", ctypes.c_double)]
+
+
 class Radar(ctypes.Structure):
     _fields_ = [("carrier_hz", ctypes.c_double), ("prf_hz", ctypes.c_double),
                 ("c_mps", ctypes.c_double), ("gate_width_m", ctypes.c_double),
                 ("beamwidth_rad", ctypes.c_double), ("n_gates", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("antenna", ctypes.POINTER(Antenna))]
 
 
 class Platform(ctypes.Structure):
@@ -114,9 +121,37 @@ def check(status: int) -> None:
         raise RsimError(status, msg.decode() if msg else "")
 
 
+_DEVICE_TABLES = weakref.WeakKeyDictionary()
+
+
+def _device_table(ant):
+    """complex64 device copy of a tabulated pattern (``ant.gain`` [nv, nu], numpy or torch),
+    made once per table object and device, kept as long as the table object lives."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    per = _DEVICE_TABLES.setdefault(ant, {})
+    t = per.get(dev)
+    if t is None:
+        g = ant.gain
+        t = (g if isinstance(g, torch.Tensor) else torch.from_numpy(
+            __import__("numpy").asarray(g))).to(device=dev, dtype=torch.complex64).contiguous()
+        if t.dim() != 2:
+            raise ValueError("antenna gain must be a 2-D [nv, nu] array")
+        per[dev] = t
+    return t
+
+
 def make_radar(r) -> Radar:
-    return Radar(float(r.carrier_hz), float(r.prf_hz), float(r.c_mps), float(r.gate_width_m),
-                 float(r.beamwidth_rad), int(r.n_gates), 0)
+    out = Radar(float(r.carrier_hz), float(r.prf_hz), float(r.c_mps), float(r.gate_width_m),
+                float(r.beamwidth_rad), int(r.n_gates), 0, None)
+    ant = getattr(r, "antenna", None)
+    if ant is not None:
+        t = _device_table(ant)
+        a = Antenna(t.data_ptr(), int(t.shape[1]), int(t.shape[0]), float(ant.u0), float(ant.du),
+                    float(ant.v0), float(ant.dv))
+        out.antenna = ctypes.pointer(a)
+        out._keep = (a, t)
+    return out
 
 
 def make_platform(p) -> Platform:

@@ -57,6 +57,15 @@ rsim_status check_radar(const rsim_radar* r) {
     if (r->n_gates < 1 || r->n_gates > 4096)
         return fail(RSIM_ERR_INVALID_ARG, "n_gates=%d outside [1, 4096]", r->n_gates);
     if (r->reserved != 0) return fail(RSIM_ERR_INVALID_ARG, "radar.reserved must be 0");
+    if (const rsim_antenna* a = r->antenna) {
+        if (!a->gain || !aligned(a->gain, 8))
+            return fail(RSIM_ERR_INVALID_ARG, "antenna.gain is NULL or not 8-byte aligned");
+        if (a->nu < 2 || a->nv < 2 || (int64_t)a->nu * a->nv >= ((int64_t)1 << 31))
+            return fail(RSIM_ERR_INVALID_ARG, "antenna grid %d x %d: need nu, nv >= 2, nu*nv < 2^31",
+                        a->nu, a->nv);
+        if (!finite_pos(a->du) || !finite_pos(a->dv) || !std::isfinite(a->u0) || !std::isfinite(a->v0))
+            return fail(RSIM_ERR_INVALID_ARG, "antenna grid origin must be finite, steps finite and > 0");
+    }
     return RSIM_OK;
 }
 
@@ -124,6 +133,20 @@ rsim::Model make_model(const rsim_radar* r, const rsim_platform* p, const rsim_s
     m.s2 = (float)(23.0 / (45.0 * m.beam_k * m.beam_k));
     m.qb_wide = (float)(1e-2 * m.beam_k);
     m.inv_beam_k = (float)(1.0 / m.beam_k);
+    m.nd_over_2pi_f = (float)((double)n_doppler / 6.283185307179586476925);
+    if (const rsim_antenna* a = r->antenna) {
+        m.ant = static_cast<const float2*>(a->gain);
+        m.ant_nu = a->nu;
+        m.ant_nv = a->nv;
+        m.ant_u0 = a->u0;
+        m.ant_v0 = a->v0;
+        m.ant_idu = 1.0 / a->du;
+        m.ant_idv = 1.0 / a->dv;
+        m.ant_u0_f = (float)a->u0;
+        m.ant_v0_f = (float)a->v0;
+        m.ant_idu_f = (float)m.ant_idu;
+        m.ant_idv_f = (float)m.ant_idv;
+    }
     return m;
 }
 

@@ -183,7 +183,7 @@ struct ChunkCtx {
 // merged and single additions does not change the result's determinism.
 constexpr int kQueue = 64 * kItems;  // entries per warp; flushed before it can overflow
 
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t chunk0, float cx,
                                          float cy, float area, const SplitConst* tab,
                                          const Fp64Const* tab64, const int* queue, int n) {
@@ -199,13 +199,13 @@ __device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t
         const SampleF k = load_sample(tab[j]);
         float re, im;
         int f;
-        const int key = eval_split<DOPPLER, true, false>(m, k, it, re, im, f, &tab64[j], x, y);
+        const int key = eval_split<DOPPLER, true, false, ANT>(m, k, it, re, im, f, &tab64[j], x, y);
         if (key >= 0) emit_cell(sample_out(tab[j]), key, re, im);
     }
     __syncwarp();
 }
 
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Schedule& sch,
                                                        const ChunkCtx& cx_, int s_begin,
                                                        int s_end) {
@@ -255,7 +255,7 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
 #pragma unroll
             for (int q = 0; q < kItems; ++q) {
                 int f;
-                key[q] = eval_split<DOPPLER, false, false>(m, k, it[q], re[q], im[q], f);
+                key[q] = eval_split<DOPPLER, false, false, ANT>(m, k, it[q], re[q], im[q], f);
                 if (f) key[q] = -1;  // deferred to the exact evaluation
                 fl |= (f != 0) << q;
             }
@@ -273,18 +273,18 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             warp_reduce_emit<float, kItems>(key, re, im, sample_out(tab[j]));
             if (nq > kQueue - 32 * kItems) {  // room for one more sample's worth
                 __syncwarp();
-                flush_queue<DOPPLER>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
+                flush_queue<DOPPLER, ANT>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
                 nq = 0;
             }
         }
         if (nq > 0) {  // before the table is rebuilt
             __syncwarp();
-            flush_queue<DOPPLER>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
+            flush_queue<DOPPLER, ANT>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
         }
     }
 }
 
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Schedule& sch,
                                                       const ChunkCtx& cx_, int s_begin,
                                                       int s_end) {
@@ -324,7 +324,7 @@ __device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Sche
             double re[kItems], im[kItems];
 #pragma unroll
             for (int q = 0; q < kItems; ++q)
-                key[q] = eval_fp64<DOPPLER, false>(m, k, it[q], base + q, sc.n, re[q], im[q], nullptr);
+                key[q] = eval_fp64<DOPPLER, false, ANT>(m, k, it[q], base + q, sc.n, re[q], im[q], nullptr);
             warp_reduce_emit<double, kItems>(key, re, im, cx_.ws + (int64_t)s * cells * 2);
         }
     }
@@ -360,7 +360,7 @@ __device__ __forceinline__ ChunkCtx batch_ctx(const BatchParams& bp, int r, int6
 }  // namespace
 
 // ------------------------------------------------------------------------------- forward
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
     unsigned long long* __restrict__ ws) {
@@ -372,20 +372,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
     c.ws = ws;
     int s0, s1;
     sample_range(sch, s0, s1);
-    accumulate_split_chunk<DOPPLER>(m, sch, c, s0, s1);
+    accumulate_split_chunk<DOPPLER, ANT>(m, sch, c, s0, s1);
 }
 
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_batched_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ BatchParams bp) {
     const int r = batch_find(bp, blockIdx.x);
     const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);
     int s0, s1;
     sample_range(sch, s0, s1);
-    accumulate_split_chunk<DOPPLER>(m, sch, c, s0, s1);
+    accumulate_split_chunk<DOPPLER, ANT>(m, sch, c, s0, s1);
 }
 
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
     unsigned long long* __restrict__ ws) {
@@ -397,17 +397,17 @@ __global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
     c.ws = ws;
     int s0, s1;
     sample_range(sch, s0, s1);
-    accumulate_fp64_chunk<DOPPLER>(m, sch, c, s0, s1);
+    accumulate_fp64_chunk<DOPPLER, ANT>(m, sch, c, s0, s1);
 }
 
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads) accumulate_fp64_batched_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ BatchParams bp) {
     const int r = batch_find(bp, blockIdx.x);
     const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);
     int s0, s1;
     sample_range(sch, s0, s1);
-    accumulate_fp64_chunk<DOPPLER>(m, sch, c, s0, s1);
+    accumulate_fp64_chunk<DOPPLER, ANT>(m, sch, c, s0, s1);
 }
 
 // Fixed point (q 2^-32) to float without the FP64 pipe: |q| = hi 2^32 + lo, both unsigned
@@ -448,6 +448,7 @@ __global__ void finalize_batched_kernel(FinalizeBatch fb, int64_t n_vals) {
 }
 
 // ------------------------------------------------------------------------------- cells
+template <bool ANT>
 __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse, int fp64,
                                                          int doppler, Scat sc, int32_t* gate,
                                                          int32_t* bin, double* gcoord,
@@ -470,8 +471,8 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
             float re, im;
             int f;
             key[q] = doppler
-                ? eval_split<true, true, false>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q])
-                : eval_split<false, true, false>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q]);
+                ? eval_split<true, true, false, ANT>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q])
+                : eval_split<false, true, false, ANT>(m, k, it[q], re, im, f, &k64, r.x[q], r.y[q], nullptr, &g[q], &gc[q], &bc[q]);
             cre[q] = re;
             cim[q] = im;
         }
@@ -482,8 +483,8 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
 #pragma unroll
         for (int q = 0; q < kItems; ++q) {
             double re, im;
-            key[q] = doppler ? eval_fp64<true, false>(m, k, it[q], base + q, sc.n, re, im, nullptr, &g[q], &gc[q], &bc[q])
-                             : eval_fp64<false, false>(m, k, it[q], base + q, sc.n, re, im, nullptr, &g[q], &gc[q], &bc[q]);
+            key[q] = doppler ? eval_fp64<true, false, ANT>(m, k, it[q], base + q, sc.n, re, im, nullptr, &g[q], &gc[q], &bc[q])
+                             : eval_fp64<false, false, ANT>(m, k, it[q], base + q, sc.n, re, im, nullptr, &g[q], &gc[q], &bc[q]);
             cre[q] = re;
             cim[q] = im;
         }
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
 }
 
 // ------------------------------------------------------------------------------- backward
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     Model m, Schedule sch, Scat sc, const float2* __restrict__ G, float* __restrict__ grad_z,
     float* __restrict__ grad_nrcs) {
@@ -555,13 +556,14 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
                 float re, im;
                 int f;
                 DerivF dv;
-                const int key = eval_split<DOPPLER, true, true>(m, k, it[q], re, im, f, &tab64[j],
+                const int key = eval_split<DOPPLER, true, true, ANT>(m, k, it[q], re, im, f, &tab64[j],
                                                                  xo[q], yo[q], &dv);
                 if (key >= 0) {
                     const float2 g = __ldg(G + (int64_t)s * cells + key);
                     const float cr = fmaf(g.x, re, g.y * im);   // Re(conj(G) C)
                     const float ci = fmaf(g.x, im, -g.y * re);  // Im(conj(G) C)
                     gz[q] = fmaf(cr, dv.dlna, fmaf(-ci, dv.dphi, gz[q]));
+                    if (ANT) gz[q] = fmaf(g.x, dv.pat.x, fmaf(g.y, dv.pat.y, gz[q]));  // Re(conj(G) dC_pat)
                     gs[q] += cr;
                 }
             }
@@ -576,7 +578,7 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     }
 }
 
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
     Model m, Schedule sch, Scat sc, const double2* __restrict__ G, float* __restrict__ grad_z,
     float* __restrict__ grad_nrcs) {
@@ -622,12 +624,13 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
             for (int q = 0; q < kItems; ++q) {
                 double re, im;
                 DerivD dv;
-                const int key = eval_fp64<DOPPLER, true>(m, k, it[q], base + q, sc.n, re, im, &dv);
+                const int key = eval_fp64<DOPPLER, true, ANT>(m, k, it[q], base + q, sc.n, re, im, &dv);
                 if (key >= 0) {
                     const double2 g = G[(int64_t)s * cells + key];
                     const double cr = g.x * re + g.y * im;
                     const double ci = g.x * im - g.y * re;
                     gz[q] += cr * dv.dlna - ci * dv.dphi;
+                    if (ANT) gz[q] += g.x * dv.pat.x + g.y * dv.pat.y;
                     gs[q] += cr;
                 }
             }
@@ -646,24 +649,46 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
 cudaError_t launch_accumulate(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
                               bool doppler, unsigned long long* ws, dim3 grid,
                               cudaStream_t stream) {
+    const bool ant = m.ant != nullptr;
     if (fp64) {
-        if (doppler) accumulate_fp64_kernel<true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
-        else accumulate_fp64_kernel<false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+        if (ant) {
+            if (doppler) accumulate_fp64_kernel<true, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+            else accumulate_fp64_kernel<false, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+        } else {
+            if (doppler) accumulate_fp64_kernel<true, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+            else accumulate_fp64_kernel<false, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+        }
     } else {
-        if (doppler) accumulate_split_kernel<true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
-        else accumulate_split_kernel<false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+        if (ant) {
+            if (doppler) accumulate_split_kernel<true, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+            else accumulate_split_kernel<false, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+        } else {
+            if (doppler) accumulate_split_kernel<true, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+            else accumulate_split_kernel<false, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+        }
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const BatchParams& bp,
                                       bool fp64, bool doppler, dim3 grid, cudaStream_t stream) {
+    const bool ant = m.ant != nullptr;
     if (fp64) {
-        if (doppler) accumulate_fp64_batched_kernel<true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
-        else accumulate_fp64_batched_kernel<false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        if (ant) {
+            if (doppler) accumulate_fp64_batched_kernel<true, true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+            else accumulate_fp64_batched_kernel<false, true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        } else {
+            if (doppler) accumulate_fp64_batched_kernel<true, false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+            else accumulate_fp64_batched_kernel<false, false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        }
     } else {
-        if (doppler) accumulate_split_batched_kernel<true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
-        else accumulate_split_batched_kernel<false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        if (ant) {
+            if (doppler) accumulate_split_batched_kernel<true, true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+            else accumulate_split_batched_kernel<false, true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        } else {
+            if (doppler) accumulate_split_batched_kernel<true, false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+            else accumulate_split_batched_kernel<false, false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+        }
     }
     return cudaGetLastError();
 }
@@ -700,8 +725,12 @@ cudaError_t launch_cells(const Model& m, int64_t pulse, bool fp64, bool doppler,
                          int32_t* gate, int32_t* bin, double* gc, double* bc, void* contrib,
                          cudaStream_t stream) {
     const unsigned blocks = (unsigned)((sc.n + kChunk - 1) / kChunk);
-    cells_kernel<<<blocks, kThreads, 0, stream>>>(m, pulse, fp64 ? 1 : 0, doppler ? 1 : 0, sc, gate,
-                                                  bin, gc, bc, contrib);
+    if (m.ant)
+        cells_kernel<true><<<blocks, kThreads, 0, stream>>>(m, pulse, fp64 ? 1 : 0, doppler ? 1 : 0,
+                                                            sc, gate, bin, gc, bc, contrib);
+    else
+        cells_kernel<false><<<blocks, kThreads, 0, stream>>>(m, pulse, fp64 ? 1 : 0, doppler ? 1 : 0,
+                                                             sc, gate, bin, gc, bc, contrib);
     return cudaGetLastError();
 }
 
@@ -711,12 +740,22 @@ cudaError_t launch_backward(const Model& m, const Schedule& sch, const Scat& sc,
     const unsigned blocks = (unsigned)((sc.n + kChunk - 1) / kChunk);
     if (fp64) {
         const double2* g = static_cast<const double2*>(G);
-        if (doppler) backward_fp64_kernel<true><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
-        else backward_fp64_kernel<false><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+        if (m.ant) {
+            if (doppler) backward_fp64_kernel<true, true><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+            else backward_fp64_kernel<false, true><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+        } else {
+            if (doppler) backward_fp64_kernel<true, false><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+            else backward_fp64_kernel<false, false><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+        }
     } else {
         const float2* g = static_cast<const float2*>(G);
-        if (doppler) backward_split_kernel<true><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
-        else backward_split_kernel<false><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+        if (m.ant) {
+            if (doppler) backward_split_kernel<true, true><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+            else backward_split_kernel<false, true><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+        } else {
+            if (doppler) backward_split_kernel<true, false><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+            else backward_split_kernel<false, false><<<blocks, kThreads, 0, stream>>>(m, sch, sc, g, grad_z, grad_nrcs);
+        }
     }
     return cudaGetLastError();
 }

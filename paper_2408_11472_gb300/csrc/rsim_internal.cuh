@@ -58,7 +58,86 @@ struct Model {
     float inv_gw_f, beam_k_f, chi_hi, chi_lo, dt_f, hdt_f, ep[3], inv_nd;
     // off-nadir series in qb = beam_k rho^2 / D_z^2: beam_k atan(q)^2 = qb (1 + qb (s1 + qb s2))
     float s1, s2, qb_wide, inv_beam_k;
+    // tabulated two-way pattern on a u-v grid (nullptr: the analytic Gaussian pattern)
+    const float2* ant;      // [ant_nv][ant_nu] complex
+    int ant_nu, ant_nv;
+    double ant_u0, ant_v0, ant_idu, ant_idv;
+    float ant_u0_f, ant_v0_f, ant_idu_f, ant_idv_f;
+    float nd_over_2pi_f;    // n_doppler / (2 pi): radians of phase advance to bins
 };
+
+// Tabulated two-way pattern at the facet's direction cosines (u, v) = (s - P)_{x,y} / R
+// (Section II.A: patterns recorded on a u-v grid, interpolated per facet): bilinear in the
+// real and imaginary parts, 0 outside the grid.  Optionally the partial derivatives of the
+// interpolant dG/du, dG/dv.  FP32 (split path) and FP64 versions.
+__device__ __forceinline__ float2 pattern_f(const Model& m, float u, float v,
+                                            float2* gu = nullptr, float2* gv = nullptr) {
+    const float fu = (u - m.ant_u0_f) * m.ant_idu_f;
+    const float fv = (v - m.ant_v0_f) * m.ant_idv_f;
+    const float iu = floorf(fu), iv = floorf(fv);
+    if (!(iu >= 0.0f && iu <= (float)(m.ant_nu - 2) && iv >= 0.0f && iv <= (float)(m.ant_nv - 2))) {
+        if (gu) *gu = make_float2(0.f, 0.f);
+        if (gv) *gv = make_float2(0.f, 0.f);
+        return make_float2(0.f, 0.f);
+    }
+    const float tu = fu - iu, tv = fv - iv;
+    const float2* p = m.ant + (int64_t)iv * m.ant_nu + (int64_t)iu;
+    const float2 g00 = __ldg(p), g10 = __ldg(p + 1);
+    const float2 g01 = __ldg(p + m.ant_nu), g11 = __ldg(p + m.ant_nu + 1);
+    const float ax = fmaf(tu, g10.x - g00.x, g00.x), ay = fmaf(tu, g10.y - g00.y, g00.y);
+    const float bx = fmaf(tu, g11.x - g01.x, g01.x), by = fmaf(tu, g11.y - g01.y, g01.y);
+    if (gu) {
+        const float cx = fmaf(tv, (g11.x - g01.x) - (g10.x - g00.x), g10.x - g00.x);
+        const float cy = fmaf(tv, (g11.y - g01.y) - (g10.y - g00.y), g10.y - g00.y);
+        *gu = make_float2(cx * m.ant_idu_f, cy * m.ant_idu_f);
+        *gv = make_float2((bx - ax) * m.ant_idv_f, (by - ay) * m.ant_idv_f);
+    }
+    return make_float2(fmaf(tv, bx - ax, ax), fmaf(tv, by - ay, ay));
+}
+
+__device__ __forceinline__ double2 pattern_d(const Model& m, double u, double v,
+                                             double2* gu = nullptr, double2* gv = nullptr) {
+    const double fu = (u - m.ant_u0) * m.ant_idu;
+    const double fv = (v - m.ant_v0) * m.ant_idv;
+    const double iu = floor(fu), iv = floor(fv);
+    if (!(iu >= 0.0 && iu <= (double)(m.ant_nu - 2) && iv >= 0.0 && iv <= (double)(m.ant_nv - 2))) {
+        if (gu) *gu = make_double2(0.0, 0.0);
+        if (gv) *gv = make_double2(0.0, 0.0);
+        return make_double2(0.0, 0.0);
+    }
+    const double tu = fu - iu, tv = fv - iv;
+    const float2* p = m.ant + (int64_t)iv * m.ant_nu + (int64_t)iu;
+    const float2 f00 = __ldg(p), f10 = __ldg(p + 1);
+    const float2 f01 = __ldg(p + m.ant_nu), f11 = __ldg(p + m.ant_nu + 1);
+    const double2 g00 = make_double2(f00.x, f00.y), g10 = make_double2(f10.x, f10.y);
+    const double2 g01 = make_double2(f01.x, f01.y), g11 = make_double2(f11.x, f11.y);
+    const double ax = fma(tu, g10.x - g00.x, g00.x), ay = fma(tu, g10.y - g00.y, g00.y);
+    const double bx = fma(tu, g11.x - g01.x, g01.x), by = fma(tu, g11.y - g01.y, g01.y);
+    if (gu) {
+        const double cx = fma(tv, (g11.x - g01.x) - (g10.x - g00.x), g10.x - g00.x);
+        const double cy = fma(tv, (g11.y - g01.y) - (g10.y - g00.y), g10.y - g00.y);
+        *gu = make_double2(cx * m.ant_idu, cy * m.ant_idu);
+        *gv = make_double2((bx - ax) * m.ant_idv, (by - ay) * m.ant_idv);
+    }
+    return make_double2(fma(tv, bx - ax, ax), fma(tv, by - ay, ay));
+}
+
+// Bins added to the pulse-pair Doppler coordinate by the tabulated pattern: Algorithm 1
+// takes D_i from arg(conj(C_{i+1}) C_i), and C carries the pattern, so the pattern's own
+// phase change between the facet's directions at the two pulses joins the geometric one.
+// g1 = the pattern at the first pulse; d = P - s there; the second pulse sees
+// d + (V - v) / PRF.
+__device__ __forceinline__ double pattern_bin_shift_d(const Model& m, double dx, double dy,
+                                                      double dz, double vx, double vy,
+                                                      double vz, double2 g1) {
+    const double dt = m.inv_prf;
+    const double x2 = fma(m.v[0] - vx, dt, dx), y2 = fma(m.v[1] - vy, dt, dy);
+    const double z2 = fma(m.v[2] - vz, dt, dz);
+    const double R2 = sqrt(fma(x2, x2, fma(y2, y2, z2 * z2)));
+    const double2 g2 = pattern_d(m, -x2 / R2, -y2 / R2);
+    const double re = fma(g2.x, g1.x, g2.y * g1.y), im = fma(g2.y, g1.x, -g2.x * g1.y);
+    return atan2(im, re) * ((double)m.n_doppler / 6.283185307179586476925);
+}
 
 // Sample schedule: sample s is pulse pulse_base + s * pulse_stride.
 struct Schedule {
@@ -294,8 +373,9 @@ struct ItemF {
 
 // Quantities the adjoint needs besides C.
 struct DerivF {
-    float dlna;  // d ln|C| / dz
+    float dlna;  // d ln|C| / dz, without the tabulated pattern's own variation
     float dphi;  // d arg C / dz  [rad / m]
+    float2 pat;  // tabulated pattern only: a e^{-j 2 pi f} dG/dz (0 otherwise)
 };
 
 // Result flags of the fast evaluation.
@@ -304,6 +384,7 @@ constexpr int kFlagWide = 2;    // off-nadir angle beyond the series' range (q^2
 
 // FP64 re-decision of the gate and bin of one scatterer (kept out of line so that none of
 // its FP64 work is hoisted into the common path).
+template <bool ANT>
 static __device__ __noinline__ void refine_fp64(const Model& m, const Fp64Const& k64, double x, double y,
                                          double z, double vx, double vy, double vz, bool doppler,
                                          int* g, int* kb, double* gc, double* bc) {
@@ -314,6 +395,10 @@ static __device__ __noinline__ void refine_fp64(const Model& m, const Fp64Const&
     *bc = 0.5;
     if (doppler) {
         *bc = bin_coord_fp64(m, gd, vx, vy, vz);
+        if (ANT) {
+            const double2 g1 = pattern_d(m, -gd.dx / gd.R, -gd.dy / gd.R);
+            *bc += pattern_bin_shift_d(m, gd.dx, gd.dy, gd.dz, vx, vy, vz, g1);
+        }
         *kb = clamp_floor(*bc) & (m.n_doppler - 1);
     }
 }
@@ -324,7 +409,7 @@ static __device__ __noinline__ void refine_fp64(const Model& m, const Fp64Const&
 //   off-nadir angle are only flagged (the caller re-evaluates them with GENERAL = true).
 // GENERAL = true: takes those branches (tab64 and the scatterer's original x, y needed).
 // For unflagged items both give bit-identical results.
-template <bool DOPPLER, bool GENERAL, bool DERIV>
+template <bool DOPPLER, bool GENERAL, bool DERIV, bool ANT = false>
 __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, const ItemF& it,
                                           float& re, float& im, int& flags,
                                           const Fp64Const* k64 = nullptr, float x_orig = 0.f,
@@ -350,12 +435,15 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float dx = k.Dx - lx, dy = k.Dy - ly;
     const float rho2 = fmaf(dx, dx, dy * dy);
     const float qb = rho2 * k.kq;
-    float T = fmaf(qb, fmaf(qb, fmaf(qb, m.s2, m.s1), 1.0f), k.l2kappa);
-    if (qb < m.qb_wide) {
-        fl |= kFlagWide;
-        if (GENERAL) {
-            const float th = atan2f(sqrtf(rho2), k.Dz - lz);
-            T = fmaf(th * th, m.beam_k_f, k.l2kappa);
+    float T = k.l2kappa;  // tabulated pattern: applied to C below
+    if (!ANT) {
+        T = fmaf(qb, fmaf(qb, fmaf(qb, m.s2, m.s1), 1.0f), k.l2kappa);
+        if (qb < m.qb_wide) {
+            fl |= kFlagWide;
+            if (GENERAL) {
+                const float th = atan2f(sqrtf(rho2), k.Dz - lz);
+                T = fmaf(th * th, m.beam_k_f, k.l2kappa);
+            }
         }
     }
     const float xr = dR * k.invRc;
@@ -368,8 +456,20 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     f -= rintf(f);
     float sn, cs;
     __sincosf(kTwoPiF * f, &sn, &cs);
-    re = a * cs;
-    im = -a * sn;
+    float2 gu, gv, G;
+    float pu = 0.f, pv = 0.f;
+    if (ANT) {
+        // C = a G(u, v) e^{-j 2 pi f}, (u, v) = -(d_x, d_y) / R, 1 / R = (1 / R_c)(1 - dR / R_c)
+        const float invR = k.invRc * (1.0f - xr);
+        pu = -dx * invR;
+        pv = -dy * invR;
+        G = pattern_f(m, pu, pv, DERIV ? &gu : nullptr, DERIV ? &gv : nullptr);
+        re = a * fmaf(G.x, cs, G.y * sn);
+        im = a * fmaf(G.y, cs, -G.x * sn);
+    } else {
+        re = a * cs;
+        im = -a * sn;
+    }
     int kb = 0;
     float b = 0.0f;
     if (DOPPLER) {
@@ -382,6 +482,14 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         const float hn2 = ((fmaf(-m.dt_f, dv_, k.K0hi) - lep) - it.c1) + k.K0lo;
         b = hn2 * k.kbin;
         b = fmaf(-b, xr, b);                       // 1 / (R_c + dR) = (1 / R_c)(1 - dR / R_c)
+        if (ANT) {
+            // the pattern's phase change over the pair joins the Doppler (arg(conj(C2) C1))
+            const float invR = k.invRc * (1.0f - xr);
+            const float ex = fmaf(-it.vx, m.dt_f, m.ep[0]), ey = fmaf(-it.vy, m.dt_f, m.ep[1]);
+            const float2 G2 = pattern_f(m, -(dx + ex) * invR, -(dy + ey) * invR);
+            const float pr = fmaf(G2.x, G.x, G2.y * G.y), pi = fmaf(G2.y, G.x, -G2.x * G.y);
+            b = fmaf(atan2f(pi, pr), m.nd_over_2pi_f, b);
+        }
         const float br = rintf(b);
         kb = __float2int_rn(b) & (m.n_doppler - 1);
         if (fabsf(b - br) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps)) fl |= kFlagRefine;
@@ -392,22 +500,31 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         const float dz = k.Dz - lz;
         const float invR = k.invRc * (1.0f - xr);
         const float invR2 = invR * invR;
-        const float q2 = qb * m.inv_beam_k;
-        float rho_theta;
-        if (q2 < 1e-2f) {
-            rho_theta = rho2 / dz * fmaf(q2, fmaf(q2, 0.2f, -1.0f / 3.0f), 1.0f);
-        } else {
-            rho_theta = sqrtf(rho2) * atan2f(sqrtf(rho2), dz);
-        }
-        // beam_k = -2 / theta_b^2 (base 2), so -4 ln2 / theta_b^2 = 2 ln2 beam_k
-        dv->dlna = (2.0f * dz + 1.38629436111989061883f * m.beam_k_f * rho_theta) * invR2;
         dv->dphi = kTwoPiF * (m.chi_hi + m.chi_lo) * dz * invR;  // chi = 2 / lambda
+        if (ANT) {
+            // d/dz of the pattern: dG/du du/dz + dG/dv dv/dz, du/dz = u d_z / R^2 (same for v)
+            dv->dlna = 2.0f * dz * invR2;
+            const float su = pu * dz * invR2, svv = pv * dz * invR2;
+            const float dgx = fmaf(gu.x, su, gv.x * svv), dgy = fmaf(gu.y, su, gv.y * svv);
+            dv->pat = make_float2(a * fmaf(dgx, cs, dgy * sn), a * fmaf(dgy, cs, -dgx * sn));
+        } else {
+            const float q2 = qb * m.inv_beam_k;
+            float rho_theta;
+            if (q2 < 1e-2f) {
+                rho_theta = rho2 / dz * fmaf(q2, fmaf(q2, 0.2f, -1.0f / 3.0f), 1.0f);
+            } else {
+                rho_theta = sqrtf(rho2) * atan2f(sqrtf(rho2), dz);
+            }
+            // beam_k = -2 / theta_b^2 (base 2), so -4 ln2 / theta_b^2 = 2 ln2 beam_k
+            dv->dlna = (2.0f * dz + 1.38629436111989061883f * m.beam_k_f * rho_theta) * invR2;
+            dv->pat = make_float2(0.f, 0.f);
+        }
     }
     double gcd = (double)k.gint + (double)gcf;
     double bcd = (double)b - (double)m.n_doppler * rint((double)b / (double)m.n_doppler) + 0.5;
     if (GENERAL && (fl & kFlagRefine)) {
         int g2, kb2;
-        refine_fp64(m, *k64, (double)x_orig, (double)y_orig, (double)it.z, (double)it.vx,
+        refine_fp64<ANT>(m, *k64, (double)x_orig, (double)y_orig, (double)it.z, (double)it.vx,
                     (double)it.vy, (double)it.vz, DOPPLER, &g2, &kb2, &gcd, &bcd);
         g = g2;
         kb = kb2;
@@ -438,9 +555,10 @@ struct ItemD {
 
 struct DerivD {
     double dlna, dphi;
+    double2 pat;  // tabulated pattern only: a e^{-j 2 pi f} dG/dz
 };
 
-template <bool DOPPLER, bool DERIV>
+template <bool DOPPLER, bool DERIV, bool ANT = false>
 __device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, const ItemD& it,
                                          int64_t n, int64_t n_total, double& re, double& im,
                                          DerivD* dv, int* g_out = nullptr,
@@ -450,32 +568,51 @@ __device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, con
                                (double)it.z, vx, vy, vz);
     const double gc = fma(gd.dR, m.inv_gw, m.half_gates);
     const int g = clamp_floor(gc);
-    const double th2 = theta2_d(gd.rho2, gd.dz);
     const double rr = k.rref / gd.R;
-    const double a = it.amp0 * exp2(m.beam_k * th2) * rr * rr;
+    const double a = ANT ? it.amp0 * rr * rr
+                         : it.amp0 * exp2(m.beam_k * theta2_d(gd.rho2, gd.dz)) * rr * rr;
     double f = k.psiref + gd.dR * m.two_over_lambda;
     f -= rint(f);
     double sn, cs;
     sincospi(2.0 * f, &sn, &cs);
-    re = a * cs;
-    im = -a * sn;
+    double2 gu, gv, G;
+    double pu = 0.0, pv = 0.0;
+    if (ANT) {
+        pu = -gd.dx / gd.R;
+        pv = -gd.dy / gd.R;
+        G = pattern_d(m, pu, pv, DERIV ? &gu : nullptr, DERIV ? &gv : nullptr);
+        re = a * fma(G.x, cs, G.y * sn);
+        im = a * fma(G.y, cs, -G.x * sn);
+    } else {
+        re = a * cs;
+        im = -a * sn;
+    }
     int kb = 0;
     double bc = 0.5;
     if (DOPPLER) {
         bc = bin_coord_fp64(m, gd, vx, vy, vz);
+        if (ANT) bc += pattern_bin_shift_d(m, gd.dx, gd.dy, gd.dz, vx, vy, vz, G);
         kb = clamp_floor(bc) & (m.n_doppler - 1);
     }
     if (DERIV) {
         const double R2 = gd.R * gd.R;
-        double rho_theta;
-        const double q2 = gd.rho2 / (gd.dz * gd.dz);
-        if (q2 < 1e-3) {
-            rho_theta = gd.rho2 / gd.dz * fma(q2, fma(q2, fma(q2, -1.0 / 7.0, 0.2), -1.0 / 3.0), 1.0);
-        } else {
-            rho_theta = sqrt(gd.rho2) * atan2(sqrt(gd.rho2), gd.dz);
-        }
-        dv->dlna = (2.0 * gd.dz + 2.0 * 0.69314718055994530942 * m.beam_k * rho_theta) / R2;
         dv->dphi = 2.0 * 3.14159265358979323846 * m.two_over_lambda * gd.dz / gd.R;
+        if (ANT) {
+            dv->dlna = 2.0 * gd.dz / R2;
+            const double su = pu * gd.dz / R2, svv = pv * gd.dz / R2;
+            const double dgx = fma(gu.x, su, gv.x * svv), dgy = fma(gu.y, su, gv.y * svv);
+            dv->pat = make_double2(a * fma(dgx, cs, dgy * sn), a * fma(dgy, cs, -dgx * sn));
+        } else {
+            double rho_theta;
+            const double q2 = gd.rho2 / (gd.dz * gd.dz);
+            if (q2 < 1e-3) {
+                rho_theta = gd.rho2 / gd.dz * fma(q2, fma(q2, fma(q2, -1.0 / 7.0, 0.2), -1.0 / 3.0), 1.0);
+            } else {
+                rho_theta = sqrt(gd.rho2) * atan2(sqrt(gd.rho2), gd.dz);
+            }
+            dv->dlna = (2.0 * gd.dz + 2.0 * 0.69314718055994530942 * m.beam_k * rho_theta) / R2;
+            dv->pat = make_double2(0.0, 0.0);
+        }
     }
     if (g_out) *g_out = g;
     if (gc_out) *gc_out = gc;
