@@ -16,6 +16,7 @@
            FP64 oracle's.
     nfast  fast mode against regular mode over the update interval n_fast and the Doppler
            bin count (N_d = n_fast, or 2 n_fast zero-padded), 2048 x 2048 surface.
+    antenna  the 2048 x 2048 fast-mode pass with a tabulated u-v antenna pattern.
 
 Every input is seeded and synthetic (the generator in ``scenegen``).  The FP64 oracle runs
 only inside each run's ``cpu_baseline`` leg, which times it on the host cores and returns
@@ -501,7 +502,50 @@ def run_nfast_sweep(torch, rsim, args):
     return line
 
 
-RUNS = {"0": run_cfg0, "2": run_cfg2, "3": run_cfg3, "4": run_cfg4, "nfast": run_nfast_sweep}
+# ------------------------------------------------------------------ antenna pattern table
+def run_antenna_table(torch, rsim, args):
+    """The 2048 x 2048 fast-mode pass with the two-way pattern tabulated on a u-v grid
+    (129 x 129 nodes over |u|, |v| <= 0.05) instead of the analytic Gaussian: time of the
+    summation and of the whole step against the Gaussian run, split vs FP64 error."""
+    import dataclasses
+    c = sg.config(1)
+    rd0, pf, fp, P, L = c["radar"], c["platform"], c["fast"], c["n_pulses"], c["L"]
+    rd = dataclasses.replace(rd0, antenna=sg.antenna_table(77))
+    dev = rsim.Scatterers.from_arrays(sg.sea_surface(L, c["seed"]))
+    N, G = dev.n, rd.n_gates
+    S = (P - 1) // fp.n_fast + 2
+    ws = torch.empty(rsim.workspace_size(S, G, fp.n_doppler), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for name, radar, prec in (("gaussian", rd0, "split"), ("table", rd, "split"),
+                              ("table_fp64", rd, "fp64")):
+        cdt = torch.complex128 if prec == "fp64" else torch.complex64
+        T = torch.zeros((S, G, fp.n_doppler), dtype=cdt, device="cuda")
+
+        def acc():
+            T.zero_()
+            rsim.doppler_accumulate(radar, pf, dev, 0, S, fp.n_fast, fp.n_doppler, prec, out=T,
+                                    workspace=ws)
+
+        t = _timed(torch, acc, 10 if prec == "split" else 2, flush)
+        acc()
+        torch.cuda.synchronize()
+        res[name] = {"accumulate_ms": round(t, 3),
+                     "scatterer_updates_per_s": round(N * S / (t / 1e3), 1), "T": _np(T)}
+    line = _base_line("fast_2048x2048_p4096_antenna_table", "fast-mode scatterer pass with a "
+                      "tabulated antenna pattern", "scatterer-updates/s",
+                      res["table"]["scatterer_updates_per_s"])
+    line["config"].update({"scatterers": N, "spectra": S, "table": "129 x 129 complex, |u|,|v| <= 0.05",
+                           "l2": "flushed before each timed call"})
+    for k in ("gaussian", "table", "table_fp64"):
+        line[k] = {kk: v for kk, v in res[k].items() if kk != "T"}
+    line["table_cost_vs_gaussian"] = round(res["table"]["accumulate_ms"] / res["gaussian"]["accumulate_ms"], 3)
+    line["split_vs_fp64_rel_l2_with_table"] = _rl2(res["table"]["T"], res["table_fp64"]["T"])
+    return line
+
+
+RUNS = {"0": run_cfg0, "2": run_cfg2, "3": run_cfg3, "4": run_cfg4, "nfast": run_nfast_sweep,
+        "antenna": run_antenna_table}
 
 
 def run(k: str, args):

@@ -361,7 +361,7 @@ __device__ __forceinline__ ChunkCtx batch_ctx(const BatchParams& bp, int r, int6
 
 // ------------------------------------------------------------------------------- forward
 template <bool DOPPLER, bool ANT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
+__global__ void __launch_bounds__(kThreads, ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
     unsigned long long* __restrict__ ws) {
     ChunkCtx c;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_kernel(
 }
 
 template <bool DOPPLER, bool ANT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) accumulate_split_batched_kernel(
+__global__ void __launch_bounds__(kThreads, ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_batched_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ BatchParams bp) {
     const int r = batch_find(bp, blockIdx.x);
     const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);

@@ -26,6 +26,7 @@ namespace rsim {
 constexpr int kThreads = RSIM_THREADS;        // summation CTA size
 constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (1, 2, 4, 8)
 constexpr int kMinBlocks = RSIM_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
+constexpr int kMinBlocksAnt = 4;              // the same with a tabulated antenna pattern
 constexpr int kChunk = kThreads * kItems;     // scatterers sharing one FP64 reference point
 constexpr int kTab = 128;                     // samples per block of reference constants
 constexpr double kFixScale = 4294967296.0;    // fixed point: value = q * 2^-32
@@ -93,6 +94,59 @@ __device__ __forceinline__ float2 pattern_f(const Model& m, float u, float v,
         *gv = make_float2((bx - ax) * m.ant_idv_f, (by - ay) * m.ant_idv_f);
     }
     return make_float2(fmaf(tv, bx - ax, ax), fmaf(tv, by - ay, ay));
+}
+
+// The facet's cell of the grid and its bilinear weights, kept to evaluate the pattern at a
+// nearby direction (the second pulse of the pair) without reloading the corners when that
+// direction falls in the same cell.
+struct PatCellF {
+    float2 g00, g10, g01, g11;
+    float iu, iv;
+};
+
+__device__ __forceinline__ float2 pattern_cell_f(const Model& m, float u, float v, PatCellF& c) {
+    const float fu = (u - m.ant_u0_f) * m.ant_idu_f;
+    const float fv = (v - m.ant_v0_f) * m.ant_idv_f;
+    c.iu = floorf(fu);
+    c.iv = floorf(fv);
+    if (!(c.iu >= 0.0f && c.iu <= (float)(m.ant_nu - 2) && c.iv >= 0.0f &&
+          c.iv <= (float)(m.ant_nv - 2))) {
+        c.iu = -1.0f;  // outside: no cell
+        return make_float2(0.f, 0.f);
+    }
+    const float2* p = m.ant + (int64_t)c.iv * m.ant_nu + (int64_t)c.iu;
+    c.g00 = __ldg(p);
+    c.g10 = __ldg(p + 1);
+    c.g01 = __ldg(p + m.ant_nu);
+    c.g11 = __ldg(p + m.ant_nu + 1);
+    const float tu = fu - c.iu, tv = fv - c.iv;
+    const float ax = fmaf(tu, c.g10.x - c.g00.x, c.g00.x), ay = fmaf(tu, c.g10.y - c.g00.y, c.g00.y);
+    const float bx = fmaf(tu, c.g11.x - c.g01.x, c.g01.x), by = fmaf(tu, c.g11.y - c.g01.y, c.g01.y);
+    return make_float2(fmaf(tv, bx - ax, ax), fmaf(tv, by - ay, ay));
+}
+
+// The pattern at (u, v), reusing cell c's corners when (u, v) lies in it (the same values
+// pattern_f would load).
+__device__ __forceinline__ float2 pattern_near_f(const Model& m, float u, float v,
+                                                 const PatCellF& c) {
+    const float fu = (u - m.ant_u0_f) * m.ant_idu_f;
+    const float fv = (v - m.ant_v0_f) * m.ant_idv_f;
+    const float iu = floorf(fu), iv = floorf(fv);
+    if (iu != c.iu || iv != c.iv) return pattern_f(m, u, v);
+    const float tu = fu - iu, tv = fv - iv;
+    const float ax = fmaf(tu, c.g10.x - c.g00.x, c.g00.x), ay = fmaf(tu, c.g10.y - c.g00.y, c.g00.y);
+    const float bx = fmaf(tu, c.g11.x - c.g01.x, c.g01.x), by = fmaf(tu, c.g11.y - c.g01.y, c.g01.y);
+    return make_float2(fmaf(tv, bx - ax, ax), fmaf(tv, by - ay, ay));
+}
+
+// arg(z) for the small phase steps of the pattern over one pulse: atan(t) = t (1 - t^2/3)
+// to 1e-11 for |t| < 0.01 (t = Im z / Re z, Re z > 0), else the full atan2.
+__device__ __forceinline__ float small_arg_f(float im, float re) {
+    if (re > 0.0f && fabsf(im) < 0.01f * re) {
+        const float t = __fdividef(im, re);
+        return t * fmaf(t * t, -1.0f / 3.0f, 1.0f);
+    }
+    return atan2f(im, re);
 }
 
 __device__ __forceinline__ double2 pattern_d(const Model& m, double u, double v,
@@ -457,13 +511,25 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     float sn, cs;
     __sincosf(kTwoPiF * f, &sn, &cs);
     float2 gu, gv, G;
-    float pu = 0.f, pv = 0.f;
+    PatCellF cell;
+    float pu = 0.f, pv = 0.f, pat_bins = 0.f;
     if (ANT) {
         // C = a G(u, v) e^{-j 2 pi f}, (u, v) = -(d_x, d_y) / R, 1 / R = (1 / R_c)(1 - dR / R_c)
         const float invR = k.invRc * (1.0f - xr);
         pu = -dx * invR;
         pv = -dy * invR;
-        G = pattern_f(m, pu, pv, DERIV ? &gu : nullptr, DERIV ? &gv : nullptr);
+        if (DERIV) G = pattern_f(m, pu, pv, &gu, &gv);
+        else G = pattern_cell_f(m, pu, pv, cell);
+        if (DOPPLER) {
+            // the pattern's phase change over the pulse pair joins the Doppler
+            // (Algorithm 1 takes it from arg(conj(C2) C1)); d at the second pulse is
+            // d + e_p - v dt
+            const float ex = fmaf(-it.vx, m.dt_f, m.ep[0]), ey = fmaf(-it.vy, m.dt_f, m.ep[1]);
+            const float u2 = -(dx + ex) * invR, v2 = -(dy + ey) * invR;
+            const float2 G2 = DERIV ? pattern_f(m, u2, v2) : pattern_near_f(m, u2, v2, cell);
+            const float pr = fmaf(G2.x, G.x, G2.y * G.y), pi = fmaf(G2.y, G.x, -G2.x * G.y);
+            pat_bins = small_arg_f(pi, pr) * m.nd_over_2pi_f;
+        }
         re = a * fmaf(G.x, cs, G.y * sn);
         im = a * fmaf(G.y, cs, -G.x * sn);
     } else {
@@ -482,14 +548,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         const float hn2 = ((fmaf(-m.dt_f, dv_, k.K0hi) - lep) - it.c1) + k.K0lo;
         b = hn2 * k.kbin;
         b = fmaf(-b, xr, b);                       // 1 / (R_c + dR) = (1 / R_c)(1 - dR / R_c)
-        if (ANT) {
-            // the pattern's phase change over the pair joins the Doppler (arg(conj(C2) C1))
-            const float invR = k.invRc * (1.0f - xr);
-            const float ex = fmaf(-it.vx, m.dt_f, m.ep[0]), ey = fmaf(-it.vy, m.dt_f, m.ep[1]);
-            const float2 G2 = pattern_f(m, -(dx + ex) * invR, -(dy + ey) * invR);
-            const float pr = fmaf(G2.x, G.x, G2.y * G.y), pi = fmaf(G2.y, G.x, -G2.x * G.y);
-            b = fmaf(atan2f(pi, pr), m.nd_over_2pi_f, b);
-        }
+        if (ANT) b += pat_bins;
         const float br = rintf(b);
         kb = __float2int_rn(b) & (m.n_doppler - 1);
         if (fabsf(b - br) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps)) fl |= kFlagRefine;
