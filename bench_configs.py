@@ -17,6 +17,7 @@
     nfast  fast mode against regular mode over the update interval n_fast and the Doppler
            bin count (N_d = n_fast, or 2 n_fast zero-padded), 2048 x 2048 surface.
     antenna  the 2048 x 2048 fast-mode pass with a tabulated u-v antenna pattern.
+    dda    delay-Doppler focusing of the fast- and regular-mode IQ of that surface.
 
 Every input is seeded and synthetic (the generator in ``scenegen``).  The FP64 oracle runs
 only inside each run's ``cpu_baseline`` leg, which times it on the host cores and returns
@@ -544,8 +545,44 @@ def run_antenna_table(torch, rsim, args):
     return line
 
 
+# ------------------------------------------------------------------ delay-Doppler focusing
+def run_delay_doppler(torch, rsim, args):
+    """Delay-Doppler focusing (Section IV.C) of the 2048 x 2048 fast-mode IQ (4096 pulses,
+    64 bursts of 64) and of the regular-mode IQ of the same surface: kernel time, and the
+    normalised mean multi-looked waveform of fast mode against regular mode (the comparison
+    of the paper's Fig. 9)."""
+    c = sg.config(1)
+    rd, pf, fp, P, L = c["radar"], c["platform"], c["fast"], c["n_pulses"], c["L"]
+    dev = rsim.Scatterers.from_arrays(sg.sea_surface(L, c["seed"]))
+    _, Yf = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, "split")
+    Yr = rsim.direct_sum(rd, pf, dev, 0, P, "split")
+    burst = 64
+    t = _timed(torch, lambda: rsim.delay_doppler(rd, pf, Yf, 0, burst, focused=True), 50)
+    t_ml = _timed(torch, lambda: rsim.delay_doppler(rd, pf, Yf, 0, burst), 50)
+    mlf, _ = rsim.delay_doppler(rd, pf, Yf, 0, burst)
+    mlr, _ = rsim.delay_doppler(rd, pf, Yr, 0, burst)
+    wf = mlf.double().mean(0)
+    wr = mlr.double().mean(0)
+    nf, nr = wf / wf.max(), wr / wr.max()
+    nb = P // burst
+    bytes_moved = P * rd.n_gates * 8 * 2 + nb * rd.n_gates * 4
+    line = _base_line("delay_doppler_fast_2048x2048_p4096", "delay-Doppler focusing time",
+                      "ms", round(t, 4), higher=False)
+    line["config"].update({"pulses": P, "burst": burst, "bursts": nb, "gates": rd.n_gates,
+                           "outputs": "focused beams + multi-look"})
+    line["multilook_only_ms"] = round(t_ml, 4)
+    line["roofline"] = {"bound": "hbm", "bytes_per_launch": bytes_moved,
+                        "achieved_gbs": round(bytes_moved / (t / 1e3) / 1e9, 1),
+                        "note": "one CTA per burst (%d CTAs): the launch is latency-bound" % nb}
+    line["normalised_mean_waveform"] = {
+        "fast": [round(float(v), 5) for v in nf], "regular": [round(float(v), 5) for v in nr],
+        "rel_l2_fast_vs_regular": float(torch.linalg.vector_norm(nf - nr) / torch.linalg.vector_norm(nr)),
+        "peak_gate_fast": int(torch.argmax(nf)), "peak_gate_regular": int(torch.argmax(nr))}
+    return line
+
+
 RUNS = {"0": run_cfg0, "2": run_cfg2, "3": run_cfg3, "4": run_cfg4, "nfast": run_nfast_sweep,
-        "antenna": run_antenna_table}
+        "antenna": run_antenna_table, "dda": run_delay_doppler}
 
 
 def run(k: str, args):

@@ -262,6 +262,29 @@ rsim_status rsim_scatterer_cells(const rsim_radar *radar, const rsim_platform *p
                                  rsim_precision precision, int32_t *gate, int32_t *bin,
                                  double *gate_coord, double *bin_coord, cudaStream_t stream);
 
+/* Delay-Doppler focusing of simulated IQ (Section IV.C): the pulses are split into bursts
+ * of `burst` consecutive pulses; per burst
+ *   1. Doppler centroid correction y_k *= exp(-j 2 pi nu_c k), k = 0 .. burst-1, with
+ *      nu_c = -2 v_z / (lambda PRF) the phase advance per pulse of the nadir echo;
+ *   2. along-track transform into Doppler beams B_f = sum_k y_k exp(-j 2 pi nu_f k),
+ *      nu_f = (f - burst/2) / burst;
+ *   3. range-migration correction with delay phase coefficients: beam f sees the
+ *      along-track offset x_f = nu_f lambda R_0 PRF / (2 |v_xy|) (flat earth, R_0 = r_ref at
+ *      the burst's centre pulse), whose range exceeds the nadir's by s_f = x_f^2 / (2 R_0)
+ *      (in gates: / gate_width); Y_f = IDFT(DFT(B_f) exp(+j 2 pi q' s_f / n_gates)), q' the
+ *      signed range frequency, IDFT normalised by 1 / n_gates (a shift of s_f gates towards
+ *      the nadir gate);
+ *   4. multi-look: W[g] = (1 / burst) sum_f |Y_f[g]|^2.
+ * iq        : [n_pulses][n_gates] complex64, pulse pulse0 first (pulse0 >= 0 sets the time of
+ *             each burst); bursts = floor(n_pulses / burst), trailing pulses unused;
+ * focused   : [bursts][burst][n_gates] complex64 (beam-major), OVERWRITTEN, or NULL;
+ * multilook : [bursts][n_gates] float, OVERWRITTEN.
+ * burst and n_gates must be powers of two >= 2 with burst * n_gates <= 12288 (one burst in
+ * shared memory), else RSIM_ERR_UNSUPPORTED.  Complex64 only (RSIM_SPLIT output). */
+rsim_status rsim_delay_doppler(const rsim_radar *radar, const rsim_platform *platform,
+                               const void *iq, int64_t pulse0, int32_t n_pulses, int32_t burst,
+                               void *focused, float *multilook, cudaStream_t stream);
+
 /* Per-scatterer complex amplitude C_n(t_pulse) of the radar equation and two-way phase
  * (Section II.A, Fig. 1 step 4; the model above), with the arithmetic of `precision`
  * exactly as the summation entry points evaluate it, for every scatterer whether or not

@@ -28,6 +28,7 @@ __all__ = [
     "doppler_accumulate", "doppler_accumulate_noalloc", "doppler_accumulate_batched",
     "autotune_batched", "Tuning",
     "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "scatterer_echo",
+    "delay_doppler",
     "synth_pulses_backward",
     "doppler_accumulate_backward", "direct_sum_backward", "spectra_range", "simulate_fast",
     "FastMode", "RegularMode", "version", "PRECISIONS", "WINDOWS",
@@ -333,6 +334,27 @@ def scatterer_echo(radar, platform, scat: Scatterers, pulse: int, precision: str
                                             int(pulse), _prec(precision), _ptr(out),
                                             _stream(stream)))
     return out
+
+
+def delay_doppler(radar, platform, iq: torch.Tensor, pulse0: int = 0, burst: int = 64,
+                  focused: bool = False, stream=None):
+    """Delay-Doppler focusing of IQ [n_pulses, n_gates] complex64 (rsim_delay_doppler,
+    Section IV.C): bursts of ``burst`` pulses, centroid correction, along-track beams,
+    range-migration delay phases, multi-look.  Returns ``(multilook, beams)``: float32
+    [bursts, n_gates] and, when ``focused``, complex64 [bursts, burst, n_gates] (else None)."""
+    if iq.dtype != torch.complex64 or iq.dim() != 2 or iq.shape[1] != radar.n_gates:
+        raise TypeError("iq must be complex64 [n_pulses, n_gates]")
+    iq = iq.contiguous()
+    nb = iq.shape[0] // int(burst)
+    ml = torch.empty((nb, radar.n_gates), dtype=torch.float32, device=iq.device)
+    beams = (torch.empty((nb, int(burst), radar.n_gates), dtype=torch.complex64, device=iq.device)
+             if focused else None)
+    rd, pf = _lib.make_radar(radar), _lib.make_platform(platform)
+    _lib.check(_lib.lib.rsim_delay_doppler(ctypes.byref(rd), ctypes.byref(pf), _ptr(iq),
+                                           int(pulse0), int(iq.shape[0]), int(burst),
+                                           _ptr(beams) if beams is not None else None, _ptr(ml),
+                                           _stream(stream)))
+    return ml, beams
 
 
 def synth_pulses_backward(radar, grad_iq: torch.Tensor, n_spectra: int, update0: int,

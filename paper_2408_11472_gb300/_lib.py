@@ -80,6 +80,7 @@ PROTOTYPES = {
     "rsim_scatterer_cells": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P, _P],
                              ctypes.c_int),
     "rsim_scatterer_echo": ([_RP, _PP, _SP, _I64, ctypes.c_int, _P, _P], ctypes.c_int),
+    "rsim_delay_doppler": ([_RP, _PP, _P, _I64, _I32, _I32, _P, _P, _P], ctypes.c_int),
     "rsim_synth_pulses_backward": ([_RP, _P, _I32, _I64, _I32, _I32, _I64, _I32, ctypes.c_int,
                                     ctypes.c_int, _P, _P], ctypes.c_int),
     "rsim_doppler_accumulate_backward": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,

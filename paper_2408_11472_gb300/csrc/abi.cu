@@ -380,6 +380,43 @@ rsim_status rsim_scatterer_cells(const rsim_radar* radar, const rsim_platform* p
     return RSIM_OK;
 }
 
+rsim_status rsim_delay_doppler(const rsim_radar* radar, const rsim_platform* platform,
+                               const void* iq, int64_t pulse0, int32_t n_pulses, int32_t burst,
+                               void* focused, float* multilook, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_platform(platform)) != RSIM_OK) return st;
+    if (pulse0 < 0 || n_pulses < 0) return fail(RSIM_ERR_INVALID_ARG, "negative pulse index or count");
+    if (!is_pow2(burst) || burst < 2 || !is_pow2(radar->n_gates) || radar->n_gates < 2 ||
+        (int64_t)burst * radar->n_gates > 12288)
+        return fail(RSIM_ERR_UNSUPPORTED, "burst=%d, n_gates=%d: need powers of two >= 2 with "
+                    "burst * n_gates <= 12288", burst, radar->n_gates);
+    const int64_t n_bursts = n_pulses / burst;
+    if (n_bursts == 0) return RSIM_OK;
+    if (!iq || !multilook) return fail(RSIM_ERR_INVALID_ARG, "iq / multilook is NULL");
+    if (!aligned(iq, 8) || !aligned(multilook, 4) || (focused && !aligned(focused, 8)))
+        return fail(RSIM_ERR_INVALID_ARG, "iq / focused / multilook misaligned");
+    rsim::DdArgs a;
+    a.n_gates = radar->n_gates;
+    a.burst = burst;
+    a.log2_g = 0;
+    while ((1 << a.log2_g) < radar->n_gates) ++a.log2_g;
+    a.log2_b = 0;
+    while ((1 << a.log2_b) < burst) ++a.log2_b;
+    a.pulse0 = pulse0;
+    a.lambda = radar->c_mps / radar->carrier_hz;
+    a.prf = radar->prf_hz;
+    a.inv_prf = 1.0 / radar->prf_hz;
+    a.nu_c = -2.0 * platform->v[2] / (a.lambda * radar->prf_hz);
+    a.vh = std::hypot(platform->v[0], platform->v[1]);
+    a.gate_width = radar->gate_width_m;
+    a.r_ref0 = platform->r_ref0;
+    a.r_ref_rate = platform->r_ref_rate;
+    const cudaError_t e = rsim::launch_dd_focus(a, n_bursts, iq, focused, multilook, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "delay-Doppler kernel launch");
+    return RSIM_OK;
+}
+
 rsim_status rsim_scatterer_echo(const rsim_radar* radar, const rsim_platform* platform,
                                 const rsim_scatterers* scat, int64_t pulse,
                                 rsim_precision precision, void* contrib, cudaStream_t stream) {

@@ -43,4 +43,15 @@ cudaError_t launch_synth(const SynthArgs& a, bool fp64, const void* spectra, voi
 cudaError_t launch_synth_backward(const SynthArgs& a, bool fp64, const void* grad_iq,
                                   void* grad_spectra, cudaStream_t stream);
 
+// Delay-Doppler focusing (ddfocus.cu).
+struct DdArgs {
+    int n_gates, burst, log2_g, log2_b;
+    int64_t pulse0;
+    double nu_c;                 // Doppler centroid, cycles per pulse
+    double lambda, prf, inv_prf, vh, gate_width, r_ref0, r_ref_rate;
+};
+size_t dd_focus_smem_bytes(int burst, int n_gates);
+cudaError_t launch_dd_focus(const DdArgs& a, int64_t n_bursts, const void* iq, void* focused,
+                            float* multilook, cudaStream_t stream);
+
 }  // namespace rsim
