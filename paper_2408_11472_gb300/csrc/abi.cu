@@ -387,10 +387,10 @@ rsim_status rsim_delay_doppler(const rsim_radar* radar, const rsim_platform* pla
     if ((st = check_radar(radar)) != RSIM_OK) return st;
     if ((st = check_platform(platform)) != RSIM_OK) return st;
     if (pulse0 < 0 || n_pulses < 0) return fail(RSIM_ERR_INVALID_ARG, "negative pulse index or count");
-    if (!is_pow2(burst) || burst < 2 || !is_pow2(radar->n_gates) || radar->n_gates < 2 ||
-        (int64_t)burst * radar->n_gates > 12288)
-        return fail(RSIM_ERR_UNSUPPORTED, "burst=%d, n_gates=%d: need powers of two >= 2 with "
-                    "burst * n_gates <= 12288", burst, radar->n_gates);
+    if (!is_pow2(burst) || burst < 2 || burst > 1024 || !is_pow2(radar->n_gates) ||
+        radar->n_gates < 2 || (int64_t)burst * radar->n_gates > 12288)
+        return fail(RSIM_ERR_UNSUPPORTED, "burst=%d, n_gates=%d: need powers of two >= 2, "
+                    "burst <= 1024, burst * n_gates <= 12288", burst, radar->n_gates);
     const int64_t n_bursts = n_pulses / burst;
     if (n_bursts == 0) return RSIM_OK;
     if (!iq || !multilook) return fail(RSIM_ERR_INVALID_ARG, "iq / multilook is NULL");

@@ -31,7 +31,9 @@ __global__ void __launch_bounds__(512) dd_focus_kernel(DdArgs a, const float2* _
     float2* tw_b = reinterpret_cast<float2*>(smem_raw);   // exp(-j 2 pi r / Nb), r < Nb/2
     float2* tw_gf = tw_b + (Nb >> 1);                      // exp(-j 2 pi r / G)
     float2* tw_gi = tw_gf + (G >> 1);                      // exp(+j 2 pi r / G)
-    float2* buf0 = tw_gi + (G >> 1);
+    float2* cent = tw_gi + (G >> 1);                       // per pulse: centroid factor
+    float2* shift = cent + Nb;                              // per beam: s_f / G (hi, lo)
+    float2* buf0 = shift + Nb;
     float2* buf1 = buf0 + Nb * G;
     const int64_t b = blockIdx.x;
     for (int r = threadIdx.x; r < (Nb >> 1); r += blockDim.x) twiddle(r, Nb, -1.0f, tw_b[r]);
@@ -39,19 +41,29 @@ __global__ void __launch_bounds__(512) dd_focus_kernel(DdArgs a, const float2* _
         twiddle(r, G, -1.0f, tw_gf[r]);
         twiddle(r, G, 1.0f, tw_gi[r]);
     }
-    // 1. load the burst (pulse-major rows), centroid correction and beam centring, stored
-    //    gate-major ([g][k]) for the along-track transforms
+    // per pulse: exp(-j 2 pi nu_c k) (-1)^k (centroid correction and beam centring);
+    // per beam: the migration in range-transform cycles s_f / G as hi + lo floats
+    const double r0 = fma(a.r_ref_rate, (double)(a.pulse0 + b * Nb + Nb / 2) * a.inv_prf, a.r_ref0);
+    for (int k = threadIdx.x; k < Nb; k += blockDim.x) {
+        double ph = a.nu_c * (double)k;                    // cycles
+        ph -= rint(ph);
+        double s, c;
+        sincospi(-2.0 * ph, &s, &c);
+        const float sg = (k & 1) ? -1.0f : 1.0f;
+        cent[k] = make_float2(sg * (float)c, sg * (float)s);
+        const double nu = (double)(k - Nb / 2) / (double)Nb;
+        const double x = a.vh > 0.0 ? nu * a.lambda * r0 * a.prf / (2.0 * a.vh) : 0.0;
+        const double sfg = x * x / (2.0 * r0 * a.gate_width) / (double)G;
+        const float hi = (float)sfg;
+        shift[k] = make_float2(hi, (float)(sfg - (double)hi));
+    }
+    __syncthreads();
+    // 1. load the burst (pulse-major rows), apply the per-pulse factor, store gate-major
+    //    ([g][k]) for the along-track transforms
     const float2* src = iq + b * (int64_t)Nb * G;
     for (int idx = threadIdx.x; idx < Nb * G; idx += blockDim.x) {
         const int k = idx / G, g = idx - k * G;
-        double ph = a.nu_c * (double)k;                    // cycles
-        ph -= rint(ph);
-        float s, c;
-        sincospif(-2.0f * (float)ph, &s, &c);
-        float2 v = __ldg(src + idx);
-        v = cmul(v, make_float2(c, s));
-        if (k & 1) v = make_float2(-v.x, -v.y);
-        buf0[g * Nb + k] = v;
+        buf0[g * Nb + k] = cmul(__ldg(src + idx), cent[k]);
     }
     __syncthreads();
     // 2. along-track transforms: rows = gates
@@ -65,17 +77,16 @@ __global__ void __launch_bounds__(512) dd_focus_kernel(DdArgs a, const float2* _
     __syncthreads();
     res = stockham(other, res, Nb, G, a.log2_g, tw_gf);
     other = (res == buf0) ? buf1 : buf0;
-    const double r0 = fma(a.r_ref_rate, (double)(a.pulse0 + b * Nb + Nb / 2) * a.inv_prf, a.r_ref0);
     for (int idx = threadIdx.x; idx < Nb * G; idx += blockDim.x) {
         const int f = idx / G, q = idx - f * G;
-        const double nu = (double)(f - Nb / 2) / (double)Nb;
-        const double x = a.vh > 0.0 ? nu * a.lambda * r0 * a.prf / (2.0 * a.vh) : 0.0;
-        const double sf = x * x / (2.0 * r0 * a.gate_width);
-        const int qs = q < G / 2 ? q : q - G;              // signed range frequency
-        double ph = (double)qs * sf / (double)G;           // cycles
-        ph -= rint(ph);
+        const float qs = (float)(q < G / 2 ? q : q - G);   // signed range frequency
+        const float2 sh = shift[f];
+        // q' s_f / G in cycles: the product with the hi part is split error-free
+        const float p = qs * sh.x;
+        const float pe = fmaf(qs, sh.x, -p);
+        const float ph = (p - rintf(p)) + fmaf(qs, sh.y, pe);
         float s, c;
-        sincospif(2.0f * (float)ph, &s, &c);
+        sincospif(2.0f * ph, &s, &c);
         res[idx] = cmul(res[idx], make_float2(c, s));
     }
     __syncthreads();
@@ -100,7 +111,8 @@ __global__ void __launch_bounds__(512) dd_focus_kernel(DdArgs a, const float2* _
 }  // namespace
 
 size_t dd_focus_smem_bytes(int burst, int n_gates) {
-    return sizeof(float2) * ((size_t)(burst / 2) + (size_t)n_gates + 2 * (size_t)burst * n_gates);
+    return sizeof(float2) * ((size_t)(burst / 2) + (size_t)n_gates + 2 * (size_t)burst +
+                             2 * (size_t)burst * n_gates);
 }
 
 cudaError_t launch_dd_focus(const DdArgs& a, int64_t n_bursts, const void* iq, void* focused,

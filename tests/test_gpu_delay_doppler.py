@@ -65,3 +65,6 @@ def test_shapes_and_rejections(rsim):
         rsim.delay_doppler(rd, pf, torch.zeros((256, 128), dtype=torch.complex64, device="cuda"), 0, 128)
     with pytest.raises(rsim.RsimError):
         rsim.delay_doppler(rd, pf, torch.zeros((64, 128), dtype=torch.complex64, device="cuda"), 0, 48)
+    with pytest.raises(rsim.RsimError):      # bursts longer than 1024 pulses
+        rsim.delay_doppler(sg.RadarParams(n_gates=2), pf,
+                           torch.zeros((2048, 2), dtype=torch.complex64, device="cuda"), 0, 2048)
