@@ -9,7 +9,8 @@ Two independent restatements of the paper's method live here:
 * ``rsim_oracle.c`` (plain C, OpenMP over fixed chunks, compensated sums,
   direct O(N_d^2) DFT), wrapped by :class:`Oracle` through ctypes;
 * ``bruteforce.py`` (vectorised numpy, for tiny inputs), used to pin the C code;
-* ``delay_doppler.py`` (numpy): delay-Doppler focusing of the IQ (Section IV.C).
+* ``delay_doppler.py`` (numpy): delay-Doppler focusing of the IQ (Section IV.C);
+* ``surface.py`` (numpy): the spectral surface update at each update time.
 
 Pins (see ``tests/test_oracle_*.py``): closed-form point-scatterer gate, phase
 and amplitude; the antenna 3 dB point; update-pulse identity; static scene;

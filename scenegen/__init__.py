@@ -49,6 +49,7 @@ __all__ = [
     "WINDOWS",
     "nadir_track",
     "sea_surface",
+    "sea_spectrum",
     "point_scene",
     "random_spectra",
     "random_iq",
@@ -224,6 +225,37 @@ def sea_surface(L: int, seed: int, spacing: float = 1.0, height_std: float = 0.5
     out["origin"] = (0.0, 0.0, 0.0)
     out["area"] = float(spacing * spacing)
     return out
+
+
+def sea_spectrum(L: int, seed: int, spacing: float = 1.0, height_std: float = 0.5,
+                 k_peak: float = 2.0 * math.pi / 100.0, sigma_k: Optional[float] = None,
+                 nrcs_mu: float = -2.0, nrcs_sigma: float = 0.5) -> Dict[str, object]:
+    """The spectral description behind ``sea_surface(L, seed, ...)`` (same draws): the
+    one-sided complex wave coefficients ``coef`` [L, L] (complex128, index [iy, ix], wave
+    numbers 2 pi fftfreq(L, spacing) along x and y), the amplitude ``scale`` that gives the
+    t = 0 heights a standard deviation of ``height_std``, the facet grid x, y and the NRCS
+    (float32, length L*L), ``origin``, ``area``, ``spacing``.  The surface at time t is
+    synthesised from these by the spectral update (linear deep-water waves)."""
+    if L < 2:
+        raise ValueError("L must be >= 2")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    re = rng.standard_normal((L, L))
+    im = rng.standard_normal((L, L))
+    ln_nrcs = rng.normal(nrcs_mu, nrcs_sigma, size=(L, L))
+    if sigma_k is None:
+        sigma_k = max(0.006, 3.0 * 2.0 * math.pi / (L * spacing))
+    k1 = 2.0 * math.pi * np.fft.fftfreq(L, d=spacing)
+    kx, ky = k1[None, :], k1[:, None]
+    spec = np.exp(-((kx - k_peak) ** 2 + ky ** 2) / (2.0 * sigma_k ** 2))
+    spec = np.where(kx > 0.0, spec, 0.0)
+    coef = np.sqrt(spec) * (re + 1j * im) / math.sqrt(2.0)
+    scale = height_std / float(np.std(np.real(np.fft.ifft2(coef))))
+    xs = (np.arange(L, dtype=np.float64) - (L - 1) / 2.0) * spacing
+    return {"coef": coef, "scale": scale, "spacing": float(spacing), "L": int(L),
+            "x": np.broadcast_to(xs[None, :], (L, L)).astype(np.float32).ravel(),
+            "y": np.broadcast_to(xs[:, None], (L, L)).astype(np.float32).ravel(),
+            "nrcs": np.exp(ln_nrcs).astype(np.float32).ravel(),
+            "origin": (0.0, 0.0, 0.0), "area": float(spacing * spacing)}
 
 
 def point_scene(points, area: float = 1.0, origin=(0.0, 0.0, 0.0)) -> Dict[str, object]:
