@@ -163,7 +163,7 @@ def main():
     ap.add_argument("--L", type=int, default=None, help="surface side (default: 2048)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e / regular / FP64 / oracle legs (profiling runs)")
-    ap.add_argument("--config", default=None, choices=["0", "2", "3", "4", "nfast", "antenna", "dda"],
+    ap.add_argument("--config", default=None, choices=["0", "2", "3", "4", "nfast", "antenna", "dda", "surface"],
                     help="run another measurement configuration instead (bench_configs.py)")
     args = ap.parse_args()
 

@@ -18,6 +18,7 @@
            bin count (N_d = n_fast, or 2 n_fast zero-padded), 2048 x 2048 surface.
     antenna  the 2048 x 2048 fast-mode pass with a tabulated u-v antenna pattern.
     dda    delay-Doppler focusing of the fast- and regular-mode IQ of that surface.
+    surface  fast mode with the surface regenerated at every update from its spectrum.
 
 Every input is seeded and synthetic (the generator in ``scenegen``).  The FP64 oracle runs
 only inside each run's ``cpu_baseline`` leg, which times it on the host cores and returns
@@ -581,8 +582,50 @@ def run_delay_doppler(torch, rsim, args):
     return line
 
 
+# ------------------------------------------------------------------ surface update
+def run_surface_update(torch, rsim, args):
+    """Fast mode with the surface regenerated at every update (Algorithm 1 in full) on the
+    2048 x 2048 surface, 4096 pulses: time of one surface synthesis (two packed 2048 x 2048
+    inverse transforms), of the whole step, and against the linear-kinematics step."""
+    c = sg.config(1)
+    rd, pf, fp, P, L = c["radar"], c["platform"], c["fast"], c["n_pulses"], c["L"]
+    spec = sg.sea_spectrum(L, c["seed"])
+    surf = rsim.EvolvingSurface(spec)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    t_surf = _timed(torch, lambda: surf.at(0.1234), 20, flush)
+    S = (P - 1) // fp.n_fast + 2
+    ws = torch.empty(rsim.workspace_size(S, rd.n_gates, fp.n_doppler), dtype=torch.uint8,
+                     device="cuda")
+
+    def evolving():
+        rsim.simulate_fast_evolving(rd, pf, surf, P, fp.n_fast, fp.n_doppler, fp.window, "split",
+                                    workspace=ws)
+
+    frozen = rsim.Scatterers.from_arrays(sg.sea_surface(L, c["seed"]))
+
+    def linear():
+        rsim.simulate_fast(rd, pf, frozen, P, fp.n_fast, fp.n_doppler, fp.window, "split",
+                           workspace=ws)
+
+    t_evo = _timed(torch, evolving, 5, flush)
+    t_lin = _timed(torch, linear, 5, flush)
+    # algorithmic bytes of one synthesis: read A (8 L^2) + omega (8 L^2), write/read the packed
+    # transforms (2 x 2 x 8 L^2), write 4 fields (16 L^2)
+    nbytes = 8 * L * L + 8 * L * L + 32 * L * L + 16 * L * L
+    line = _base_line("fast_2048x2048_p4096_evolving_surface",
+                      "fast-mode IQ pulses/s with the surface regenerated per update", "IQ pulses/s",
+                      round(P / (t_evo / 1e3), 1))
+    line["config"].update({"grid": L, "pulses": P, "updates": S, "window": fp.window,
+                           "precision": "split", "l2": "flushed before each timed call"})
+    line["surface_synthesis_ms"] = round(t_surf, 4)
+    line["surface_synthesis_roofline"] = {"bound": "hbm", "bytes": nbytes,
+                                          "achieved_gbs": round(nbytes / (t_surf / 1e3) / 1e9, 1)}
+    line["step_ms"] = {"evolving_surface": round(t_evo, 3), "linear_kinematics": round(t_lin, 3)}
+    return line
+
+
 RUNS = {"0": run_cfg0, "2": run_cfg2, "3": run_cfg3, "4": run_cfg4, "nfast": run_nfast_sweep,
-        "antenna": run_antenna_table, "dda": run_delay_doppler}
+        "antenna": run_antenna_table, "dda": run_delay_doppler, "surface": run_surface_update}
 
 
 def run(k: str, args):

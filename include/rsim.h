@@ -286,6 +286,42 @@ rsim_status rsim_delay_doppler(const rsim_radar *radar, const rsim_platform *pla
                                const void *iq, int64_t pulse0, int32_t n_pulses, int32_t burst,
                                void *focused, float *multilook, cudaStream_t stream);
 
+/* Sea-surface spectrum for the surface update at each update time (Algorithm 1's
+ * update_simulation regenerates the surface at every update).  Linear deep-water waves:
+ * one-sided complex coefficients A(k) on the L x L wave-number grid k = 2 pi fftfreq(L,
+ * spacing) (index [iy][ix]), omega = sqrt(g |k|), and at time t
+ *   z   = s Re IFFT2[A e^{-j omega t}],            v_z = s Re IFFT2[-j omega A e^{-j omega t}],
+ *   v_x = s Re IFFT2[omega k_x/|k| A e^{-j omega t}], v_y = s Re IFFT2[omega k_y/|k| A ...],
+ * IFFT2 normalised by 1 / L^2, on the facet grid x = (ix - (L-1)/2) spacing (y likewise),
+ * row-major n = iy L + ix.
+ * coef : DEVICE [L][L] complex64, 8-byte aligned; L a power of two in [2, 4096]. */
+typedef struct {
+    const void *coef;
+    int32_t L;
+    int32_t reserved;    /* must be 0 */
+    double spacing;      /* facet grid step (m), > 0 */
+    double scale;        /* amplitude scale s */
+    double g;            /* gravity (m/s^2), > 0 */
+} rsim_wave_spectrum;
+
+/* Workspace bytes of the surface update: a table of omega / (2 pi) (8 L^2 bytes) and two
+ * packed L x L complex transforms (16 L^2 bytes). */
+size_t rsim_surface_workspace_size(int32_t L);
+
+/* Fills the workspace's omega table for `spectrum` (once per spectrum and workspace; the
+ * table depends on L, spacing and g only).  Asynchronous on `stream`. */
+rsim_status rsim_surface_prepare(const rsim_wave_spectrum *spectrum, void *workspace,
+                                 size_t workspace_bytes, cudaStream_t stream);
+
+/* The surface at time t (seconds): heights z and velocities vx, vy, vz ([L*L] float DEVICE
+ * arrays, OVERWRITTEN) by two packed L x L inverse transforms per call (eta + j v_z and
+ * v_x + j v_y: each real field is the transform of the Hermitian part of its spectrum).
+ * The workspace must have been prepared for this spectrum (rsim_surface_prepare).  With
+ * the facet grid and NRCS these are a scatterer set whose state epoch t0 is t. */
+rsim_status rsim_surface_at(const rsim_wave_spectrum *spectrum, double t, float *z, float *vx,
+                            float *vy, float *vz, void *workspace, size_t workspace_bytes,
+                            cudaStream_t stream);
+
 /* Per-scatterer complex amplitude C_n(t_pulse) of the radar equation and two-way phase
  * (Section II.A, Fig. 1 step 4; the model above), with the arithmetic of `precision`
  * exactly as the summation entry points evaluate it, for every scatterer whether or not

@@ -28,7 +28,7 @@ __all__ = [
     "doppler_accumulate", "doppler_accumulate_noalloc", "doppler_accumulate_batched",
     "autotune_batched", "Tuning",
     "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "scatterer_echo",
-    "delay_doppler",
+    "delay_doppler", "EvolvingSurface", "simulate_fast_evolving",
     "synth_pulses_backward",
     "doppler_accumulate_backward", "direct_sum_backward", "spectra_range", "simulate_fast",
     "FastMode", "RegularMode", "version", "PRECISIONS", "WINDOWS",
@@ -479,6 +479,66 @@ class RegularMode(torch.autograd.Function):
         s, radar, platform, pulse0 = ctx.args
         gz, gs = direct_sum_backward(radar, platform, s, pulse0, grad_y.contiguous())
         return gz, gs, None, None, None, None, None, None
+
+
+class EvolvingSurface:
+    """The sea surface regenerated at each update from its wave spectrum (rsim_surface_at;
+    Algorithm 1's update_simulation): the facet grid and NRCS are fixed, heights and
+    velocities are synthesised at time t by two packed L x L inverse transforms.
+
+    ``spectrum``: dict with ``coef`` (one-sided complex coefficients [L, L]), ``scale``,
+    ``spacing``, ``x``, ``y``, ``nrcs``, ``origin``, ``area`` (as ``scenegen.sea_spectrum``
+    returns).  ``at(t)`` returns a Scatterers view of the surface at t (state epoch t0 = t)
+    whose arrays are overwritten by the next call."""
+
+    def __init__(self, spectrum: dict, device="cuda", g: float = 9.81):
+        coef = torch.as_tensor(spectrum["coef"])
+        L = int(coef.shape[0])
+        if coef.dim() != 2 or coef.shape[1] != L:
+            raise ValueError("coef must be [L, L]")
+        self.L = L
+        self.coef = coef.to(device=device, dtype=torch.complex64).contiguous()
+        dev = self.coef.device
+        f32 = dict(device=dev, dtype=torch.float32)
+        self.x = torch.as_tensor(spectrum["x"]).to(**f32).contiguous()
+        self.y = torch.as_tensor(spectrum["y"]).to(**f32).contiguous()
+        self.nrcs = torch.as_tensor(spectrum["nrcs"]).to(**f32).contiguous()
+        self.origin = tuple(spectrum.get("origin", (0.0, 0.0, 0.0)))
+        self.area = float(spectrum.get("area", 1.0))
+        self.z, self.vx, self.vy, self.vz = (torch.empty(L * L, **f32) for _ in range(4))
+        self.spec = _lib.WaveSpectrum(self.coef.data_ptr(), L, 0, float(spectrum["spacing"]),
+                                      float(spectrum["scale"]), float(g))
+        n = int(_lib.lib.rsim_surface_workspace_size(L))
+        self.workspace = torch.empty(n, dtype=torch.uint8, device=dev)
+        _lib.check(_lib.lib.rsim_surface_prepare(ctypes.byref(self.spec), _ptr(self.workspace),
+                                                 n, _stream(None)))
+
+    def at(self, t: float, stream=None) -> Scatterers:
+        _lib.check(_lib.lib.rsim_surface_at(
+            ctypes.byref(self.spec), float(t), _ptr(self.z), _ptr(self.vx), _ptr(self.vy),
+            _ptr(self.vz), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
+        return Scatterers(self.x, self.y, self.z, self.vx, self.vy, self.vz, self.nrcs,
+                          origin=self.origin, area=self.area, t0=float(t))
+
+
+def simulate_fast_evolving(radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
+                           n_doppler: int, window: str = "sqrt_raised_cosine",
+                           precision: str = "split", pulse0: int = 0,
+                           workspace: Optional[torch.Tensor] = None, stream=None):
+    """Fast mode with the surface regenerated at every update (Algorithm 1 in full): for each
+    update i the surface at t_i = p_i / PRF, its Doppler spectrum, then the post-processing.
+    Returns (spectra, iq)."""
+    u0, S = spectra_range(pulse0, n_pulses, n_fast)
+    G = radar.n_gates
+    dev = surface.coef.device
+    T = torch.zeros((S, G, n_doppler), dtype=_cdtype(precision), device=dev)
+    ws = _workspace(workspace, workspace_size(1, G, n_doppler), dev)
+    for s in range(S):
+        sc = surface.at((u0 + s) * n_fast / radar.prf_hz, stream=stream)
+        doppler_accumulate(radar, platform, sc, u0 + s, 1, n_fast, n_doppler, precision,
+                           out=T[s:s + 1], workspace=ws, stream=stream)
+    Y = synth_pulses(radar, T, u0, n_fast, pulse0, n_pulses, window, stream=stream)
+    return T, Y
 
 
 class BatchedFastMode:

@@ -60,6 +60,11 @@ class Tuning(ctypes.Structure):
                                                                      self.samples_per_group)
 
 
+class WaveSpectrum(ctypes.Structure):
+    _fields_ = [("coef", ctypes.c_void_p), ("L", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("spacing", ctypes.c_double), ("scale", ctypes.c_double), ("g", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _RP = ctypes.POINTER(Radar)
 _PP = ctypes.POINTER(Platform)
@@ -81,6 +86,10 @@ PROTOTYPES = {
                              ctypes.c_int),
     "rsim_scatterer_echo": ([_RP, _PP, _SP, _I64, ctypes.c_int, _P, _P], ctypes.c_int),
     "rsim_delay_doppler": ([_RP, _PP, _P, _I64, _I32, _I32, _P, _P, _P], ctypes.c_int),
+    "rsim_surface_workspace_size": ([_I32], ctypes.c_size_t),
+    "rsim_surface_prepare": ([ctypes.POINTER(WaveSpectrum), _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "rsim_surface_at": ([ctypes.POINTER(WaveSpectrum), ctypes.c_double, _P, _P, _P, _P, _P,
+                         ctypes.c_size_t, _P], ctypes.c_int),
     "rsim_synth_pulses_backward": ([_RP, _P, _I32, _I64, _I32, _I32, _I64, _I32, ctypes.c_int,
                                     ctypes.c_int, _P, _P], ctypes.c_int),
     "rsim_doppler_accumulate_backward": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,

@@ -417,6 +417,70 @@ rsim_status rsim_delay_doppler(const rsim_radar* radar, const rsim_platform* pla
     return RSIM_OK;
 }
 
+static rsim_status surface_args(const rsim_wave_spectrum* sp, rsim::SurfArgs* a) {
+    if (!sp) return fail(RSIM_ERR_INVALID_ARG, "spectrum is NULL");
+    if (!is_pow2(sp->L) || sp->L < 2 || sp->L > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "spectrum L=%d must be a power of two in [2, 4096]", sp->L);
+    if (!sp->coef || !aligned(sp->coef, 8))
+        return fail(RSIM_ERR_INVALID_ARG, "spectrum coef is NULL or not 8-byte aligned");
+    if (sp->reserved != 0) return fail(RSIM_ERR_INVALID_ARG, "spectrum.reserved must be 0");
+    if (!finite_pos(sp->spacing) || !finite_pos(sp->g) || !std::isfinite(sp->scale))
+        return fail(RSIM_ERR_INVALID_ARG, "spectrum spacing, g must be finite and > 0, scale finite");
+    a->L = sp->L;
+    a->log2L = 0;
+    while ((1 << a->log2L) < sp->L) ++a->log2L;
+    int c = 8;
+    while (c > 1 && ((int64_t)c * sp->L > 12288 || c > sp->L)) c >>= 1;
+    a->cols = c;
+    a->dk = 6.283185307179586476925 / ((double)sp->L * sp->spacing);
+    a->g = sp->g;
+    a->t_hi = 0.f;
+    a->t_lo = 0.f;
+    a->scale_over_L2 = (float)(sp->scale / ((double)sp->L * (double)sp->L));
+    return RSIM_OK;
+}
+
+size_t rsim_surface_workspace_size(int32_t L) {
+    if (L < 1) return 0;
+    return (size_t)24 * (size_t)L * (size_t)L;
+}
+
+rsim_status rsim_surface_prepare(const rsim_wave_spectrum* spectrum, void* workspace,
+                                 size_t workspace_bytes, cudaStream_t stream) {
+    rsim::SurfArgs a;
+    rsim_status st = surface_args(spectrum, &a);
+    if (st != RSIM_OK) return st;
+    const size_t need = rsim_surface_workspace_size(a.L);
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < need)
+        return fail(RSIM_ERR_WORKSPACE, "surface workspace: need %zu bytes, 256-byte aligned", need);
+    const cudaError_t e = rsim::launch_surf_prepare(a, static_cast<float2*>(workspace), device_sms(),
+                                                    stream);
+    if (e != cudaSuccess) return cuda_fail(e, "surface prepare kernel launch");
+    return RSIM_OK;
+}
+
+rsim_status rsim_surface_at(const rsim_wave_spectrum* spectrum, double t, float* z, float* vx,
+                            float* vy, float* vz, void* workspace, size_t workspace_bytes,
+                            cudaStream_t stream) {
+    rsim::SurfArgs a;
+    rsim_status st = surface_args(spectrum, &a);
+    if (st != RSIM_OK) return st;
+    if (!std::isfinite(t)) return fail(RSIM_ERR_INVALID_ARG, "t must be finite");
+    const size_t need = rsim_surface_workspace_size(a.L);
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < need)
+        return fail(RSIM_ERR_WORKSPACE, "surface workspace: need %zu bytes, 256-byte aligned", need);
+    float* outs[4] = {z, vx, vy, vz};
+    for (int i = 0; i < 4; ++i)
+        if (!outs[i] || !aligned(outs[i], 4)) return fail(RSIM_ERR_INVALID_ARG, "output field NULL or misaligned");
+    a.t_hi = (float)t;
+    a.t_lo = (float)(t - (double)a.t_hi);
+    float2* omega = static_cast<float2*>(workspace);
+    float2* tmp = omega + (size_t)a.L * a.L;
+    const cudaError_t e = rsim::launch_surf_at(a, spectrum->coef, omega, tmp, z, vx, vy, vz, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "surface kernels launch");
+    return RSIM_OK;
+}
+
 rsim_status rsim_scatterer_echo(const rsim_radar* radar, const rsim_platform* platform,
                                 const rsim_scatterers* scat, int64_t pulse,
                                 rsim_precision precision, void* contrib, cudaStream_t stream) {

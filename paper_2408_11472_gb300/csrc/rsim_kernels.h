@@ -54,4 +54,17 @@ size_t dd_focus_smem_bytes(int burst, int n_gates);
 cudaError_t launch_dd_focus(const DdArgs& a, int64_t n_bursts, const void* iq, void* focused,
                             float* multilook, cudaStream_t stream);
 
+// Spectral surface update (surface.cu).
+struct SurfArgs {
+    int L, log2L, cols;          // grid side (power of two), columns per column-pass CTA
+    double dk, g;                // wave-number step 2 pi / (L spacing), gravity
+    float t_hi, t_lo;            // update time as hi + lo
+    float scale_over_L2;         // amplitude scale / L^2
+};
+size_t surf_rows_smem(int L);
+size_t surf_cols_smem(int L, int cols);
+cudaError_t launch_surf_prepare(const SurfArgs& a, float2* omega, int n_sms, cudaStream_t stream);
+cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const float2* omega, float2* tmp,
+                           float* z, float* vx, float* vy, float* vz, cudaStream_t stream);
+
 }  // namespace rsim

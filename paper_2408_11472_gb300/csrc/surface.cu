@@ -1,0 +1,154 @@
+// surface.cu -- spectral update of the sea surface at an update time (Algorithm 1's
+// update_simulation: the surface is regenerated at every update), for sm_103a.
+//
+// Linear deep-water waves from one-sided coefficients A(k) on the L x L wave-number grid
+// (index [iy][ix], k = 2 pi fftfreq(L, spacing)), omega = sqrt(g |k|):
+//   eta = s Re IFFT2[A e^{-j omega t}],  v_z = s Re IFFT2[-j omega A e^{-j omega t}],
+//   v_x = s Re IFFT2[omega k_x/|k| A e^{-j omega t}],  v_y likewise with k_y,
+// IFFT2 normalised by 1/L^2.  Each real field is the inverse transform of the Hermitian part
+// H(k) = (X(k) + conj(X(-k))) / 2 of its spectrum X, so two real fields share one complex
+// transform: IFFT2[H_a + j H_b] = a + j b.  Two packed transforms (eta + j v_z,
+// v_x + j v_y) per update:
+//   rows pass    : one CTA per row iy builds both packed rows from A(k), A(-k) and the
+//                  phase e^{-j omega t}, and transforms them along x (shared memory);
+//   columns pass : one CTA per block of columns transforms along y and writes the fields.
+// omega / (2 pi) is tabulated once per spectrum (FP64, stored as hi + lo floats) so that
+// the phase omega t stays accurate to ~1e-7 cycles for t of hours.
+#include "rsim_internal.cuh"
+#include "rsim_kernels.h"
+#include "fft_smem.cuh"
+
+namespace rsim {
+
+namespace {
+
+using namespace fft;
+
+__device__ __forceinline__ double wave_number(int i, int L, double dk) {
+    return (double)(i < L / 2 ? i : i - L) * dk;      // 2 pi fftfreq(L, spacing)[i]
+}
+
+// omega / (2 pi) as hi + lo floats for every grid point.
+__global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega) {
+    const int64_t n = (int64_t)a.L * a.L;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int iy = (int)(idx / a.L), ix = (int)(idx - (int64_t)iy * a.L);
+        const double kx = wave_number(ix, a.L, a.dk), ky = wave_number(iy, a.L, a.dk);
+        const double w = sqrt(a.g * sqrt(kx * kx + ky * ky)) / 6.283185307179586476925;
+        const float hi = (float)w;
+        omega[idx] = make_float2(hi, (float)(w - (double)hi));
+    }
+}
+
+__global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2* __restrict__ coef,
+                                                        const float2* __restrict__ omega,
+                                                        float2* __restrict__ tmp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = a.L;
+    float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L)
+    float2* buf0 = tw + (L >> 1);
+    float2* buf1 = buf0 + 2 * L;
+    const int iy = blockIdx.x;
+    const int iyn = (L - iy) & (L - 1);                     // row of -k
+    for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
+    const float ky = (float)wave_number(iy, L, a.dk);
+    for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
+        const int ixn = (L - ix) & (L - 1);
+        const float kx = (float)wave_number(ix, L, a.dk);
+        const float2 A1 = __ldg(coef + (int64_t)iy * L + ix);
+        const float2 A2 = __ldg(coef + (int64_t)iyn * L + ixn);
+        // e^{-j omega t}: omega t / 2 pi = w t with w = hi + lo, t = t_hi + t_lo
+        const float2 w = __ldg(omega + (int64_t)iy * L + ix);
+        const float p = w.x * a.t_hi;
+        const float pe = fmaf(w.x, a.t_hi, -p);
+        float f = (p - rintf(p)) + (pe + fmaf(w.x, a.t_lo, w.y * a.t_hi));
+        f -= rintf(f);
+        float sn, cs;
+        sincospif(2.0f * f, &sn, &cs);
+        const float2 E = make_float2(cs, -sn);
+        const float2 F1 = cmul(A1, E), F2 = cmul(A2, E);    // F(k), F(-k)
+        const float om = 6.283185307179586f * (w.x + w.y);
+        const float kk = sqrtf(fmaf(kx, kx, ky * ky));
+        const float ux = kk > 0.f ? kx / kk : 0.f, uy = kk > 0.f ? ky / kk : 0.f;
+        // Hermitian parts (X(k) + conj(X(-k))) / 2 of the four spectra
+        const float2 he = make_float2(0.5f * (F1.x + F2.x), 0.5f * (F1.y - F2.y));       // X = F
+        // X = -j omega F (the same factor at -k): (-j omega F1 + conj(-j omega F2)) / 2
+        const float2 hz = make_float2(0.5f * om * (F1.y + F2.y), 0.5f * om * (F2.x - F1.x));
+        // X = omega u F, the factor at -k is -omega u
+        const float2 hx = make_float2(0.5f * om * ux * (F1.x - F2.x), 0.5f * om * ux * (F1.y + F2.y));
+        const float2 hy = make_float2(0.5f * om * uy * (F1.x - F2.x), 0.5f * om * uy * (F1.y + F2.y));
+        buf0[ix] = make_float2(he.x - hz.y, he.y + hz.x);   // H_eta + j H_vz
+        buf0[L + ix] = make_float2(hx.x - hy.y, hx.y + hy.x); // H_vx + j H_vy
+    }
+    __syncthreads();
+    const float2* res = stockham(buf0, buf1, 2, L, a.log2L, tw);
+    for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
+        tmp[(int64_t)iy * L + ix] = res[ix];
+        tmp[(int64_t)L * L + (int64_t)iy * L + ix] = res[L + ix];
+    }
+}
+
+__global__ void __launch_bounds__(512) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
+                                                        float* __restrict__ z, float* __restrict__ vx,
+                                                        float* __restrict__ vy, float* __restrict__ vz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = a.L, C = a.cols;
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* buf0 = tw + (L >> 1);
+    float2* buf1 = buf0 + C * L;
+    const int ix0 = blockIdx.x * C;
+    const int pair = blockIdx.y;
+    const float2* src = tmp + (int64_t)pair * L * L;
+    for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
+    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+        const int iy = idx / C, c = idx - iy * C;
+        buf0[c * L + iy] = __ldg(src + (int64_t)iy * L + ix0 + c);
+    }
+    __syncthreads();
+    const float2* res = stockham(buf0, buf1, C, L, a.log2L, tw);
+    float* fa = pair == 0 ? z : vx;
+    float* fb = pair == 0 ? vz : vy;
+    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+        const int iy = idx / C, c = idx - iy * C;
+        const float2 v = res[c * L + iy];
+        const int64_t o = (int64_t)iy * L + ix0 + c;
+        fa[o] = v.x * a.scale_over_L2;
+        fb[o] = v.y * a.scale_over_L2;
+    }
+}
+
+}  // namespace
+
+size_t surf_rows_smem(int L) { return sizeof(float2) * ((size_t)(L / 2) + 4 * (size_t)L); }
+size_t surf_cols_smem(int L, int cols) {
+    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)cols * L);
+}
+
+cudaError_t launch_surf_prepare(const SurfArgs& a, float2* omega, int n_sms, cudaStream_t stream) {
+    const int64_t n = (int64_t)a.L * a.L;
+    const int64_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < (int64_t)n_sms * 8 ? want : (int64_t)n_sms * 8);
+    surf_prepare_kernel<<<blocks, 256, 0, stream>>>(a, omega);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const float2* omega, float2* tmp,
+                           float* z, float* vx, float* vy, float* vz, cudaStream_t stream) {
+    const size_t s1 = surf_rows_smem(a.L), s2 = surf_cols_smem(a.L, a.cols);
+    cudaError_t e;
+    if (s1 > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(surf_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)s1)) != cudaSuccess)
+        return e;
+    if (s2 > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(surf_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)s2)) != cudaSuccess)
+        return e;
+    surf_rows_kernel<<<(unsigned)a.L, 512, s1, stream>>>(a, static_cast<const float2*>(coef), omega, tmp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), 512, s2, stream>>>(a, tmp, z, vx, vy, vz);
+    return cudaGetLastError();
+}
+
+}  // namespace rsim

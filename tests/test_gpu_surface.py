@@ -1,0 +1,87 @@
+"""Spectral surface update on the GPU (rsim_surface_prepare / rsim_surface_at, Algorithm 1's
+update_simulation) against the FP64 numpy restatement, and the fast mode with the surface
+regenerated at every update against the oracle fed with the oracle's own surfaces."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from helpers import TOL, gpu_cells, np_, rel_l2
+from oracle import surface as sf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsim():
+    import paper_2408_11472_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("L,spacing", [(64, 1.0), (256, 1.0), (128, 2.5), (4, 1.0)])
+def test_fields_match_oracle(rsim, L, spacing):
+    spec = sg.sea_spectrum(L, 40 + L, spacing=spacing)
+    surf = rsim.EvolvingSurface(spec)
+    for t in (0.0, 0.35, 7.0, 3600.25):
+        sc = surf.at(t)
+        ref = sf.surface_at(spec, t)
+        assert sc.t0 == t
+        for key, arr in (("z", sc.z), ("vx", sc.vx), ("vy", sc.vy), ("vz", sc.vz)):
+            r = ref[key]
+            err = np.abs(np_(arr).astype(np.float64) - r).max()
+            assert err <= 5e-6 * max(np.abs(r).max(), 1e-30), (key, t, err)
+
+
+def test_t0_surface_is_the_seeded_surface(rsim):
+    spec = sg.sea_spectrum(128, 3)
+    sc = rsim.EvolvingSurface(spec).at(0.0)
+    ref = sg.sea_surface(128, 3)
+    assert torch.equal(sc.x, torch.as_tensor(ref["x"]).cuda())
+    assert torch.equal(sc.nrcs, torch.as_tensor(ref["nrcs"]).cuda())
+    for key in ("z", "vx", "vy", "vz"):
+        r = ref[key].astype(np.float64)
+        assert np.abs(np_(getattr(sc, key)) - r).max() <= 5e-6 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_fast_mode_with_evolving_surface_matches_oracle(rsim, orc, precision):
+    rd = sg.RadarParams()
+    P, nf, nd = 384, 64, 64
+    pf = sg.nadir_track(P)
+    spec = sg.sea_spectrum(128, 21)
+    surf = rsim.EvolvingSurface(spec)
+    T, Y = rsim.simulate_fast_evolving(rd, pf, surf, P, nf, nd, "sqrt_raised_cosine", precision)
+    u0, S = rsim.spectra_range(0, P, nf)
+    for s in range(S):
+        t = (u0 + s) * nf / rd.prf_hz
+        sc_gpu = surf.at(t)
+        G, B = gpu_cells(rsim, rd, pf, sc_gpu, [(u0 + s) * nf], nd, precision)
+        Tref = orc.doppler_spectra_cells(rd, pf, sf.scene_at(spec, t), u0 + s, nf, nd, G, B)
+        # the surfaces differ by the FP32 transforms (~1e-7 m of height): 1e-4 of phase
+        assert rel_l2(np_(T)[s], Tref[0]) <= 1e-3
+    # the surface moves: the spectra differ from those of the frozen t = 0 surface moved
+    # along straight lines
+    frozen = rsim.Scatterers.from_arrays(sg.sea_surface(128, 21))
+    T_lin = rsim.doppler_accumulate(rd, pf, frozen, u0, S, nf, nd, precision)
+    assert rel_l2(np_(T)[-1], np_(T_lin)[-1]) > 1e-2
+
+
+def test_bad_spectra_are_rejected(rsim):
+    import paper_2408_11472_gb300._lib as L
+    spec = sg.sea_spectrum(16, 1)
+    with pytest.raises(ValueError):
+        rsim.EvolvingSurface(dict(spec, coef=spec["coef"][:, :8]))
+    for bad in (dict(spec, coef=np.zeros((12, 12), complex)), dict(spec, spacing=0.0),
+                dict(spec, scale=float("nan"))):
+        with pytest.raises(rsim.RsimError):
+            rsim.EvolvingSurface(bad)
+    surf = rsim.EvolvingSurface(spec)
+    with pytest.raises(rsim.RsimError):
+        surf.at(float("inf"))
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(rsim.RsimError):            # workspace too small
+        L.check(L.lib.rsim_surface_at(ctypes.byref(surf.spec), 0.0, surf.z.data_ptr(),
+                                      surf.vx.data_ptr(), surf.vy.data_ptr(), surf.vz.data_ptr(),
+                                      small.data_ptr(), 16, None))
