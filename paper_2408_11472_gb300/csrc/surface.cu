@@ -68,16 +68,21 @@ __global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2
         sincospif(2.0f * f, &sn, &cs);
         const float2 E = make_float2(cs, -sn);
         const float2 F1 = cmul(A1, E), F2 = cmul(A2, E);    // F(k), F(-k)
-        const float om = 6.283185307179586f * (w.x + w.y);
+        const float om = 6.283185307179586f * (w.x + w.y);   // the same |k| at n and -n
         const float kk = sqrtf(fmaf(kx, kx, ky * ky));
         const float ux = kk > 0.f ? kx / kk : 0.f, uy = kk > 0.f ? ky / kk : 0.f;
-        // Hermitian parts (X(k) + conj(X(-k))) / 2 of the four spectra
+        // direction at the grid point -n: -k_hat, except on the Nyquist row / column, which
+        // the grid maps onto itself with the same wave number
+        const float uxn = ixn == ix ? ux : -ux, uyn = iyn == iy ? uy : -uy;
+        // Hermitian parts (X(n) + conj(X(-n))) / 2 of the four spectra
         const float2 he = make_float2(0.5f * (F1.x + F2.x), 0.5f * (F1.y - F2.y));       // X = F
-        // X = -j omega F (the same factor at -k): (-j omega F1 + conj(-j omega F2)) / 2
+        // X = -j omega F (the same factor at -n): (-j omega F1 + conj(-j omega F2)) / 2
         const float2 hz = make_float2(0.5f * om * (F1.y + F2.y), 0.5f * om * (F2.x - F1.x));
-        // X = omega u F, the factor at -k is -omega u
-        const float2 hx = make_float2(0.5f * om * ux * (F1.x - F2.x), 0.5f * om * ux * (F1.y + F2.y));
-        const float2 hy = make_float2(0.5f * om * uy * (F1.x - F2.x), 0.5f * om * uy * (F1.y + F2.y));
+        // X = omega u F
+        const float2 hx = make_float2(0.5f * om * fmaf(ux, F1.x, uxn * F2.x),
+                                      0.5f * om * fmaf(ux, F1.y, -uxn * F2.y));
+        const float2 hy = make_float2(0.5f * om * fmaf(uy, F1.x, uyn * F2.x),
+                                      0.5f * om * fmaf(uy, F1.y, -uyn * F2.y));
         buf0[ix] = make_float2(he.x - hz.y, he.y + hz.x);   // H_eta + j H_vz
         buf0[L + ix] = make_float2(hx.x - hy.y, hx.y + hy.x); // H_vx + j H_vy
     }
