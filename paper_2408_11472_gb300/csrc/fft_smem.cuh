@@ -62,5 +62,66 @@ __device__ T* stockham(T* a, T* b, int rows, int N, int L, const T* __restrict__
     return a;
 }
 
+// Radix-4 Stockham autosort (a final radix-2 stage when log2 N is odd) over `rows`
+// independent N-point rows in shared memory: half the passes over the data of the radix-2
+// version.  tw[n] = exp(sign j 2 pi n / N) for n < N/2 (the other half by W^{n+N/2} = -W^n);
+// `sign` (+1 or -1) is the transform's.  Returns the buffer holding the natural-order result.
+template <typename T>
+__device__ __forceinline__ T tw_full(const T* tw, int e, int N) {
+    const int h = N >> 1;
+    if (e < h) return tw[e];
+    const T w = tw[e - h];
+    T r;
+    r.x = -w.x;
+    r.y = -w.y;
+    return r;
+}
+
+template <typename T>
+__device__ T* stockham4(T* a, T* b, int rows, int N, int L, const T* __restrict__ tw, int sign) {
+    int s = 1, lg = 0;
+    const int quarter = N >> 2;
+    while (lg + 2 <= L) {                       // radix-4 stages: s = 4^(lg/2) = 2^lg
+        const int m = quarter >> lg;
+        for (int idx = threadIdx.x; idx < rows * quarter; idx += blockDim.x) {
+            const int row = idx >> (L - 2);
+            const int bi = idx & (quarter - 1);
+            const int p = bi >> lg, q = bi & (s - 1);
+            const T* ar = a + row * N;
+            T* br = b + row * N;
+            const T x0 = ar[q + s * p], x1 = ar[q + s * (p + m)];
+            const T x2 = ar[q + s * (p + 2 * m)], x3 = ar[q + s * (p + 3 * m)];
+            const T t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), d = csub(x1, x3);
+            T t3;                               // sign j (x1 - x3)
+            t3.x = -sign * d.y;
+            t3.y = sign * d.x;
+            const int e = p * s;
+            br[q + s * (4 * p)] = cadd(t0, t2);
+            br[q + s * (4 * p + 1)] = cmul(cadd(t1, t3), tw_full(tw, e, N));
+            br[q + s * (4 * p + 2)] = cmul(csub(t0, t2), tw_full(tw, 2 * e, N));
+            br[q + s * (4 * p + 3)] = cmul(csub(t1, t3), tw_full(tw, 3 * e, N));
+        }
+        __syncthreads();
+        T* t = a; a = b; b = t;
+        s <<= 2;
+        lg += 2;
+    }
+    if (lg < L) {                               // last radix-2 stage: m = 1, unit twiddle
+        const int half = N >> 1;
+        for (int idx = threadIdx.x; idx < rows * half; idx += blockDim.x) {
+            const int row = idx >> (L - 1);
+            const int q = idx & (half - 1);
+            const T* ar = a + row * N;
+            T* br = b + row * N;
+            const T x0 = ar[q], x1 = ar[q + half];
+            br[q] = cadd(x0, x1);
+            br[q + half] = csub(x0, x1);
+        }
+        __syncthreads();
+        T* t = a; a = b; b = t;
+    }
+    return a;
+}
+
 }  // namespace fft
 }  // namespace rsim

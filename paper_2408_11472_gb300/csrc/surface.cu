@@ -65,12 +65,13 @@ __global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2
         float f = (p - rintf(p)) + (pe + fmaf(w.x, a.t_lo, w.y * a.t_hi));
         f -= rintf(f);
         float sn, cs;
-        sincospif(2.0f * f, &sn, &cs);
+        __sincosf(6.283185307179586f * f, &sn, &cs);       // |2 pi f| <= pi
         const float2 E = make_float2(cs, -sn);
         const float2 F1 = cmul(A1, E), F2 = cmul(A2, E);    // F(k), F(-k)
         const float om = 6.283185307179586f * (w.x + w.y);   // the same |k| at n and -n
-        const float kk = sqrtf(fmaf(kx, kx, ky * ky));
-        const float ux = kk > 0.f ? kx / kk : 0.f, uy = kk > 0.f ? ky / kk : 0.f;
+        const float k2 = fmaf(kx, kx, ky * ky);
+        const float ik = k2 > 0.f ? rsqrtf(k2) : 0.f;
+        const float ux = kx * ik, uy = ky * ik;
         // direction at the grid point -n: -k_hat, except on the Nyquist row / column, which
         // the grid maps onto itself with the same wave number
         const float uxn = ixn == ix ? ux : -ux, uyn = iyn == iy ? uy : -uy;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2
         buf0[L + ix] = make_float2(hx.x - hy.y, hx.y + hy.x); // H_vx + j H_vy
     }
     __syncthreads();
-    const float2* res = stockham(buf0, buf1, 2, L, a.log2L, tw);
+    const float2* res = stockham4(buf0, buf1, 2, L, a.log2L, tw, 1);
     for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
         tmp[(int64_t)iy * L + ix] = res[ix];
         tmp[(int64_t)L * L + (int64_t)iy * L + ix] = res[L + ix];
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(512) surf_cols_kernel(SurfArgs a, const float2
         buf0[c * L + iy] = __ldg(src + (int64_t)iy * L + ix0 + c);
     }
     __syncthreads();
-    const float2* res = stockham(buf0, buf1, C, L, a.log2L, tw);
+    const float2* res = stockham4(buf0, buf1, C, L, a.log2L, tw, 1);
     float* fa = pair == 0 ? z : vx;
     float* fb = pair == 0 ? vz : vy;
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
