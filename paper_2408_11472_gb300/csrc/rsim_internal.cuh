@@ -402,16 +402,23 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, const dou
     const double Gi = floor(G);
     double psi = Rc * m.two_over_lambda;
     psi -= rint(psi);
-    const double inv = 1.0 / Rc;
+    // 1 / R_c from the FP32 reciprocal and one Newton step (FP64 accurate, no FP64 divide:
+    // the FP64 pipe is 1/64 of FP32 and this runs once per CTA and sample)
+    const double inv0 = (double)(1.0f / (float)Rc);
+    const double inv = fma(inv0, fma(-Rc, inv0, 1.0), inv0);
     const double dt = m.inv_prf;
     const double epx = m.v[0] * dt, epy = m.v[1] * dt, epz = m.v[2] * dt;
     const double K0 = (Dx + 0.5 * epx) * epx + (Dy + 0.5 * epy) * epy + (Dz + 0.5 * epz) * epz;
     const float K0hi = (float)K0;
+    // log2 (r_ref / R_c)^2 = 2 log2(1 + x), x = (r_ref - R_c) / R_c tiny: FP32 log1p of the
+    // FP64 difference; beam_k / D_z^2 in FP32 (a float constant either way)
+    const float xref = (float)((rref - Rc) * inv);
+    const float invDz = 1.0f / (float)Dz;
     SplitConst k;
     k.a = make_float4((float)ts, (float)Dx, (float)Dy, (float)Dz);
     k.b = make_float4((float)(Dx * inv), (float)(Dy * inv), (float)(Dz * inv), (float)(0.5 * inv));
-    k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, (float)(2.0 * log2(rref * inv)));
-    k.d = make_float4((float)(m.beam_k / (Dz * Dz)), K0hi, (float)(K0 - (double)K0hi),
+    k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, 2.0f * kInvLn2F * log1pf(xref));
+    k.d = make_float4(m.beam_k_f * invDz * invDz, K0hi, (float)(K0 - (double)K0hi),
                       (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
     k.e = make_float4(__int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)),
                       __int_as_float(window_reachable(m, G, ts, lmax, vmax)), 0.f, 0.f);
