@@ -332,9 +332,17 @@ __device__ __forceinline__ int cta_reaches_window(const Model& m, const double* 
     const double Dx = platform_coord(m, p0, 0, t) - (double)cx;
     const double Dy = platform_coord(m, p0, 1, t) - (double)cy;
     const double Dz = platform_coord(m, p0, 2, t);
-    const double Rc = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
     const double rref = fma(m.r_ref_rate, t, m.r_ref0);
-    const double G = (Rc - rref) * m.inv_gw + m.half_gates;
+    // R_c - r_ref = (D_x^2 + D_y^2 + (D_z - r_ref)(D_z + r_ref)) / (R_c + r_ref), the
+    // cancelling difference taken in FP64, the rest in FP32 (no FP64 square root); with
+    // R_c + r_ref from one refinement the relative error is ~1e-7 + (dR / 2 r_ref)^2, far
+    // inside the 2-gate margin of the bound
+    const float num = fmaf((float)Dx, (float)Dx,
+                           fmaf((float)Dy, (float)Dy, (float)(Dz - rref) * (float)(Dz + rref)));
+    const float two_r = 2.0f * (float)rref;
+    const float d1 = num / two_r;
+    const float dR = num / (two_r + d1);
+    const double G = (double)dR * m.inv_gw + m.half_gates;
     return window_reachable(m, G, t - t0, lmax, vmax);
 }
 
