@@ -572,8 +572,12 @@ def run_delay_doppler(torch, rsim, args):
     line["config"].update({"pulses": P, "burst": burst, "bursts": nb, "gates": rd.n_gates,
                            "outputs": "focused beams + multi-look"})
     line["multilook_only_ms"] = round(t_ml, 4)
+    import bench
+    peak, basis = bench.measured_hbm_gbs()
     line["roofline"] = {"bound": "hbm", "bytes_per_launch": bytes_moved,
                         "achieved_gbs": round(bytes_moved / (t / 1e3) / 1e9, 1),
+                        "peak_gbs": peak, "peak_basis": basis,
+                        "frac": round(bytes_moved / (t / 1e3) / 1e9 / peak, 4),
                         "note": "one CTA per burst (%d CTAs): the launch is latency-bound" % nb}
     line["normalised_mean_waveform"] = {
         "fast": [round(float(v), 5) for v in nf], "regular": [round(float(v), 5) for v in nr],
@@ -618,8 +622,12 @@ def run_surface_update(torch, rsim, args):
     line["config"].update({"grid": L, "pulses": P, "updates": S, "window": fp.window,
                            "precision": "split", "l2": "flushed before each timed call"})
     line["surface_synthesis_ms"] = round(t_surf, 4)
+    import bench
+    peak, basis = bench.measured_hbm_gbs()
     line["surface_synthesis_roofline"] = {"bound": "hbm", "bytes": nbytes,
-                                          "achieved_gbs": round(nbytes / (t_surf / 1e3) / 1e9, 1)}
+                                          "achieved_gbs": round(nbytes / (t_surf / 1e3) / 1e9, 1),
+                                          "peak_gbs": peak, "peak_basis": basis,
+                                          "frac": round(nbytes / (t_surf / 1e3) / 1e9 / peak, 4)}
     line["step_ms"] = {"evolving_surface": round(t_evo, 3), "linear_kinematics": round(t_lin, 3)}
     return line
 

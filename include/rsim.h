@@ -192,6 +192,28 @@ rsim_status rsim_doppler_accumulate(const rsim_radar *radar, const rsim_platform
 size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_gates,
                                    int32_t n_doppler);
 
+/* Blockwise summation into one exact fixed-point workspace, for a scatterer set that
+ * arrives in blocks (streamed from host memory, or larger than device memory):
+ *   rsim_workspace_clear, then rsim_doppler_accumulate_partial for every block (each adds
+ *   its contributions to the workspace's exact sums; no clear, no conversion), then
+ *   rsim_workspace_finalize (adds the sums to the complex spectra, +=).
+ * Blocks that start at multiples of rsim_block_scatterers() keep every scatterer's FP64
+ * reference point, so the spectra are bit-identical to one rsim_doppler_accumulate call on
+ * the whole set.  Arguments as rsim_doppler_accumulate; workspace 16-byte aligned, of at
+ * least rsim_workspace_size(n_updates, n_gates, n_doppler) bytes, and must not be shared
+ * by overlapping calls. */
+rsim_status rsim_workspace_clear(int32_t n_updates, int32_t n_gates, int32_t n_doppler,
+                                 void *workspace, size_t workspace_bytes, cudaStream_t stream);
+rsim_status rsim_doppler_accumulate_partial(const rsim_radar *radar,
+                                            const rsim_platform *platform,
+                                            const rsim_scatterers *scat, int64_t update0,
+                                            int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                            rsim_precision precision, void *workspace,
+                                            size_t workspace_bytes, cudaStream_t stream);
+rsim_status rsim_workspace_finalize(int32_t n_updates, int32_t n_gates, int32_t n_doppler,
+                                    rsim_precision precision, const void *workspace,
+                                    size_t workspace_bytes, void *spectra, cudaStream_t stream);
+
 /* Launch plan of the batched scatterer pass.  Every choice gives bit-identical results;
  * only the speed differs (see rsim_autotune_batched). */
 typedef struct {

@@ -28,7 +28,7 @@ __all__ = [
     "doppler_accumulate", "doppler_accumulate_noalloc", "doppler_accumulate_batched",
     "autotune_batched", "Tuning",
     "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "scatterer_echo",
-    "delay_doppler", "EvolvingSurface", "simulate_fast_evolving",
+    "delay_doppler", "EvolvingSurface", "simulate_fast_evolving", "HostStreamer",
     "synth_pulses_backward",
     "doppler_accumulate_backward", "direct_sum_backward", "spectra_range", "simulate_fast",
     "FastMode", "RegularMode", "version", "PRECISIONS", "WINDOWS",
@@ -436,6 +436,76 @@ def simulate_fast(radar, platform, scat: Scatterers, n_pulses: int, n_fast: int,
                            out=spectra, workspace=workspace, stream=stream)
     Y = synth_pulses(radar, T, u0, n_fast, pulse0, n_pulses, window, out=out, stream=stream)
     return T, Y
+
+
+class HostStreamer:
+    """Fast mode from scatterer arrays in pinned host memory, with the host-to-device copies
+    overlapped with the scatterer pass: the set is cut into ``chunks`` blocks of whole
+    512-scatterer blocks (default: one per full wave of CTAs on the device); block i+1 is
+    copied on a copy stream while the summation of block i
+    runs (the summation adds, so the blocks' spectra sum to the set's; every scatterer keeps
+    its FP64 reference point).  Device buffers and the workspace are allocated once."""
+
+    def __init__(self, n: int, n_gates: int, n_doppler: int, max_spectra: int,
+                 chunks: Optional[int] = None, device="cuda", precision: str = "split"):
+        self.n, self.precision = int(n), precision
+        self.dev = torch.device(device)
+        blk = int(_lib.lib.rsim_block_scatterers())
+        nb = (self.n + blk - 1) // blk
+        if chunks is None:
+            # blocks of whole waves of CTAs (6 resident per SM), so no launch ends in a
+            # partly filled wave
+            wave = 6 * torch.cuda.get_device_properties(self.dev).multi_processor_count
+            chunks = max(1, (nb + wave - 1) // wave)
+        self.chunks = max(1, int(chunks))
+        self.buf = {k: torch.empty(self.n, dtype=torch.float32, device=self.dev) for k in _KEYS}
+        self.ws = torch.empty(max(16, workspace_size(max_spectra, n_gates, n_doppler)),
+                              dtype=torch.uint8, device=self.dev)
+        self.copy_stream = torch.cuda.Stream(device=self.dev)
+        if chunks is not None and self.chunks > 1 and nb >= self.chunks:
+            edges = [min(self.n, (nb * i // self.chunks) * blk) for i in range(self.chunks + 1)]
+        else:
+            per = (nb + self.chunks - 1) // self.chunks          # whole waves, last one short
+            edges = [min(self.n, i * per * blk) for i in range(self.chunks + 1)]
+        self.ranges = [(a, b) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+        self.events = [torch.cuda.Event() for _ in self.ranges]
+
+    def run(self, radar, platform, host: dict, n_pulses: int, n_fast: int, n_doppler: int,
+            window: str = "sqrt_raised_cosine", pulse0: int = 0, spectra=None, out=None):
+        """host: pinned CPU float32 arrays x, y, z, vx, vy, vz, nrcs [n] (+ origin, area, t0).
+        Returns (spectra, iq) on the device, enqueued on the current stream."""
+        u0, S = spectra_range(pulse0, n_pulses, n_fast)
+        cur = torch.cuda.current_stream(self.dev)
+        T = spectra
+        if T is None:
+            T = torch.zeros((S, radar.n_gates, n_doppler), dtype=_cdtype(self.precision),
+                            device=self.dev)
+        else:
+            T.zero_()
+        self.copy_stream.wait_stream(cur)        # buffers are free once earlier work is done
+        with torch.cuda.stream(self.copy_stream):
+            for (a, b), ev in zip(self.ranges, self.events):
+                for k in _KEYS:
+                    self.buf[k][a:b].copy_(host[k][a:b], non_blocking=True)
+                ev.record(self.copy_stream)
+        origin, area, t0 = host.get("origin", (0.0, 0.0, 0.0)), host.get("area", 1.0), host.get("t0", 0.0)
+        G, nbytes = radar.n_gates, self.ws.numel()
+        rd, pf, prec = _lib.make_radar(radar), _lib.make_platform(platform), _prec(self.precision)
+        st = _stream(cur)
+        # one exact fixed-point workspace for all blocks: the spectra are bit-identical to
+        # a single call on the whole set
+        _lib.check(_lib.lib.rsim_workspace_clear(S, G, n_doppler, _ptr(self.ws), nbytes, st))
+        for (a, b), ev in zip(self.ranges, self.events):
+            cur.wait_event(ev)
+            part = Scatterers(*[self.buf[k][a:b] for k in _KEYS], origin=origin, area=area, t0=t0)
+            sc = part.c_struct()
+            _lib.check(_lib.lib.rsim_doppler_accumulate_partial(
+                ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(u0), int(S), int(n_fast),
+                int(n_doppler), prec, _ptr(self.ws), nbytes, st))
+        _lib.check(_lib.lib.rsim_workspace_finalize(S, G, n_doppler, prec, _ptr(self.ws), nbytes,
+                                                    _ptr(T), st))
+        Y = synth_pulses(radar, T, u0, n_fast, pulse0, n_pulses, window, out=out)
+        return T, Y
 
 
 class FastMode(torch.autograd.Function):

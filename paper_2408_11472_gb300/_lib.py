@@ -85,6 +85,11 @@ PROTOTYPES = {
     "rsim_scatterer_cells": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P, _P],
                              ctypes.c_int),
     "rsim_scatterer_echo": ([_RP, _PP, _SP, _I64, ctypes.c_int, _P, _P], ctypes.c_int),
+    "rsim_workspace_clear": ([_I32, _I32, _I32, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "rsim_doppler_accumulate_partial": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int, _P,
+                                         ctypes.c_size_t, _P], ctypes.c_int),
+    "rsim_workspace_finalize": ([_I32, _I32, _I32, ctypes.c_int, _P, ctypes.c_size_t, _P, _P],
+                                ctypes.c_int),
     "rsim_delay_doppler": ([_RP, _PP, _P, _I64, _I32, _I32, _P, _P, _P], ctypes.c_int),
     "rsim_surface_workspace_size": ([_I32], ctypes.c_size_t),
     "rsim_surface_prepare": ([ctypes.POINTER(WaveSpectrum), _P, ctypes.c_size_t, _P], ctypes.c_int),

@@ -196,12 +196,13 @@ size_t batch_stride(int32_t n_samples, int32_t n_gates, int32_t n_doppler) {
     return (b + 255u) & ~(size_t)255u;
 }
 
-// Shared body of rsim_direct_sum and rsim_doppler_accumulate.
+// Shared body of rsim_direct_sum and rsim_doppler_accumulate; with partial = true (the
+// blockwise entry point) only the summation kernel runs: no clear, no finalize, out unused.
 rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platform,
                            const rsim_scatterers* scat, int64_t pulse_base, int32_t stride,
                            int32_t n_samples, int32_t n_doppler, bool doppler,
                            rsim_precision precision, void* out, void* workspace,
-                           size_t workspace_bytes, cudaStream_t stream) {
+                           size_t workspace_bytes, cudaStream_t stream, bool partial = false) {
     rsim_status st;
     if ((st = check_radar(radar)) != RSIM_OK) return st;
     if ((st = check_platform(platform)) != RSIM_OK) return st;
@@ -212,9 +213,11 @@ rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platfor
     if (pulse_base + (int64_t)n_samples * stride > ((int64_t)1 << 52))
         return fail(RSIM_ERR_INVALID_ARG, "pulse index out of range");
     if (n_samples == 0 || scat->n == 0) return RSIM_OK;  // nothing to add
-    if (!out) return fail(RSIM_ERR_INVALID_ARG, "output is NULL");
     const bool fp64 = precision == RSIM_FP64;
-    if (!aligned(out, fp64 ? 16 : 8)) return fail(RSIM_ERR_INVALID_ARG, "output misaligned");
+    if (!partial) {
+        if (!out) return fail(RSIM_ERR_INVALID_ARG, "output is NULL");
+        if (!aligned(out, fp64 ? 16 : 8)) return fail(RSIM_ERR_INVALID_ARG, "output misaligned");
+    }
     const size_t need = ws_bytes(n_samples, radar->n_gates, n_doppler);
     if (!workspace) return fail(RSIM_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
     if (!aligned(workspace, 16)) return fail(RSIM_ERR_WORKSPACE, "workspace not 16-byte aligned");
@@ -228,11 +231,16 @@ rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platfor
     rsim::Schedule sch;
     const int64_t groups = plan_samples(chunks, pulse_base, stride, n_samples, &sch);
 
-    cudaError_t e = cudaMemsetAsync(workspace, 0, need, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    cudaError_t e = cudaSuccess;
+    if (!partial && (e = cudaMemsetAsync(workspace, 0, need, stream)) != cudaSuccess)
+        return cuda_fail(e, "workspace clear");
     e = rsim::launch_accumulate(m, sch, sc, fp64, doppler,
                                 static_cast<unsigned long long*>(workspace),
                                 dim3((unsigned)chunks, (unsigned)groups), stream);
+    if (partial) {
+        if (e != cudaSuccess) return cuda_fail(e, "summation kernel launch");
+        return RSIM_OK;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "summation kernel launch");
     e = rsim::launch_finalize(workspace, out, (int64_t)(need / 8), fp64, device_sms(), stream);
     if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
@@ -377,6 +385,53 @@ rsim_status rsim_scatterer_cells(const rsim_radar* radar, const rsim_platform* p
     const cudaError_t e = rsim::launch_cells(m, pulse, precision == RSIM_FP64, n_doppler > 1, sc,
                                              gate, bin, gate_coord, bin_coord, nullptr, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cells kernel launch");
+    return RSIM_OK;
+}
+
+rsim_status rsim_doppler_accumulate_partial(const rsim_radar* radar, const rsim_platform* platform,
+                                            const rsim_scatterers* scat, int64_t update0,
+                                            int32_t n_updates, int32_t n_fast, int32_t n_doppler,
+                                            rsim_precision precision, void* workspace,
+                                            size_t workspace_bytes, cudaStream_t stream) {
+    if (n_fast < 1) return fail(RSIM_ERR_INVALID_ARG, "n_fast=%d < 1", n_fast);
+    if (!is_pow2(n_doppler) || n_doppler > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [1, 4096]", n_doppler);
+    if (update0 < 0 || update0 > (((int64_t)1 << 52) / n_fast))
+        return fail(RSIM_ERR_INVALID_ARG, "update index out of range");
+    return run_accumulate(radar, platform, scat, update0 * (int64_t)n_fast, n_fast, n_updates,
+                          n_doppler, true, precision, nullptr, workspace, workspace_bytes, stream,
+                          true);
+}
+
+rsim_status rsim_workspace_clear(int32_t n_updates, int32_t n_gates, int32_t n_doppler,
+                                 void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+    if (n_updates < 0 || n_gates < 1 || n_doppler < 1)
+        return fail(RSIM_ERR_INVALID_ARG, "bad workspace shape");
+    const size_t need = ws_bytes(n_updates, n_gates, n_doppler);
+    if (need == 0) return RSIM_OK;
+    if (!workspace || !aligned(workspace, 16) || workspace_bytes < need)
+        return fail(RSIM_ERR_WORKSPACE, "workspace: need %zu bytes, 16-byte aligned", need);
+    const cudaError_t e = cudaMemsetAsync(workspace, 0, need, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    return RSIM_OK;
+}
+
+rsim_status rsim_workspace_finalize(int32_t n_updates, int32_t n_gates, int32_t n_doppler,
+                                    rsim_precision precision, const void* workspace,
+                                    size_t workspace_bytes, void* out, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (n_updates < 0 || n_gates < 1 || n_doppler < 1)
+        return fail(RSIM_ERR_INVALID_ARG, "bad workspace shape");
+    const size_t need = ws_bytes(n_updates, n_gates, n_doppler);
+    if (need == 0) return RSIM_OK;
+    const bool fp64 = precision == RSIM_FP64;
+    if (!workspace || !aligned(workspace, 16) || workspace_bytes < need)
+        return fail(RSIM_ERR_WORKSPACE, "workspace: need %zu bytes, 16-byte aligned", need);
+    if (!out || !aligned(out, fp64 ? 16 : 8)) return fail(RSIM_ERR_INVALID_ARG, "output NULL or misaligned");
+    const cudaError_t e = rsim::launch_finalize(workspace, out, (int64_t)(need / 8), fp64,
+                                                device_sms(), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
     return RSIM_OK;
 }
 
