@@ -123,5 +123,81 @@ __device__ T* stockham4(T* a, T* b, int rows, int N, int L, const T* __restrict_
     return a;
 }
 
+// The same radix-4 Stockham transform with a single buffer: every pass reads all of a
+// thread's butterfly inputs into registers, waits at a barrier, then writes the outputs to
+// their Stockham positions in the same array.  Needs rows * N / 4 <= MAXB * blockDim.x
+// (the caller checks); the result is in `a`, natural order.
+template <typename T, int MAXB>
+__device__ void stockham4_1buf(T* a, int rows, int N, int L, const T* __restrict__ tw, int sign) {
+    const int quarter = N >> 2;
+    const int total4 = rows * quarter;
+    int s = 1, lg = 0;
+    while (lg + 2 <= L) {
+        const int m = quarter >> lg;
+        T x[MAXB][4];
+#pragma unroll
+        for (int u = 0; u < MAXB; ++u) {
+            const int idx = threadIdx.x + u * blockDim.x;
+            if (idx < total4) {
+                const int row = idx >> (L - 2), bi = idx & (quarter - 1);
+                const int p = bi >> lg, q = bi & (s - 1);
+                const T* ar = a + row * N;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) x[u][k] = ar[q + s * (p + k * m)];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < MAXB; ++u) {
+            const int idx = threadIdx.x + u * blockDim.x;
+            if (idx < total4) {
+                const int row = idx >> (L - 2), bi = idx & (quarter - 1);
+                const int p = bi >> lg, q = bi & (s - 1);
+                T* ar = a + row * N;
+                const T t0 = cadd(x[u][0], x[u][2]), t1 = csub(x[u][0], x[u][2]);
+                const T t2 = cadd(x[u][1], x[u][3]), d = csub(x[u][1], x[u][3]);
+                T t3;
+                t3.x = -sign * d.y;
+                t3.y = sign * d.x;
+                const int e = p * s;
+                ar[q + s * (4 * p)] = cadd(t0, t2);
+                ar[q + s * (4 * p + 1)] = cmul(cadd(t1, t3), tw_full(tw, e, N));
+                ar[q + s * (4 * p + 2)] = cmul(csub(t0, t2), tw_full(tw, 2 * e, N));
+                ar[q + s * (4 * p + 3)] = cmul(csub(t1, t3), tw_full(tw, 3 * e, N));
+            }
+        }
+        __syncthreads();
+        s <<= 2;
+        lg += 2;
+    }
+    if (lg < L) {                               // last radix-2 stage: pairs N/2 apart
+        const int half = N >> 1;
+        const int total2 = rows * half;
+        T y[2 * MAXB][2];
+#pragma unroll
+        for (int u = 0; u < 2 * MAXB; ++u) {
+            const int idx = threadIdx.x + u * blockDim.x;
+            if (idx < total2) {
+                const T* ar = a + (idx >> (L - 1)) * N;
+                const int q = idx & (half - 1);
+                y[u][0] = ar[q];
+                y[u][1] = ar[q + half];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2 * MAXB; ++u) {
+            const int idx = threadIdx.x + u * blockDim.x;
+            if (idx < total2) {
+                T* ar = a + (idx >> (L - 1)) * N;
+                const int q = idx & (half - 1);
+                ar[q] = cadd(y[u][0], y[u][1]);
+                ar[q + half] = csub(y[u][0], y[u][1]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace fft
 }  // namespace rsim

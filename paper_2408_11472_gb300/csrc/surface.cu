@@ -11,7 +11,10 @@
 // v_x + j v_y) per update:
 //   rows pass    : one CTA per row iy builds both packed rows from A(k), A(-k) and the
 //                  phase e^{-j omega t}, and transforms them along x (shared memory);
-//   columns pass : one CTA per block of columns transforms along y and writes the fields.
+//   columns pass : one CTA per block of columns (32 bytes of every row) transforms along y
+//                  and writes the fields.
+// Both passes use the single-buffer radix-4 transform (one shared-memory copy of the data,
+// three CTAs per SM).
 // omega / (2 pi) is tabulated once per spectrum (FP64, stored as hi + lo floats) so that
 // the phase omega t stays accurate to ~1e-7 cycles for t of hours.
 #include "rsim_internal.cuh"
@@ -48,7 +51,6 @@ __global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2
     const int L = a.L;
     float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L)
     float2* buf0 = tw + (L >> 1);
-    float2* buf1 = buf0 + 2 * L;
     const int iy = blockIdx.x;
     const int iyn = (L - iy) & (L - 1);                     // row of -k
     for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
@@ -88,7 +90,8 @@ __global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2
         buf0[L + ix] = make_float2(hx.x - hy.y, hx.y + hy.x); // H_vx + j H_vy
     }
     __syncthreads();
-    const float2* res = stockham4(buf0, buf1, 2, L, a.log2L, tw, 1);
+    stockham4_1buf<float2, 4>(buf0, 2, L, a.log2L, tw, 1);   // 2 L / 4 <= 4 x 512
+    const float2* res = buf0;
     for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
         tmp[(int64_t)iy * L + ix] = res[ix];
         tmp[(int64_t)L * L + (int64_t)iy * L + ix] = res[L + ix];
@@ -102,7 +105,6 @@ __global__ void __launch_bounds__(512) surf_cols_kernel(SurfArgs a, const float2
     const int L = a.L, C = a.cols;
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* buf0 = tw + (L >> 1);
-    float2* buf1 = buf0 + C * L;
     const int ix0 = blockIdx.x * C;
     const int pair = blockIdx.y;
     const float2* src = tmp + (int64_t)pair * L * L;
@@ -112,7 +114,8 @@ __global__ void __launch_bounds__(512) surf_cols_kernel(SurfArgs a, const float2
         buf0[c * L + iy] = __ldg(src + (int64_t)iy * L + ix0 + c);
     }
     __syncthreads();
-    const float2* res = stockham4(buf0, buf1, C, L, a.log2L, tw, 1);
+    stockham4_1buf<float2, 4>(buf0, C, L, a.log2L, tw, 1);   // C L / 4 <= 4 x 512
+    const float2* res = buf0;
     float* fa = pair == 0 ? z : vx;
     float* fb = pair == 0 ? vz : vy;
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
@@ -126,9 +129,9 @@ __global__ void __launch_bounds__(512) surf_cols_kernel(SurfArgs a, const float2
 
 }  // namespace
 
-size_t surf_rows_smem(int L) { return sizeof(float2) * ((size_t)(L / 2) + 4 * (size_t)L); }
+size_t surf_rows_smem(int L) { return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)L); }
 size_t surf_cols_smem(int L, int cols) {
-    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)cols * L);
+    return sizeof(float2) * ((size_t)(L / 2) + (size_t)cols * L);
 }
 
 cudaError_t launch_surf_prepare(const SurfArgs& a, float2* omega, int n_sms, cudaStream_t stream) {
