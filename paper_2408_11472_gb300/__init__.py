@@ -440,25 +440,34 @@ def simulate_fast(radar, platform, scat: Scatterers, n_pulses: int, n_fast: int,
 
 class HostStreamer:
     """Fast mode from scatterer arrays in pinned host memory, with the host-to-device copies
-    overlapped with the scatterer pass: the set is cut into ``chunks`` blocks of whole
-    512-scatterer blocks (default: one per full wave of CTAs on the device); block i+1 is
-    copied on a copy stream while the summation of block i
-    runs (the summation adds, so the blocks' spectra sum to the set's; every scatterer keeps
-    its FP64 reference point).  Device buffers and the workspace are allocated once."""
+    overlapped with the scatterer pass.  Device buffers come in two sets, so the copies of
+    one run overlap the summation of the previous run: for a stream of runs one block
+    (``chunks=1``, the default) hides the copies entirely.  For the latency of a single run
+    the set can be cut into ``chunks`` blocks of whole 512-scatterer blocks ("waves": one
+    block per full wave of CTAs), block i+1 copied while block i is summed (the summation
+    adds, so the blocks' sums make the set's; every scatterer keeps its FP64 reference
+    point).  All blocks add into one exact workspace, so the spectra are bit-identical to a
+    single call on the whole set.  Buffers and workspace are allocated once."""
 
     def __init__(self, n: int, n_gates: int, n_doppler: int, max_spectra: int,
-                 chunks: Optional[int] = None, device="cuda", precision: str = "split"):
+                 chunks=None, device="cuda", precision: str = "split"):
         self.n, self.precision = int(n), precision
         self.dev = torch.device(device)
         blk = int(_lib.lib.rsim_block_scatterers())
         nb = (self.n + blk - 1) // blk
         if chunks is None:
+            chunks = 1
+        elif chunks == "waves":
             # blocks of whole waves of CTAs (6 resident per SM), so no launch ends in a
             # partly filled wave
             wave = 6 * torch.cuda.get_device_properties(self.dev).multi_processor_count
             chunks = max(1, (nb + wave - 1) // wave)
         self.chunks = max(1, int(chunks))
-        self.buf = {k: torch.empty(self.n, dtype=torch.float32, device=self.dev) for k in _KEYS}
+        # two sets of device buffers: the copies of one run overlap the summation of the last
+        self.sets = [{k: torch.empty(self.n, dtype=torch.float32, device=self.dev) for k in _KEYS}
+                     for _ in range(2)]
+        self.released = [torch.cuda.Event() for _ in range(2)]
+        self.turn = 0
         self.ws = torch.empty(max(16, workspace_size(max_spectra, n_gates, n_doppler)),
                               dtype=torch.uint8, device=self.dev)
         self.copy_stream = torch.cuda.Stream(device=self.dev)
@@ -482,11 +491,13 @@ class HostStreamer:
                             device=self.dev)
         else:
             T.zero_()
-        self.copy_stream.wait_stream(cur)        # buffers are free once earlier work is done
+        buf, rel = self.sets[self.turn], self.released[self.turn]
+        self.turn ^= 1
+        self.copy_stream.wait_event(rel)          # this set's last summation has read it
         with torch.cuda.stream(self.copy_stream):
             for (a, b), ev in zip(self.ranges, self.events):
                 for k in _KEYS:
-                    self.buf[k][a:b].copy_(host[k][a:b], non_blocking=True)
+                    buf[k][a:b].copy_(host[k][a:b], non_blocking=True)
                 ev.record(self.copy_stream)
         origin, area, t0 = host.get("origin", (0.0, 0.0, 0.0)), host.get("area", 1.0), host.get("t0", 0.0)
         G, nbytes = radar.n_gates, self.ws.numel()
@@ -497,11 +508,12 @@ class HostStreamer:
         _lib.check(_lib.lib.rsim_workspace_clear(S, G, n_doppler, _ptr(self.ws), nbytes, st))
         for (a, b), ev in zip(self.ranges, self.events):
             cur.wait_event(ev)
-            part = Scatterers(*[self.buf[k][a:b] for k in _KEYS], origin=origin, area=area, t0=t0)
+            part = Scatterers(*[buf[k][a:b] for k in _KEYS], origin=origin, area=area, t0=t0)
             sc = part.c_struct()
             _lib.check(_lib.lib.rsim_doppler_accumulate_partial(
                 ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(u0), int(S), int(n_fast),
                 int(n_doppler), prec, _ptr(self.ws), nbytes, st))
+        rel.record(cur)
         _lib.check(_lib.lib.rsim_workspace_finalize(S, G, n_doppler, prec, _ptr(self.ws), nbytes,
                                                     _ptr(T), st))
         Y = synth_pulses(radar, T, u0, n_fast, pulse0, n_pulses, window, out=out)

@@ -173,5 +173,11 @@ def test_host_streamer_overlaps_copies_and_matches(rsim):
     # blockwise exact sums in one workspace: bit-identical to one call on the whole set
     assert torch.equal(T, T1)
     assert torch.equal(Y, Y1)
-    T2, _ = hs.run(rd, pf, host, P, fp.n_fast, fp.n_doppler, fp.window)   # buffers reused
+    T2, _ = hs.run(rd, pf, host, P, fp.n_fast, fp.n_doppler, fp.window)   # the other buffer set
     assert torch.equal(T2, T)
+    T3, _ = hs.run(rd, pf, host, P, fp.n_fast, fp.n_doppler, fp.window)   # the first set again
+    assert torch.equal(T3, T)
+    one = rsim.HostStreamer(scene["x"].size, rd.n_gates, fp.n_doppler, S)  # default: one block
+    assert len(one.ranges) == 1
+    T4, _ = one.run(rd, pf, host, P, fp.n_fast, fp.n_doppler, fp.window)
+    assert torch.equal(T4, T)
