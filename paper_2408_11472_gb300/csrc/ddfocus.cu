@@ -4,7 +4,7 @@
 // (burst x n_gates complex, two buffers):
 //   1. Doppler centroid correction  y_k *= exp(-j 2 pi nu_c k), and the factor (-1)^k that
 //      centres the beams (beam f <-> nu_f = (f - burst/2) / burst);
-//   2. along-track transform per gate (radix-2 Stockham, twiddles exp(-j 2 pi r / N));
+//   2. along-track transform per gate (radix-4 Stockham, twiddles exp(-j 2 pi r / N));
 //   3. range transform per beam, the delay phase coefficients exp(+j 2 pi q' s_f / n_gates)
 //      (signed range frequency q', range migration s_f of the beam in gates), inverse range
 //      transform scaled by 1 / n_gates;
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(512) dd_focus_kernel(DdArgs a, const float2* _
     }
     __syncthreads();
     // 2. along-track transforms: rows = gates
-    float2* res = stockham(buf0, buf1, G, Nb, a.log2_b, tw_b);
+    float2* res = stockham4(buf0, buf1, G, Nb, a.log2_b, tw_b, -1);
     float2* other = (res == buf0) ? buf1 : buf0;
     // 3. beams as rows ([f][g]) for the range transforms
     for (int idx = threadIdx.x; idx < Nb * G; idx += blockDim.x) {
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(512) dd_focus_kernel(DdArgs a, const float2* _
         other[idx] = res[g * Nb + f];
     }
     __syncthreads();
-    res = stockham(other, res, Nb, G, a.log2_g, tw_gf);
+    res = stockham4(other, res, Nb, G, a.log2_g, tw_gf, -1);
     other = (res == buf0) ? buf1 : buf0;
     for (int idx = threadIdx.x; idx < Nb * G; idx += blockDim.x) {
         const int f = idx / G, q = idx - f * G;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(512) dd_focus_kernel(DdArgs a, const float2* _
         res[idx] = cmul(res[idx], make_float2(c, s));
     }
     __syncthreads();
-    res = stockham(res, other, Nb, G, a.log2_g, tw_gi);
+    res = stockham4(res, other, Nb, G, a.log2_g, tw_gi, 1);
     const float inv_g = 1.0f / (float)G;
     // 4. outputs
     if (focused) {

@@ -3,7 +3,7 @@
 //
 // Forward: one CTA per (segment i, block of gates).  It stages the spectra of updates i
 // and i+1 for its gates in shared memory, runs the n_doppler-point inverse transforms
-// there (radix-2 Stockham autosort, unnormalised, twiddles exp(+j 2 pi r / N)), and
+// there (radix-4 Stockham autosort, unnormalised, twiddles exp(+j 2 pi r / N)), and
 // writes the blended pulses x in [p_i, p_{i+1}) directly:
 //   Y[x, g] = W(u) s_i[g, (x - p_i) mod N] + W(1 - u) s_{i+1}[g, (x - p_{i+1}) mod N],
 //   u = (x - p_i) / n_fast.
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) synth_kernel(SynthArgs a, int64_t seg0, i
         buf0[idx] = v;
     }
     __syncthreads();
-    const T* res = stockham(buf0, buf1, 2 * gpc, N, a.log2_nd, tw);
+    const T* res = stockham4(buf0, buf1, 2 * gpc, N, a.log2_nd, tw, 1);
     const int64_t p_i = i * a.n_fast;
     const int64_t x_lo = max(p_i, a.pulse0);
     const int64_t x_hi = min(p_i + a.n_fast, a.pulse0 + a.n_pulses);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) synth_backward_kernel(
         buf0[gg * N + m] = acc;
     }
     __syncthreads();
-    const T* res = stockham(buf0, buf1, gpc, N, a.log2_nd, tw);
+    const T* res = stockham4(buf0, buf1, gpc, N, a.log2_nd, tw, -1);
     for (int idx = threadIdx.x; idx < gpc * N; idx += blockDim.x) {
         const int gg = idx / N, k = idx - gg * N;
         const int g = g0 + gg;
