@@ -82,7 +82,11 @@ __device__ __forceinline__ ItemF item_split(const Model& m, float x, float y, fl
     it.amp0 = sqrtf(nrcs * area);
     const float epv = fmaf(m.ep[0], vx, fmaf(m.ep[1], vy, m.ep[2] * vz));
     const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-    it.c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
+    const float c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
+    const float ex = fmaf(-vx, m.dt_f, m.ep[0]), ey = fmaf(-vy, m.dt_f, m.ep[1]);
+    const float ez = fmaf(-vz, m.dt_f, m.ep[2]);
+    it.gam = fmaf(it.lx0, ex, fmaf(it.ly0, ey, fmaf(z, ez, c1)));
+    it.beta = fmaf(vx, ex, fmaf(vy, ey, vz * ez));
     return it;
 }
 

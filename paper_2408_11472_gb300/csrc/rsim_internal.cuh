@@ -39,6 +39,9 @@ static_assert(kThreads >= kTab && kThreads % 32 == 0, "CTA size");
 constexpr float kGateEps = 2e-5f;
 constexpr float kBinEps = 5e-6f;
 constexpr float kEpsSlope = 4e-7f;
+// 1.5 2^23: for |x| < 2^22, x + kRoundMagic is an integer-valued float whose bit pattern is
+// that of kRoundMagic plus rint(x)
+constexpr float kRoundMagic = 12582912.0f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kInvLn2F = 1.44269504088896340736f;
 
@@ -353,15 +356,18 @@ __device__ __forceinline__ int cta_reaches_window(const Model& m, const double* 
 struct __align__(16) SplitConst {
     float4 a;   // t - t0 (scatterer time since the set's epoch), D_x, D_y, D_z
     float4 b;   // D / R_c (x, y, z), 1 / (2 R_c)
-    float4 c;   // 1 / R_c, frac of the gate coordinate of c, 2 R_c / lambda - rint(.), log2 (r_ref/R_c)^2
+    float4 c;   // 1 / R_c, frac of the gate coordinate of c less 1/2, 2 R_c / lambda - rint(.),
+                // log2 (r_ref/R_c)^2
     float4 d;   // beam_k / D_z^2, K0 = M . e_p as hi + lo (M = D + e_p/2), -n_doppler 2 / (lambda R_c)
     float4 e;   // floor of the gate coordinate of c (int bits); active flag, then the sample
                 // index (int bits); the sample's workspace slice (pointer bits, lo + hi)
+    float4 f;   // D dt (x, y, z) with dt = 1 / PRF; band of the FP32 gate decision
 };
 
 // Register copy of one table entry.
 struct SampleF {
-    float t, Dx, Dy, Dz, ux, uy, uz, h, invRc, gfrac, psic, l2kappa, kq, K0hi, K0lo, kbin;
+    float t, Dx, Dy, Dz, ux, uy, uz, h, invRc, gfrac_h, psic, l2kappa, kq, K0hi, K0lo, kbin;
+    float dtDx, dtDy, dtDz, gthr;
     int gint;
 };
 
@@ -386,12 +392,13 @@ __device__ __forceinline__ unsigned long long* sample_out(const SplitConst& s) {
 }
 
 __device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
-    const float4 a = s.a, b = s.b, c = s.c, d = s.d;
+    const float4 a = s.a, b = s.b, c = s.c, d = s.d, f = s.f;
     SampleF k;
     k.t = a.x; k.Dx = a.y; k.Dy = a.z; k.Dz = a.w;
     k.ux = b.x; k.uy = b.y; k.uz = b.z; k.h = b.w;
-    k.invRc = c.x; k.gfrac = c.y; k.psic = c.z; k.l2kappa = c.w;
+    k.invRc = c.x; k.gfrac_h = c.y; k.psic = c.z; k.l2kappa = c.w;
     k.kq = d.x; k.K0hi = d.y; k.K0lo = d.z; k.kbin = d.w;
+    k.dtDx = f.x; k.dtDy = f.y; k.dtDz = f.z; k.gthr = f.w;
     k.gint = __float_as_int(s.e.x);
     return k;
 }
@@ -425,19 +432,28 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, const dou
     SplitConst k;
     k.a = make_float4((float)ts, (float)Dx, (float)Dy, (float)Dz);
     k.b = make_float4((float)(Dx * inv), (float)(Dy * inv), (float)(Dz * inv), (float)(0.5 * inv));
-    k.c = make_float4((float)inv, (float)(G - Gi), (float)psi, 2.0f * kInvLn2F * log1pf(xref));
+    k.c = make_float4((float)inv, (float)(G - Gi - 0.5), (float)psi, 2.0f * kInvLn2F * log1pf(xref));
     k.d = make_float4(m.beam_k_f * invDz * invDz, K0hi, (float)(K0 - (double)K0hi),
                       (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
-    k.e = make_float4(__int_as_float((int)fmax(fmin(Gi, 1.0e9), -1.0e9)),
+    const double gi = fmax(fmin(Gi, 1.0e9), -1.0e9);
+    k.e = make_float4(__int_as_float((int)gi),
                       __int_as_float(window_reachable(m, G, ts, lmax, vmax)), 0.f, 0.f);
+    // an item inside the window has |gate coordinate - gi| <= max(|gi|, |n_gates - gi|): the
+    // FP32 error of its coordinate grows with that bound (out-of-window items need no band)
+    const double gspan = fmax(fabs(gi), fabs((double)m.n_gates - gi)) + 2.0;
+    k.f = make_float4((float)(Dx * dt), (float)(Dy * dt), (float)(Dz * dt),
+                      (float)(0.5 - (double)kGateEps - (double)kEpsSlope * gspan));
     return k;
 }
 
 // Scatterer registers of the split path (positions relative to the CTA reference point).
 // c1 = dt (e_p . v) - dt^2 |v|^2 / 2 is the part of the pulse-pair range change that depends
 // on the scatterer alone.
+// e = e_p - v dt is the scatterer's displacement relative to the platform over one PRI;
+// gam = l0.e + c1 and beta = v.e carry the item's part of the pulse-pair range change
+// (c1 = dt e_p.v - dt^2 |v|^2 / 2, l0 = (lx0, ly0, z) the position at the set's epoch).
 struct ItemF {
-    float lx0, ly0, z, vx, vy, vz, amp0, c1;  // padding past the end of a set: amp0 = 0
+    float lx0, ly0, z, vx, vy, vz, amp0, gam, beta;  // padding past the end of a set: amp0 = 0
 };
 
 // Quantities the adjoint needs besides C.
@@ -493,12 +509,15 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
     const float dR0 = fmaf(ll, k.h, -ul);
     const float dR = dR0 * fmaf(-dR0, k.h, 1.0f);
-    // gate: floor of the coordinate; re-decided in FP64 within the band of an edge
-    const float gcf = fmaf(dR, m.inv_gw_f, k.gfrac);
-    const float gfl = floorf(gcf);
-    int g = k.gint + (int)gfl;
-    int fl = (fabsf((gcf - gfl) - 0.5f) > fmaf(-fabsf(gcf), kEpsSlope, 0.5f - kGateEps))
-                 ? kFlagRefine : 0;
+    // gate: the coordinate less 1/2 (gch), rounded to the nearest integer, is the offset from
+    // the reference gate, read from the low mantissa bits of gch + 1.5 2^23 (|gch| < 2^22; a
+    // larger |gch| lands outside the window, or the sample's band flags every item); cell
+    // edges sit at half-integers of gch, and items within the band of one are re-decided in
+    // FP64
+    const float gch = fmaf(dR, m.inv_gw_f, k.gfrac_h);
+    const float gr = gch + kRoundMagic;
+    int g = k.gint + (__float_as_int(gr) - __float_as_int(kRoundMagic));
+    int fl = fabsf(gch - (gr - kRoundMagic)) > k.gthr ? kFlagRefine : 0;
     // |C| = sqrt(sigma A) 2^E, E = beam_k atan(q)^2 + log2 (r_ref/R_c)^2 - 2 log2(1 + dR/R_c),
     // q = rho / d_z (series in qb = beam_k q^2 below 0.01 q^2; the exact angle beyond)
     const float dx = k.Dx - lx, dy = k.Dy - ly;
@@ -521,8 +540,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     // phase in cycles: psi_c + dR 2/lambda (2/lambda as hi + lo, the product error-free)
     const float p = dR * m.chi_hi;
     const float perr = fmaf(dR, m.chi_hi, -p);
-    float f = (p - rintf(p)) + (k.psic + fmaf(dR, m.chi_lo, perr));
-    f -= rintf(f);
+    // |f| <= 1 cycle: the hardware sine and cosine take their arguments modulo one turn
+    const float f = (p - rintf(p)) + (k.psic + fmaf(dR, m.chi_lo, perr));
     float sn, cs;
     __sincosf(kTwoPiF * f, &sn, &cs);
     float2 gu, gv, G;
@@ -555,18 +574,20 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     float b = 0.0f;
     if (DOPPLER) {
         // pulse-pair range change D = 2 (d + e/2).e / (R + R'), d = D - l, e = e_p - v dt:
-        // (d + e/2).e = K0 - l.e_p - dt (d.v) - c1;  b = nu n_doppler = -n_doppler 2 D / lambda
-        // (unwrapped: the bin is taken mod n_doppler); bin = nearest integer to b
-        const float dz = k.Dz - lz;
-        const float dv_ = fmaf(dx, it.vx, fmaf(dy, it.vy, dz * it.vz));
-        const float lep = fmaf(lx, m.ep[0], fmaf(ly, m.ep[1], lz * m.ep[2]));
-        const float hn2 = ((fmaf(-m.dt_f, dv_, k.K0hi) - lep) - it.c1) + k.K0lo;
-        b = hn2 * k.kbin;
+        // (d + e/2).e = K0 - dt (d.v) - l.e_p - c1, and with l = l0 + v t,
+        // dt (d.v) + l.e_p = dt (D.v) + l0.e + t (v.e);  b = nu n_doppler = -n_doppler 2 D /
+        // lambda (unwrapped: the bin is taken mod n_doppler); bin = nearest integer to b
+        const float item = fmaf(k.dtDx, it.vx, fmaf(k.dtDy, it.vy,
+                                fmaf(k.dtDz, it.vz, fmaf(k.t, it.beta, it.gam))));
+        b = ((k.K0hi - item) + k.K0lo) * k.kbin;
         b = fmaf(-b, xr, b);                       // 1 / (R_c + dR) = (1 / R_c)(1 - dR / R_c)
         if (ANT) b += pat_bins;
-        const float br = rintf(b);
-        kb = __float2int_rn(b) & (m.n_doppler - 1);
-        if (fabsf(b - br) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps)) fl |= kFlagRefine;
+        // nearest integer mod n_doppler (a power of two <= 2^22) from the low mantissa bits;
+        // beyond |b| ~ 1e6 the band below flags every item
+        const float bm = b + kRoundMagic;
+        kb = __float_as_int(bm) & (m.n_doppler - 1);
+        if (fabsf(b - (bm - kRoundMagic)) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps))
+            fl |= kFlagRefine;
     }
     if (DERIV) {
         // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
@@ -594,7 +615,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
             dv->pat = make_float2(0.f, 0.f);
         }
     }
-    double gcd = (double)k.gint + (double)gcf;
+    double gcd = (double)k.gint + (double)gch + 0.5;
     double bcd = (double)b - (double)m.n_doppler * rint((double)b / (double)m.n_doppler) + 0.5;
     if (GENERAL && (fl & kFlagRefine)) {
         int g2, kb2;
@@ -705,7 +726,16 @@ __device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, con
 // on this GPU; one per emitted run made that pipe the bottleneck of the whole summation.
 // Here v = t + r with t = trunc(v) and |r| < 1 (both exact in FP32), and only 32-bit
 // conversions are used.
+#ifndef RSIM_F2I64
+#define RSIM_F2I64 0
+#endif
+#ifndef RSIM_ZCHK
+#define RSIM_ZCHK 1
+#endif
 __device__ __forceinline__ long long fixed_from_f32(float v) {
+#if RSIM_F2I64
+    return __float2ll_rn(v * 4294967296.0f);
+#endif
     const float t = truncf(v);
     const float r = v - t;
     const long long hi = (long long)__float2int_rz(t);
@@ -752,8 +782,8 @@ template <typename T>
 __device__ __forceinline__ void emit_cell(unsigned long long* __restrict__ base, int key, T re,
                                           T im) {
     const long long qr = to_fixed(re), qi = to_fixed(im);
-    if (qr) red_add_u64(base + 2 * (int64_t)key, (unsigned long long)qr);
-    if (qi) red_add_u64(base + 2 * (int64_t)key + 1, (unsigned long long)qi);
+    if (!RSIM_ZCHK || qr) red_add_u64(base + 2 * (int64_t)key, (unsigned long long)qr);
+    if (!RSIM_ZCHK || qi) red_add_u64(base + 2 * (int64_t)key + 1, (unsigned long long)qi);
 }
 
 template <typename T, int J>
@@ -767,32 +797,30 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
     sr[0] = re[0];
     si[0] = im[0];
     unsigned tails = 0u;
-    int first_end = J - 1;
 #pragma unroll
     for (int q = 1; q < J; ++q) {
         const bool same = key[q] == key[q - 1];
         sr[q] = same ? sr[q - 1] + re[q] : re[q];
         si[q] = same ? si[q - 1] + im[q] : im[q];
-        if (!same) {
-            tails |= 1u << (q - 1);
-            first_end = min(first_end, q - 1);
-        }
+        if (!same) tails |= 1u << (q - 1);
     }
     const bool uniform = tails == 0u;
+    const int first_end = __ffs(tails | (1u << (J - 1))) - 1;  // end of the lane's first run
     const int prev_last = __shfl_up_sync(kFull, key[J - 1], 1);
     const bool link = lane > 0 && prev_last == key[0];  // first run continues lane-1's last run
-    // segmented inclusive scan (fixed order) of the lanes' last-run sums
+    // segmented inclusive scan (fixed order) of the lanes' last-run sums; a lane heads a
+    // segment unless all its items continue lane-1's last run, and a lane at distance dist
+    // from its segment's head takes the partial of lane - d while d <= dist
     T cr = sr[J - 1], ci = si[J - 1];
-    int head = (!uniform || !link) ? 1 : 0;
+    const unsigned heads = __ballot_sync(kFull, !uniform || !link);  // bit 0 always set
+    const int dist = lane - (31 - __clz(heads & (kFull >> (31 - lane))));
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const T ur = __shfl_up_sync(kFull, cr, d);
         const T ui = __shfl_up_sync(kFull, ci, d);
-        const int uh = __shfl_up_sync(kFull, head, d);
-        if (lane >= d && !head) {
+        if (dist >= d) {
             cr = ur + cr;
             ci = ui + ci;
-            head = uh;
         }
     }
     T in_r = __shfl_up_sync(kFull, cr, 1), in_i = __shfl_up_sync(kFull, ci, 1);
