@@ -24,34 +24,38 @@ namespace rsim {
 
 namespace {
 
-// Load kItems consecutive floats starting at base (vectorised when all arrays are 16-byte
-// aligned and the items are in range; base is a multiple of kItems).
+// Load IT consecutive floats starting at base (vectorised when all arrays are 16-byte
+// aligned and the items are in range; base is a multiple of IT).
+template <int IT>
 __device__ __forceinline__ void load_items(const float* __restrict__ p, int64_t base, int64_t n,
-                                           bool vec, float (&v)[kItems]) {
-    if (vec && base + kItems <= n) {
-        if (kItems % 4 == 0) {
+                                           bool vec, float (&v)[IT]) {
+    if (vec && base + IT <= n) {
+        if (IT % 4 == 0) {
 #pragma unroll
-            for (int j = 0; j < kItems / 4; ++j) {
+            for (int j = 0; j < IT / 4; ++j) {
                 const float4 q = __ldcs(reinterpret_cast<const float4*>(p + base) + j);
                 v[4 * j + 0] = q.x; v[4 * j + 1] = q.y; v[4 * j + 2] = q.z; v[4 * j + 3] = q.w;
             }
-        } else if (kItems == 2) {
+        } else if (IT == 2) {
             const float2 q = __ldcs(reinterpret_cast<const float2*>(p + base));
-            v[0] = q.x; v[kItems - 1] = q.y;
+            v[0] = q.x; v[IT - 1] = q.y;
         } else {
             v[0] = __ldcs(p + base);
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < kItems; ++q) v[q] = (base + q < n) ? __ldcs(p + base + q) : 0.0f;
+        for (int q = 0; q < IT; ++q) v[q] = (base + q < n) ? __ldcs(p + base + q) : 0.0f;
     }
 }
 
-struct Raw {
-    float x[kItems], y[kItems], z[kItems], vx[kItems], vy[kItems], vz[kItems], s[kItems];
+template <int IT>
+struct RawT {
+    float x[IT], y[IT], z[IT], vx[IT], vy[IT], vz[IT], s[IT];
 };
+using Raw = RawT<kItems>;
 
-__device__ __forceinline__ void load_raw(const Scat& sc, int64_t base, Raw& r) {
+template <int IT>
+__device__ __forceinline__ void load_raw(const Scat& sc, int64_t base, RawT<IT>& r) {
     const bool vec = sc.vec4 != 0;
     load_items(sc.x, base, sc.n, vec, r.x);
     load_items(sc.y, base, sc.n, vec, r.y);
@@ -90,10 +94,11 @@ __device__ __forceinline__ ItemF item_split(const Model& m, float x, float y, fl
     return it;
 }
 
-__device__ __forceinline__ void items_split(const Model& m, const Raw& r, float cx, float cy,
-                                            float area, ItemF (&it)[kItems]) {
+template <int IT>
+__device__ __forceinline__ void items_split(const Model& m, const RawT<IT>& r, float cx, float cy,
+                                            float area, ItemF (&it)[IT]) {
 #pragma unroll
-    for (int q = 0; q < kItems; ++q)
+    for (int q = 0; q < IT; ++q)
         it[q] = item_split(m, r.x[q], r.y[q], r.z[q], r.vx[q], r.vy[q], r.vz[q], r.s[q], cx, cy,
                            area);
 }
@@ -114,11 +119,12 @@ __device__ __forceinline__ void items_fp64(const Raw& r, double area, ItemD (&it
 // Culling bounds of the CTA's scatterers around its reference point (cx, cy, 0):
 // lmax >= max |r - c|, vmax >= max |v| over the real (non-padding) items, enlarged so that
 // FP32 rounding of the norms cannot make the bound too tight.
-__device__ __forceinline__ void chunk_bounds(const Raw& r, float cx, float cy, int64_t base,
+template <int IT>
+__device__ __forceinline__ void chunk_bounds(const RawT<IT>& r, float cx, float cy, int64_t base,
                                              int64_t n, float* s_red) {
     float l = 0.f, v = 0.f;
 #pragma unroll
-    for (int q = 0; q < kItems; ++q) {
+    for (int q = 0; q < IT; ++q) {
         if (base + q < n) {
             const float dx = r.x[q] - cx, dy = r.y[q] - cy;
             l = fmaxf(l, sqrtf(fmaf(dx, dx, fmaf(dy, dy, r.z[q] * r.z[q]))));
@@ -150,8 +156,9 @@ __device__ __forceinline__ int64_t sample_pulse(const Schedule& sch, int s) {
 // scatterers can reach the range window there.  Returns how many can (CTA-uniform) and sets
 // slot to this thread's place among them, in sample order.  s_cnt: one int per warp.
 // Every thread of the CTA calls this (it holds a barrier).
+template <int TH = kThreads>
 __device__ __forceinline__ int compact_samples(bool act, int* s_cnt, int& slot) {
-    constexpr int kWarps = kThreads / 32;
+    constexpr int kWarps = TH / 32;
     const unsigned bal = __ballot_sync(0xffffffffu, act);
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) s_cnt[w] = __popc(bal);
@@ -185,7 +192,7 @@ struct ChunkCtx {
 // that rare, register-hungry path out of the per-sample loop keeps the loop within the
 // register budget.  Every contribution is added in fixed point, so the split between
 // merged and single additions does not change the result's determinism.
-constexpr int kQueue = 64 * kItems;  // entries per warp; flushed before it can overflow
+constexpr int queue_len(int items) { return 64 * items; }  // entries per warp; flushed before it can overflow
 
 template <bool DOPPLER, bool ANT>
 __device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t chunk0, float cx,
@@ -209,25 +216,28 @@ __device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t
     __syncwarp();
 }
 
-template <bool DOPPLER, bool ANT>
+template <bool DOPPLER, bool ANT, int IT>
 __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Schedule& sch,
                                                        const ChunkCtx& cx_, int s_begin,
                                                        int s_end) {
+    constexpr int TH = kChunk / IT;       // threads of the CTA
+    constexpr int kQueue = queue_len(IT);
+    static_assert(TH >= kTab && TH % 32 == 0, "CTA shape");
     __shared__ SplitConst tab[kTab];
     __shared__ Fp64Const tab64[kTab];
     __shared__ float s_red[2];
-    __shared__ int s_cnt[kThreads / 32];
-    __shared__ int s_queue[kThreads / 32][kQueue];
+    __shared__ int s_cnt[TH / 32];
+    __shared__ int s_queue[TH / 32][kQueue];
     constexpr unsigned kFull = 0xffffffffu;
     const Scat& sc = *cx_.sc;
     const int lane = threadIdx.x & 31;
     int* const queue = s_queue[threadIdx.x >> 5];
     float cx, cy;
     chunk_ref(sc, cx_.chunk0, cx, cy);
-    ItemF it[kItems];
+    ItemF it[IT];
     {
-        const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * kItems;
-        Raw r;
+        const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * IT;
+        RawT<IT> r;
         load_raw(sc, base, r);
         items_split(m, r, cx, cy, cx_.area, it);
         chunk_bounds(r, cx, cy, base, sc.n, s_red);
@@ -242,7 +252,7 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
         const bool act = threadIdx.x < nb &&
                          cta_reaches_window(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
         int slot;
-        const int na = compact_samples(act, s_cnt, slot);
+        const int na = compact_samples<TH>(act, s_cnt, slot);
         if (act) {
             SplitConst kc = make_split_const(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
             set_sample_slot(kc, s, cx_.ws + (int64_t)s * cells * 2);
@@ -253,11 +263,11 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
         int nq = 0;  // entries in this warp's queue (warp-uniform)
         for (int j = 0; j < na; ++j) {
             const SampleF k = load_sample(tab[j]);
-            int key[kItems];
-            float re[kItems], im[kItems];
+            int key[IT];
+            float re[IT], im[IT];
             int fl = 0;
 #pragma unroll
-            for (int q = 0; q < kItems; ++q) {
+            for (int q = 0; q < IT; ++q) {
                 int f;
                 key[q] = eval_split<DOPPLER, false, false, ANT>(m, k, it[q], re[q], im[q], f);
                 if (f) key[q] = -1;  // deferred to the exact evaluation
@@ -265,17 +275,17 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             }
             if (__any_sync(kFull, fl != 0)) {  // rare: queue the flagged items
 #pragma unroll
-                for (int q = 0; q < kItems; ++q) {
+                for (int q = 0; q < IT; ++q) {
                     const bool mine = (fl >> q) & 1;
                     const unsigned b = __ballot_sync(kFull, mine);
                     if (mine)
                         queue[nq + __popc(b & ((1u << lane) - 1u))] =
-                            (threadIdx.x * kItems + q) | (j << 16);
+                            (threadIdx.x * IT + q) | (j << 16);
                     nq += __popc(b);
                 }
             }
-            warp_reduce_emit<float, kItems>(key, re, im, sample_out(tab[j]));
-            if (nq > kQueue - 32 * kItems) {  // room for one more sample's worth
+            warp_reduce_emit<float, IT>(key, re, im, sample_out(tab[j]));
+            if (nq > kQueue - 32 * IT) {  // room for one more sample's worth
                 __syncwarp();
                 flush_queue<DOPPLER, ANT>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
                 nq = 0;
@@ -365,7 +375,7 @@ __device__ __forceinline__ ChunkCtx batch_ctx(const BatchParams& bp, int r, int6
 
 // ------------------------------------------------------------------------------- forward
 template <bool DOPPLER, bool ANT>
-__global__ void __launch_bounds__(kThreads, ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_kernel(
+__global__ void __launch_bounds__(kChunk / split_items(ANT), ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
     unsigned long long* __restrict__ ws) {
     ChunkCtx c;
@@ -376,17 +386,17 @@ __global__ void __launch_bounds__(kThreads, ANT ? kMinBlocksAnt : kMinBlocks) ac
     c.ws = ws;
     int s0, s1;
     sample_range(sch, s0, s1);
-    accumulate_split_chunk<DOPPLER, ANT>(m, sch, c, s0, s1);
+    accumulate_split_chunk<DOPPLER, ANT, split_items(ANT)>(m, sch, c, s0, s1);
 }
 
 template <bool DOPPLER, bool ANT>
-__global__ void __launch_bounds__(kThreads, ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_batched_kernel(
+__global__ void __launch_bounds__(kChunk / split_items(ANT), ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_batched_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ BatchParams bp) {
     const int r = batch_find(bp, blockIdx.x);
     const ChunkCtx c = batch_ctx(bp, r, blockIdx.x);
     int s0, s1;
     sample_range(sch, s0, s1);
-    accumulate_split_chunk<DOPPLER, ANT>(m, sch, c, s0, s1);
+    accumulate_split_chunk<DOPPLER, ANT, split_items(ANT)>(m, sch, c, s0, s1);
 }
 
 template <bool DOPPLER, bool ANT>
@@ -664,11 +674,11 @@ cudaError_t launch_accumulate(const Model& m, const Schedule& sch, const Scat& s
         }
     } else {
         if (ant) {
-            if (doppler) accumulate_split_kernel<true, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
-            else accumulate_split_kernel<false, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+            if (doppler) accumulate_split_kernel<true, true><<<grid, kChunk / split_items(true), 0, stream>>>(m, sch, sc, ws);
+            else accumulate_split_kernel<false, true><<<grid, kChunk / split_items(true), 0, stream>>>(m, sch, sc, ws);
         } else {
-            if (doppler) accumulate_split_kernel<true, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
-            else accumulate_split_kernel<false, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, ws);
+            if (doppler) accumulate_split_kernel<true, false><<<grid, kChunk / split_items(false), 0, stream>>>(m, sch, sc, ws);
+            else accumulate_split_kernel<false, false><<<grid, kChunk / split_items(false), 0, stream>>>(m, sch, sc, ws);
         }
     }
     return cudaGetLastError();
@@ -687,11 +697,11 @@ cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const
         }
     } else {
         if (ant) {
-            if (doppler) accumulate_split_batched_kernel<true, true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
-            else accumulate_split_batched_kernel<false, true><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+            if (doppler) accumulate_split_batched_kernel<true, true><<<grid, kChunk / split_items(true), 0, stream>>>(m, sch, bp);
+            else accumulate_split_batched_kernel<false, true><<<grid, kChunk / split_items(true), 0, stream>>>(m, sch, bp);
         } else {
-            if (doppler) accumulate_split_batched_kernel<true, false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
-            else accumulate_split_batched_kernel<false, false><<<grid, kThreads, 0, stream>>>(m, sch, bp);
+            if (doppler) accumulate_split_batched_kernel<true, false><<<grid, kChunk / split_items(false), 0, stream>>>(m, sch, bp);
+            else accumulate_split_batched_kernel<false, false><<<grid, kChunk / split_items(false), 0, stream>>>(m, sch, bp);
         }
     }
     return cudaGetLastError();

@@ -18,20 +18,32 @@ namespace rsim {
 #define RSIM_THREADS 128
 #endif
 #ifndef RSIM_ITEMS
-#define RSIM_ITEMS 4
+#define RSIM_ITEMS 8
 #endif
 #ifndef RSIM_MIN_BLOCKS
-#define RSIM_MIN_BLOCKS 6
+#define RSIM_MIN_BLOCKS 4
+#endif
+#ifndef RSIM_ITEMS_ANT
+#define RSIM_ITEMS_ANT 4
+#endif
+#ifndef RSIM_MIN_BLOCKS_ANT
+#define RSIM_MIN_BLOCKS_ANT 2
 #endif
 constexpr int kThreads = RSIM_THREADS;        // summation CTA size
 constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (1, 2, 4, 8)
 constexpr int kMinBlocks = RSIM_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
-constexpr int kMinBlocksAnt = 4;              // the same with a tabulated antenna pattern
 constexpr int kChunk = kThreads * kItems;     // scatterers sharing one FP64 reference point
-constexpr int kTab = 128;                     // samples per block of reference constants
+// The split summation kernels with a tabulated antenna pattern hold more per item, so they
+// run the same chunk with fewer items per thread (and more threads).
+constexpr int kItemsAnt = RSIM_ITEMS_ANT;
+constexpr int kMinBlocksAnt = RSIM_MIN_BLOCKS_ANT;
+constexpr int split_items(bool ant) { return ant ? kItemsAnt : kItems; }
+constexpr int kTab = kThreads < 128 ? kThreads : 128;  // samples per block of reference constants
 constexpr double kFixScale = 4294967296.0;    // fixed point: value = q * 2^-32
 static_assert(kItems == 1 || kItems == 2 || kItems == 4 || kItems == 8, "items per thread");
-static_assert(kThreads >= kTab && kThreads % 32 == 0, "CTA size");
+static_assert(kChunk % kItemsAnt == 0 && (kChunk / kItemsAnt) % 32 == 0 && kChunk / kItemsAnt <= 1024,
+              "antenna CTA shape");
+static_assert(kThreads >= 64 && kThreads >= kTab && kThreads % 32 == 0, "CTA size");
 // Split path: an FP32 gate / bin coordinate this close to an integer edge is re-decided
 // in FP64.  The FP32 coordinate error grows with the coordinate's distance from the
 // CTA reference point (about 3e-7 of it) on top of a few 1e-7 absolute, so the band is

@@ -166,7 +166,8 @@ def test_host_streamer_overlaps_copies_and_matches(rsim):
     u0, S = rsim.spectra_range(0, P, fp.n_fast)
     hs = rsim.HostStreamer(scene["x"].size, rd.n_gates, fp.n_doppler, S, chunks=3)
     assert len(hs.ranges) == 3 and hs.ranges[0][0] == 0 and hs.ranges[-1][1] == scene["x"].size
-    assert all(a % 512 == 0 for a, _ in hs.ranges)
+    from paper_2408_11472_gb300.sharding import block_scatterers
+    assert all(a % block_scatterers() == 0 for a, _ in hs.ranges)
     T, Y = hs.run(rd, pf, host, P, fp.n_fast, fp.n_doppler, fp.window)
     dev = rsim.Scatterers.from_arrays(scene)
     T1, Y1 = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window)
