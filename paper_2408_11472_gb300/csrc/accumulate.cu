@@ -192,7 +192,7 @@ struct ChunkCtx {
 // that rare, register-hungry path out of the per-sample loop keeps the loop within the
 // register budget.  Every contribution is added in fixed point, so the split between
 // merged and single additions does not change the result's determinism.
-constexpr int queue_len(int items) { return 64 * items; }  // entries per warp; flushed before it can overflow
+__host__ __device__ constexpr int queue_len(int items) { return 64 * items; }  // entries per warp; flushed before it can overflow
 
 template <bool DOPPLER, bool ANT>
 __device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t chunk0, float cx,
@@ -265,18 +265,17 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             const SampleF k = load_sample(tab[j]);
             int key[IT];
             float re[IT], im[IT];
-            int fl = 0;
+            bool deferred = false;
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
                 int f;
                 key[q] = eval_split<DOPPLER, false, false, ANT>(m, k, it[q], re[q], im[q], f);
-                if (f) key[q] = -1;  // deferred to the exact evaluation
-                fl |= (f != 0) << q;
+                deferred |= key[q] == kKeyDeferred;
             }
-            if (__any_sync(kFull, fl != 0)) {  // rare: queue the flagged items
+            if (__any_sync(kFull, deferred)) {  // rare: queue the flagged items
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {
-                    const bool mine = (fl >> q) & 1;
+                    const bool mine = key[q] == kKeyDeferred;
                     const unsigned b = __ballot_sync(kFull, mine);
                     if (mine)
                         queue[nq + __popc(b & ((1u << lane) - 1u))] =

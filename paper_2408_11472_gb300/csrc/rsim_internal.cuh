@@ -37,7 +37,7 @@ constexpr int kChunk = kThreads * kItems;     // scatterers sharing one FP64 ref
 // run the same chunk with fewer items per thread (and more threads).
 constexpr int kItemsAnt = RSIM_ITEMS_ANT;
 constexpr int kMinBlocksAnt = RSIM_MIN_BLOCKS_ANT;
-constexpr int split_items(bool ant) { return ant ? kItemsAnt : kItems; }
+__host__ __device__ constexpr int split_items(bool ant) { return ant ? kItemsAnt : kItems; }
 constexpr int kTab = kThreads < 128 ? kThreads : 128;  // samples per block of reference constants
 constexpr double kFixScale = 4294967296.0;    // fixed point: value = q * 2^-32
 static_assert(kItems == 1 || kItems == 2 || kItems == 4 || kItems == 8, "items per thread");
@@ -478,6 +478,9 @@ struct DerivF {
 // Result flags of the fast evaluation.
 constexpr int kFlagRefine = 1;  // gate or bin coordinate within rounding of a cell edge
 constexpr int kFlagWide = 2;    // off-nadir angle beyond the series' range (q^2 >= 0.01)
+// Key of an item the fast evaluation defers to the exact one (distinct from -1, out of the
+// window; both are below every cell key).
+constexpr int kKeyDeferred = -2;
 
 // FP64 re-decision of the gate and bin of one scatterer (kept out of line so that none of
 // its FP64 work is hoisted into the common path).
@@ -503,7 +506,8 @@ static __device__ __noinline__ void refine_fp64(const Model& m, const Fp64Const&
 // Split-path evaluation of one scatterer at one sample.  Returns the cell key
 // g * n_doppler + bin, or -1 when out of the range window or not a scatterer.
 // GENERAL = false: straight-line code; items that need the FP64 re-decision or the exact
-//   off-nadir angle are only flagged (the caller re-evaluates them with GENERAL = true).
+//   off-nadir angle are only flagged, and their key is kKeyDeferred (the caller
+//   re-evaluates them with GENERAL = true).
 // GENERAL = true: takes those branches (tab64 and the scatterer's original x, y needed).
 // For unflagged items both give bit-identical results.
 template <bool DOPPLER, bool GENERAL, bool DERIV, bool ANT = false>
@@ -529,7 +533,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float gch = fmaf(dR, m.inv_gw_f, k.gfrac_h);
     const float gr = gch + kRoundMagic;
     int g = k.gint + (__float_as_int(gr) - __float_as_int(kRoundMagic));
-    int fl = fabsf(gch - (gr - kRoundMagic)) > k.gthr ? kFlagRefine : 0;
+    const bool gflag = fabsf(gch - (gr - kRoundMagic)) > k.gthr;
+    bool wide = false, bflag = false;
     // |C| = sqrt(sigma A) 2^E, E = beam_k atan(q)^2 + log2 (r_ref/R_c)^2 - 2 log2(1 + dR/R_c),
     // q = rho / d_z (series in qb = beam_k q^2 below 0.01 q^2; the exact angle beyond)
     const float dx = k.Dx - lx, dy = k.Dy - ly;
@@ -538,8 +543,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     float T = k.l2kappa;  // tabulated pattern: applied to C below
     if (!ANT) {
         T = fmaf(qb, fmaf(qb, fmaf(qb, m.s2, m.s1), 1.0f), k.l2kappa);
-        if (qb < m.qb_wide) {
-            fl |= kFlagWide;
+        wide = qb < m.qb_wide;
+        if (wide) {
             if (GENERAL) {
                 const float th = atan2f(sqrtf(rho2), k.Dz - lz);
                 T = fmaf(th * th, m.beam_k_f, k.l2kappa);
@@ -598,8 +603,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         // beyond |b| ~ 1e6 the band below flags every item
         const float bm = b + kRoundMagic;
         kb = __float_as_int(bm) & (m.n_doppler - 1);
-        if (fabsf(b - (bm - kRoundMagic)) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps))
-            fl |= kFlagRefine;
+        bflag = fabsf(b - (bm - kRoundMagic)) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps);
     }
     if (DERIV) {
         // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
@@ -629,19 +633,21 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     }
     double gcd = (double)k.gint + (double)gch + 0.5;
     double bcd = (double)b - (double)m.n_doppler * rint((double)b / (double)m.n_doppler) + 0.5;
-    if (GENERAL && (fl & kFlagRefine)) {
+    const bool refine = gflag || bflag;
+    if (GENERAL && refine) {
         int g2, kb2;
         refine_fp64<ANT>(m, *k64, (double)x_orig, (double)y_orig, (double)it.z, (double)it.vx,
                     (double)it.vy, (double)it.vz, DOPPLER, &g2, &kb2, &gcd, &bcd);
         g = g2;
         kb = kb2;
     }
-    flags = fl;
+    flags = (refine ? kFlagRefine : 0) | (wide ? kFlagWide : 0);
     if (g_out) *g_out = g;
     if (gc_out) *gc_out = gcd;
     if (bc_out) *bc_out = bcd;
     // padding items (past the end of the set) carry zero amplitude: harmless in any cell
-    return ((unsigned)g < (unsigned)m.n_gates) ? g * m.n_doppler + kb : -1;
+    const int key = ((unsigned)g < (unsigned)m.n_gates) ? g * m.n_doppler + kb : -1;
+    return (!GENERAL && (refine || wide)) ? kKeyDeferred : key;
 }
 
 // Squared off-nadir angle atan(rho / d_z)^2 in FP64 (series for small angles).
