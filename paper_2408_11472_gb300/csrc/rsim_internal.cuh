@@ -840,10 +840,6 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
     }
     const int next_link = __shfl_down_sync(kFull, link ? 1 : 0, 1);
     if (lane == 31 || !next_link) tails |= 1u << (J - 1);
-    // runs of out-of-window items (key -1) are not emitted
-#pragma unroll
-    for (int q = 0; q < J; ++q)
-        if (key[q] < 0) tails &= ~(1u << q);
     // emit the pending run tails, one per lane per round
     while (__any_sync(kFull, tails != 0u)) {
         if (tails) {
@@ -863,7 +859,7 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
                 vr += in_r;
                 vi += in_i;
             }
-            emit_cell(base, k, vr, vi);
+            if (k >= 0) emit_cell(base, k, vr, vi);  // runs out of the window are dropped
         }
     }
 }
