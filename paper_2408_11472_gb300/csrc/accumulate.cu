@@ -266,12 +266,24 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             int key[IT];
             float re[IT], im[IT];
             bool deferred = false;
+            if constexpr (!ANT && IT % 2 == 0) {
 #pragma unroll
-            for (int q = 0; q < IT; ++q) {
-                int f;
-                key[q] = eval_split<DOPPLER, false, false, ANT>(m, k, it[q], re[q], im[q], f);
-                deferred |= key[q] == kKeyDeferred;
+                for (int q = 0; q < IT; q += 2) {
+                    float2 r2, i2;
+                    eval_split_pair<DOPPLER>(m, k, pack_items(it[q], it[q + 1]), key[q], key[q + 1],
+                                             r2, i2);
+                    re[q] = r2.x; re[q + 1] = r2.y;
+                    im[q] = i2.x; im[q + 1] = i2.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < IT; ++q) {
+                    int f;
+                    key[q] = eval_split<DOPPLER, false, false, ANT>(m, k, it[q], re[q], im[q], f);
+                }
             }
+#pragma unroll
+            for (int q = 0; q < IT; ++q) deferred |= key[q] == kKeyDeferred;
             if (__any_sync(kFull, deferred)) {  // rare: queue the flagged items
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {

@@ -650,6 +650,94 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     return (!GENERAL && (refine || wide)) ? kKeyDeferred : key;
 }
 
+// Two scatterers (items 2p and 2p + 1 of a thread) as lanes of packed FP32 pairs.
+struct ItemF2 {
+    float2 lx0, ly0, z, vx, vy, vz, amp0, gam, beta;
+};
+
+__device__ __forceinline__ ItemF2 pack_items(const ItemF& a, const ItemF& b) {
+    ItemF2 r;
+    r.lx0 = make_float2(a.lx0, b.lx0);
+    r.ly0 = make_float2(a.ly0, b.ly0);
+    r.z = make_float2(a.z, b.z);
+    r.vx = make_float2(a.vx, b.vx);
+    r.vy = make_float2(a.vy, b.vy);
+    r.vz = make_float2(a.vz, b.vz);
+    r.amp0 = make_float2(a.amp0, b.amp0);
+    r.gam = make_float2(a.gam, b.gam);
+    r.beta = make_float2(a.beta, b.beta);
+    return r;
+}
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// eval_split<DOPPLER, GENERAL = false, DERIV = false, ANT = false> for two scatterers at
+// once on the paired FP32 instructions (fma / add / mul .f32x2: one issue slot for both).
+// Every pair operation rounds each lane as the scalar operation it replaces, and the
+// negations the pair forms cannot take as operand modifiers are exact rewrites
+// (fma(x, -1, y) = y - x, products with negated constants), so each lane's key, re and im
+// are bit-identical to the scalar evaluation's.
+template <bool DOPPLER>
+__device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k, const ItemF2& it,
+                                                int& key0, int& key1, float2& re, float2& im) {
+    const float2 one = f2(1.0f), neg1 = f2(-1.0f);
+    const float2 t2 = f2(k.t);
+    const float2 lx = __ffma2_rn(it.vx, t2, it.lx0);
+    const float2 ly = __ffma2_rn(it.vy, t2, it.ly0);
+    const float2 lz = __ffma2_rn(it.vz, t2, it.z);
+    // -u.l, with the signs carried by the constants (exact)
+    const float2 nul = __ffma2_rn(f2(-k.ux), lx, __ffma2_rn(f2(-k.uy), ly, __fmul2_rn(f2(-k.uz), lz)));
+    const float2 ll = __ffma2_rn(lx, lx, __ffma2_rn(ly, ly, __fmul2_rn(lz, lz)));
+    const float2 dR0 = __ffma2_rn(ll, f2(k.h), nul);
+    const float2 dR = __fmul2_rn(dR0, __ffma2_rn(dR0, f2(-k.h), one));
+    // gate (as eval_split)
+    const float2 gch = __ffma2_rn(dR, f2(m.inv_gw_f), f2(k.gfrac_h));
+    const float2 gr = __fadd2_rn(gch, f2(kRoundMagic));
+    const float2 gd = __ffma2_rn(__fadd2_rn(gr, f2(-kRoundMagic)), neg1, gch);
+    const int g0 = k.gint + (__float_as_int(gr.x) - __float_as_int(kRoundMagic));
+    const int g1 = k.gint + (__float_as_int(gr.y) - __float_as_int(kRoundMagic));
+    // amplitude
+    const float2 dx = __ffma2_rn(lx, neg1, f2(k.Dx));
+    const float2 dy = __ffma2_rn(ly, neg1, f2(k.Dy));
+    const float2 rho2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+    const float2 qb = __fmul2_rn(rho2, f2(k.kq));
+    const float2 T = __ffma2_rn(qb, __ffma2_rn(qb, __ffma2_rn(qb, f2(m.s2), f2(m.s1)), one),
+                                f2(k.l2kappa));
+    // -x_r = -dR / R_c; E = x_r (x_r c - 2c) + T = (-x_r)((-x_r) c + 2c) + T
+    const float2 nxr = __fmul2_rn(dR, f2(-k.invRc));
+    const float2 E = __ffma2_rn(nxr, __ffma2_rn(nxr, f2(kInvLn2F), f2(2.0f * kInvLn2F)), T);
+    const float2 a = __fmul2_rn(it.amp0, make_float2(ex2_approx(E.x), ex2_approx(E.y)));
+    // phase in cycles with p = dR chi_hi carried as -p (exact)
+    const float2 np = __fmul2_rn(dR, f2(-m.chi_hi));
+    const float2 perr = __ffma2_rn(dR, f2(m.chi_hi), np);
+    const float2 fr = __ffma2_rn(make_float2(rintf(np.x), rintf(np.y)), neg1, np);  // -(p - rint p)
+    const float2 s = __fadd2_rn(f2(k.psic), __ffma2_rn(dR, f2(m.chi_lo), perr));
+    const float2 arg = __fmul2_rn(f2(kTwoPiF), __ffma2_rn(fr, neg1, s));
+    float2 sn, cs;
+    __sincosf(arg.x, &sn.x, &cs.x);
+    __sincosf(arg.y, &sn.y, &cs.y);
+    re = __fmul2_rn(a, cs);
+    im = __fmul2_rn(__fmul2_rn(a, sn), neg1);
+    bool refine0 = fabsf(gd.x) > k.gthr, refine1 = fabsf(gd.y) > k.gthr;
+    int kb0 = 0, kb1 = 0;
+    if (DOPPLER) {
+        const float2 item = __ffma2_rn(f2(k.dtDx), it.vx, __ffma2_rn(f2(k.dtDy), it.vy,
+                              __ffma2_rn(f2(k.dtDz), it.vz, __ffma2_rn(t2, it.beta, it.gam))));
+        float2 b = __fmul2_rn(__fadd2_rn(__ffma2_rn(item, neg1, f2(k.K0hi)), f2(k.K0lo)), f2(k.kbin));
+        b = __ffma2_rn(b, nxr, b);
+        const float2 bm = __fadd2_rn(b, f2(kRoundMagic));
+        const float2 bd = __ffma2_rn(__fadd2_rn(bm, f2(-kRoundMagic)), neg1, b);
+        kb0 = __float_as_int(bm.x) & (m.n_doppler - 1);
+        kb1 = __float_as_int(bm.y) & (m.n_doppler - 1);
+        refine0 |= fabsf(bd.x) > fmaf(-fabsf(b.x), kEpsSlope, 0.5f - kBinEps);
+        refine1 |= fabsf(bd.y) > fmaf(-fabsf(b.y), kEpsSlope, 0.5f - kBinEps);
+    }
+    const int c0 = ((unsigned)g0 < (unsigned)m.n_gates) ? g0 * m.n_doppler + kb0 : -1;
+    const int c1 = ((unsigned)g1 < (unsigned)m.n_gates) ? g1 * m.n_doppler + kb1 : -1;
+    key0 = (refine0 || qb.x < m.qb_wide) ? kKeyDeferred : c0;
+    key1 = (refine1 || qb.y < m.qb_wide) ? kKeyDeferred : c1;
+}
+
 // Squared off-nadir angle atan(rho / d_z)^2 in FP64 (series for small angles).
 __device__ __forceinline__ double theta2_d(double rho2, double dz) {
     const double q2 = rho2 / (dz * dz);
