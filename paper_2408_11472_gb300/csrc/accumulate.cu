@@ -266,11 +266,11 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             int key[IT];
             float re[IT], im[IT];
             bool deferred = false;
-            if constexpr (!ANT && IT % 2 == 0) {
+            if constexpr (IT % 2 == 0) {
 #pragma unroll
                 for (int q = 0; q < IT; q += 2) {
                     float2 r2, i2;
-                    eval_split_pair<DOPPLER>(m, k, pack_items(it[q], it[q + 1]), key[q], key[q + 1],
+                    eval_split_pair<DOPPLER, ANT>(m, k, pack_items(it[q], it[q + 1]), key[q], key[q + 1],
                                              r2, i2);
                     re[q] = r2.x; re[q + 1] = r2.y;
                     im[q] = i2.x; im[q + 1] = i2.y;

@@ -671,13 +671,14 @@ __device__ __forceinline__ ItemF2 pack_items(const ItemF& a, const ItemF& b) {
 
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 
-// eval_split<DOPPLER, GENERAL = false, DERIV = false, ANT = false> for two scatterers at
-// once on the paired FP32 instructions (fma / add / mul .f32x2: one issue slot for both).
+// eval_split<DOPPLER, GENERAL = false, DERIV = false, ANT> for two scatterers at once on
+// the paired FP32 instructions (fma / add / mul .f32x2: one issue slot for both); the
+// tabulated pattern's look-ups run per lane.
 // Every pair operation rounds each lane as the scalar operation it replaces, and the
 // negations the pair forms cannot take as operand modifiers are exact rewrites
 // (fma(x, -1, y) = y - x, products with negated constants), so each lane's key, re and im
 // are bit-identical to the scalar evaluation's.
-template <bool DOPPLER>
+template <bool DOPPLER, bool ANT>
 __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k, const ItemF2& it,
                                                 int& key0, int& key1, float2& re, float2& im) {
     const float2 one = f2(1.0f), neg1 = f2(-1.0f);
@@ -696,13 +697,18 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
     const float2 gd = __ffma2_rn(__fadd2_rn(gr, f2(-kRoundMagic)), neg1, gch);
     const int g0 = k.gint + (__float_as_int(gr.x) - __float_as_int(kRoundMagic));
     const int g1 = k.gint + (__float_as_int(gr.y) - __float_as_int(kRoundMagic));
-    // amplitude
-    const float2 dx = __ffma2_rn(lx, neg1, f2(k.Dx));
-    const float2 dy = __ffma2_rn(ly, neg1, f2(k.Dy));
-    const float2 rho2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-    const float2 qb = __fmul2_rn(rho2, f2(k.kq));
-    const float2 T = __ffma2_rn(qb, __ffma2_rn(qb, __ffma2_rn(qb, f2(m.s2), f2(m.s1)), one),
-                                f2(k.l2kappa));
+    // amplitude (the tabulated pattern multiplies C below)
+    float2 T = f2(k.l2kappa), qb = f2(0.0f), ndx, ndy;
+    if (!ANT) {
+        const float2 dx = __ffma2_rn(lx, neg1, f2(k.Dx));
+        const float2 dy = __ffma2_rn(ly, neg1, f2(k.Dy));
+        const float2 rho2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        qb = __fmul2_rn(rho2, f2(k.kq));
+        T = __ffma2_rn(qb, __ffma2_rn(qb, __ffma2_rn(qb, f2(m.s2), f2(m.s1)), one), T);
+    } else {
+        ndx = __ffma2_rn(f2(k.Dx), neg1, lx);   // -d_x = l_x - D_x (exact negation)
+        ndy = __ffma2_rn(f2(k.Dy), neg1, ly);
+    }
     // -x_r = -dR / R_c; E = x_r (x_r c - 2c) + T = (-x_r)((-x_r) c + 2c) + T
     const float2 nxr = __fmul2_rn(dR, f2(-k.invRc));
     const float2 E = __ffma2_rn(nxr, __ffma2_rn(nxr, f2(kInvLn2F), f2(2.0f * kInvLn2F)), T);
@@ -716,8 +722,33 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
     float2 sn, cs;
     __sincosf(arg.x, &sn.x, &cs.x);
     __sincosf(arg.y, &sn.y, &cs.y);
-    re = __fmul2_rn(a, cs);
-    im = __fmul2_rn(__fmul2_rn(a, sn), neg1);
+    float2 pat_bins = f2(0.0f);
+    if (!ANT) {
+        re = __fmul2_rn(a, cs);
+        im = __fmul2_rn(__fmul2_rn(a, sn), neg1);
+    } else {
+        // (u, v) = -(d_x, d_y) / R with 1 / R = (1 / R_c)(1 - x_r), as eval_split
+        const float2 invR = __fmul2_rn(f2(k.invRc), __fadd2_rn(one, nxr));
+        const float2 pu = __fmul2_rn(ndx, invR), pv = __fmul2_rn(ndy, invR);
+        PatCellF c0, c1;
+        const float2 G0 = pattern_cell_f(m, pu.x, pv.x, c0);
+        const float2 G1 = pattern_cell_f(m, pu.y, pv.y, c1);
+        if (DOPPLER) {
+            // -(d + e) at the second pulse, e = e_p - v dt carried as -e (exact)
+            const float2 nex = __ffma2_rn(it.vx, f2(m.dt_f), f2(-m.ep[0]));
+            const float2 ney = __ffma2_rn(it.vy, f2(m.dt_f), f2(-m.ep[1]));
+            const float2 u2 = __fmul2_rn(__fadd2_rn(ndx, nex), invR);
+            const float2 v2 = __fmul2_rn(__fadd2_rn(ndy, ney), invR);
+            const float2 H0 = pattern_near_f(m, u2.x, v2.x, c0);
+            const float2 H1 = pattern_near_f(m, u2.y, v2.y, c1);
+            pat_bins.x = small_arg_f(fmaf(H0.y, G0.x, -H0.x * G0.y), fmaf(H0.x, G0.x, H0.y * G0.y)) *
+                         m.nd_over_2pi_f;
+            pat_bins.y = small_arg_f(fmaf(H1.y, G1.x, -H1.x * G1.y), fmaf(H1.x, G1.x, H1.y * G1.y)) *
+                         m.nd_over_2pi_f;
+        }
+        re = make_float2(a.x * fmaf(G0.x, cs.x, G0.y * sn.x), a.y * fmaf(G1.x, cs.y, G1.y * sn.y));
+        im = make_float2(a.x * fmaf(G0.y, cs.x, -G0.x * sn.x), a.y * fmaf(G1.y, cs.y, -G1.x * sn.y));
+    }
     bool refine0 = fabsf(gd.x) > k.gthr, refine1 = fabsf(gd.y) > k.gthr;
     int kb0 = 0, kb1 = 0;
     if (DOPPLER) {
@@ -725,6 +756,7 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
                               __ffma2_rn(f2(k.dtDz), it.vz, __ffma2_rn(t2, it.beta, it.gam))));
         float2 b = __fmul2_rn(__fadd2_rn(__ffma2_rn(item, neg1, f2(k.K0hi)), f2(k.K0lo)), f2(k.kbin));
         b = __ffma2_rn(b, nxr, b);
+        if (ANT) b = __fadd2_rn(b, pat_bins);
         const float2 bm = __fadd2_rn(b, f2(kRoundMagic));
         const float2 bd = __ffma2_rn(__fadd2_rn(bm, f2(-kRoundMagic)), neg1, b);
         kb0 = __float_as_int(bm.x) & (m.n_doppler - 1);
@@ -734,8 +766,8 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
     }
     const int c0 = ((unsigned)g0 < (unsigned)m.n_gates) ? g0 * m.n_doppler + kb0 : -1;
     const int c1 = ((unsigned)g1 < (unsigned)m.n_gates) ? g1 * m.n_doppler + kb1 : -1;
-    key0 = (refine0 || qb.x < m.qb_wide) ? kKeyDeferred : c0;
-    key1 = (refine1 || qb.y < m.qb_wide) ? kKeyDeferred : c1;
+    key0 = (refine0 || (!ANT && qb.x < m.qb_wide)) ? kKeyDeferred : c0;
+    key1 = (refine1 || (!ANT && qb.y < m.qb_wide)) ? kKeyDeferred : c1;
 }
 
 // Squared off-nadir angle atan(rho / d_z)^2 in FP64 (series for small angles).
