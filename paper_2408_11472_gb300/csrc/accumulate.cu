@@ -234,12 +234,16 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
     int* const queue = s_queue[threadIdx.x >> 5];
     float cx, cy;
     chunk_ref(sc, cx_.chunk0, cx, cy);
-    ItemF it[IT];
+    static_assert(IT % 2 == 0, "items are evaluated in pairs");
+    ItemF2 it2[IT / 2];  // the thread's scatterers, paired for the .f32x2 evaluation
     {
         const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * IT;
         RawT<IT> r;
         load_raw(sc, base, r);
+        ItemF it[IT];
         items_split(m, r, cx, cy, cx_.area, it);
+#pragma unroll
+        for (int p = 0; p < IT / 2; ++p) it2[p] = pack_items(it[2 * p], it[2 * p + 1]);
         chunk_bounds(r, cx, cy, base, sc.n, s_red);
     }
     const int cells = m.n_gates * m.n_doppler;
@@ -266,21 +270,12 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             int key[IT];
             float re[IT], im[IT];
             bool deferred = false;
-            if constexpr (IT % 2 == 0) {
 #pragma unroll
-                for (int q = 0; q < IT; q += 2) {
-                    float2 r2, i2;
-                    eval_split_pair<DOPPLER, ANT>(m, k, pack_items(it[q], it[q + 1]), key[q], key[q + 1],
-                                             r2, i2);
-                    re[q] = r2.x; re[q + 1] = r2.y;
-                    im[q] = i2.x; im[q + 1] = i2.y;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < IT; ++q) {
-                    int f;
-                    key[q] = eval_split<DOPPLER, false, false, ANT>(m, k, it[q], re[q], im[q], f);
-                }
+            for (int q = 0; q < IT; q += 2) {
+                float2 r2, i2;
+                eval_split_pair<DOPPLER, ANT>(m, k, it2[q / 2], key[q], key[q + 1], r2, i2);
+                re[q] = r2.x; re[q + 1] = r2.y;
+                im[q] = i2.x; im[q + 1] = i2.y;
             }
 #pragma unroll
             for (int q = 0; q < IT; ++q) deferred |= key[q] == kKeyDeferred;

@@ -30,7 +30,7 @@ namespace rsim {
 #define RSIM_MIN_BLOCKS_ANT 2
 #endif
 constexpr int kThreads = RSIM_THREADS;        // summation CTA size
-constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (1, 2, 4, 8)
+constexpr int kItems = RSIM_ITEMS;            // consecutive scatterers per thread (2, 4, 8)
 constexpr int kMinBlocks = RSIM_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
 constexpr int kChunk = kThreads * kItems;     // scatterers sharing one FP64 reference point
 // The split summation kernels with a tabulated antenna pattern hold more per item, so they
@@ -40,7 +40,7 @@ constexpr int kMinBlocksAnt = RSIM_MIN_BLOCKS_ANT;
 __host__ __device__ constexpr int split_items(bool ant) { return ant ? kItemsAnt : kItems; }
 constexpr int kTab = kThreads < 128 ? kThreads : 128;  // samples per block of reference constants
 constexpr double kFixScale = 4294967296.0;    // fixed point: value = q * 2^-32
-static_assert(kItems == 1 || kItems == 2 || kItems == 4 || kItems == 8, "items per thread");
+static_assert(kItems == 2 || kItems == 4 || kItems == 8, "items per thread");
 static_assert(kChunk % kItemsAnt == 0 && (kChunk / kItemsAnt) % 32 == 0 && kChunk / kItemsAnt <= 1024,
               "antenna CTA shape");
 static_assert(kThreads >= 64 && kThreads >= kTab && kThreads % 32 == 0, "CTA size");
@@ -965,16 +965,23 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
         if (tails) {
             const int q = __ffs(tails) - 1;
             tails &= tails - 1u;
-            int k = key[0];
-            T vr = sr[0], vi = si[0];
+            // binary selection by the bits of q
+            int kk[J];
+            T rr[J], ii[J];
 #pragma unroll
-            for (int j = 1; j < J; ++j) {
-                if (q == j) {
-                    k = key[j];
-                    vr = sr[j];
-                    vi = si[j];
+            for (int j = 0; j < J; ++j) { kk[j] = key[j]; rr[j] = sr[j]; ii[j] = si[j]; }
+#pragma unroll
+            for (int w = 1; w < J; w <<= 1) {
+                const bool bit = (q & w) != 0;
+#pragma unroll
+                for (int j = 0; j < J; j += 2 * w) {
+                    kk[j] = bit ? kk[j + w] : kk[j];
+                    rr[j] = bit ? rr[j + w] : rr[j];
+                    ii[j] = bit ? ii[j + w] : ii[j];
                 }
             }
+            const int k = kk[0];
+            T vr = rr[0], vi = ii[0];
             if (q <= first_end) {  // the lane's first run: add the carry from the left
                 vr += in_r;
                 vi += in_i;
