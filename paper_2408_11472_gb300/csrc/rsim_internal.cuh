@@ -88,8 +88,8 @@ struct Model {
 // interpolant dG/du, dG/dv.  FP32 (split path) and FP64 versions.
 __device__ __forceinline__ float2 pattern_f(const Model& m, float u, float v,
                                             float2* gu = nullptr, float2* gv = nullptr) {
-    const float fu = (u - m.ant_u0_f) * m.ant_idu_f;
-    const float fv = (v - m.ant_v0_f) * m.ant_idv_f;
+    const float fu = __fmul_rn(u - m.ant_u0_f, m.ant_idu_f);  // not contracted into tu below
+    const float fv = __fmul_rn(v - m.ant_v0_f, m.ant_idv_f);
     const float iu = floorf(fu), iv = floorf(fv);
     if (!(iu >= 0.0f && iu <= (float)(m.ant_nu - 2) && iv >= 0.0f && iv <= (float)(m.ant_nv - 2))) {
         if (gu) *gu = make_float2(0.f, 0.f);
@@ -120,8 +120,8 @@ struct PatCellF {
 };
 
 __device__ __forceinline__ float2 pattern_cell_f(const Model& m, float u, float v, PatCellF& c) {
-    const float fu = (u - m.ant_u0_f) * m.ant_idu_f;
-    const float fv = (v - m.ant_v0_f) * m.ant_idv_f;
+    const float fu = __fmul_rn(u - m.ant_u0_f, m.ant_idu_f);  // not contracted into tu below
+    const float fv = __fmul_rn(v - m.ant_v0_f, m.ant_idv_f);
     c.iu = floorf(fu);
     c.iv = floorf(fv);
     if (!(c.iu >= 0.0f && c.iu <= (float)(m.ant_nu - 2) && c.iv >= 0.0f &&
@@ -144,8 +144,8 @@ __device__ __forceinline__ float2 pattern_cell_f(const Model& m, float u, float 
 // pattern_f would load).
 __device__ __forceinline__ float2 pattern_near_f(const Model& m, float u, float v,
                                                  const PatCellF& c) {
-    const float fu = (u - m.ant_u0_f) * m.ant_idu_f;
-    const float fv = (v - m.ant_v0_f) * m.ant_idv_f;
+    const float fu = __fmul_rn(u - m.ant_u0_f, m.ant_idu_f);  // not contracted into tu below
+    const float fv = __fmul_rn(v - m.ant_v0_f, m.ant_idv_f);
     const float iu = floorf(fu), iv = floorf(fv);
     if (iu != c.iu || iv != c.iv) return pattern_f(m, u, v);
     const float tu = fu - iu, tv = fv - iv;
@@ -551,11 +551,13 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
             }
         }
     }
-    const float xr = dR * k.invRc;
+    // products that later meet an addition are rounded on their own (__fmul_rn is never
+    // contracted into an FMA), as in the paired evaluation
+    const float xr = __fmul_rn(dR, k.invRc);
     const float E = fmaf(xr, fmaf(xr, kInvLn2F, -2.0f * kInvLn2F), T);
     const float a = it.amp0 * ex2_approx(E);
     // phase in cycles: psi_c + dR 2/lambda (2/lambda as hi + lo, the product error-free)
-    const float p = dR * m.chi_hi;
+    const float p = __fmul_rn(dR, m.chi_hi);
     const float perr = fmaf(dR, m.chi_hi, -p);
     // |f| <= 1 cycle: the hardware sine and cosine take their arguments modulo one turn
     const float f = (p - rintf(p)) + (k.psic + fmaf(dR, m.chi_lo, perr));
@@ -567,8 +569,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     if (ANT) {
         // C = a G(u, v) e^{-j 2 pi f}, (u, v) = -(d_x, d_y) / R, 1 / R = (1 / R_c)(1 - dR / R_c)
         const float invR = k.invRc * (1.0f - xr);
-        pu = -dx * invR;
-        pv = -dy * invR;
+        pu = __fmul_rn(-dx, invR);  // rounded before the table look-up subtracts u0
+        pv = __fmul_rn(-dy, invR);
         if (DERIV) G = pattern_f(m, pu, pv, &gu, &gv);
         else G = pattern_cell_f(m, pu, pv, cell);
         if (DOPPLER) {
@@ -576,10 +578,10 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
             // (Algorithm 1 takes it from arg(conj(C2) C1)); d at the second pulse is
             // d + e_p - v dt
             const float ex = fmaf(-it.vx, m.dt_f, m.ep[0]), ey = fmaf(-it.vy, m.dt_f, m.ep[1]);
-            const float u2 = -(dx + ex) * invR, v2 = -(dy + ey) * invR;
+            const float u2 = __fmul_rn(-(dx + ex), invR), v2 = __fmul_rn(-(dy + ey), invR);
             const float2 G2 = DERIV ? pattern_f(m, u2, v2) : pattern_near_f(m, u2, v2, cell);
             const float pr = fmaf(G2.x, G.x, G2.y * G.y), pi = fmaf(G2.y, G.x, -G2.x * G.y);
-            pat_bins = small_arg_f(pi, pr) * m.nd_over_2pi_f;
+            pat_bins = __fmul_rn(small_arg_f(pi, pr), m.nd_over_2pi_f);
         }
         re = a * fmaf(G.x, cs, G.y * sn);
         im = a * fmaf(G.y, cs, -G.x * sn);
@@ -741,10 +743,10 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
             const float2 v2 = __fmul2_rn(__fadd2_rn(ndy, ney), invR);
             const float2 H0 = pattern_near_f(m, u2.x, v2.x, c0);
             const float2 H1 = pattern_near_f(m, u2.y, v2.y, c1);
-            pat_bins.x = small_arg_f(fmaf(H0.y, G0.x, -H0.x * G0.y), fmaf(H0.x, G0.x, H0.y * G0.y)) *
-                         m.nd_over_2pi_f;
-            pat_bins.y = small_arg_f(fmaf(H1.y, G1.x, -H1.x * G1.y), fmaf(H1.x, G1.x, H1.y * G1.y)) *
-                         m.nd_over_2pi_f;
+            pat_bins.x = __fmul_rn(small_arg_f(fmaf(H0.y, G0.x, -H0.x * G0.y),
+                                               fmaf(H0.x, G0.x, H0.y * G0.y)), m.nd_over_2pi_f);
+            pat_bins.y = __fmul_rn(small_arg_f(fmaf(H1.y, G1.x, -H1.x * G1.y),
+                                               fmaf(H1.x, G1.x, H1.y * G1.y)), m.nd_over_2pi_f);
         }
         re = make_float2(a.x * fmaf(G0.x, cs.x, G0.y * sn.x), a.y * fmaf(G1.x, cs.y, G1.y * sn.y));
         im = make_float2(a.x * fmaf(G0.y, cs.x, -G0.x * sn.x), a.y * fmaf(G1.y, cs.y, -G1.x * sn.y));
