@@ -51,8 +51,8 @@
  *     per-thread message for the last failure.  Nothing throws across the ABI.
  *   - Scatterer order: any order is accepted; RSIM_SPLIT is most accurate when
  *     consecutive scatterers are spatially close (e.g. a row-major grid),
- *     because each block of 512 consecutive scatterers shares one FP64
- *     reference point.
+ *     because each block of rsim_block_scatterers() (1024) consecutive
+ *     scatterers shares one FP64 reference point.
  *   - Accumulation is exact: contributions are summed in 64-bit fixed point
  *     (2^-32 resolution, |sum| < 2^31 per cell), so results are bitwise
  *     reproducible run to run regardless of scheduling.

@@ -443,8 +443,9 @@ class HostStreamer:
     overlapped with the scatterer pass.  Device buffers come in two sets, so the copies of
     one run overlap the summation of the previous run: for a stream of runs one block
     (``chunks=1``, the default) hides the copies entirely.  For the latency of a single run
-    the set can be cut into ``chunks`` blocks of whole 512-scatterer blocks ("waves": one
-    block per full wave of CTAs), block i+1 copied while block i is summed (the summation
+    the set can be cut into ``chunks`` blocks of whole summation blocks (1024 scatterers,
+    ``rsim_block_scatterers()``; "waves": one block per full wave of CTAs), block i+1
+    copied while block i is summed (the summation
     adds, so the blocks' sums make the set's; every scatterer keeps its FP64 reference
     point).  All blocks add into one exact workspace, so the spectra are bit-identical to a
     single call on the whole set.  Buffers and workspace are allocated once."""
