@@ -199,5 +199,160 @@ __device__ void stockham4_1buf(T* a, int rows, int N, int L, const T* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Mixed-radix Stockham passes held in registers: radix-16 passes while at least four
+// bits of the length remain, then one radix-8, 4 or 2 pass (2048 = 16 x 16 x 8: three
+// passes over shared memory instead of six radix-4 ones).  Each pass is the radix-R
+// Stockham step (stride s = product of the previous radices, m = N / (R s)):
+//     y[q + s (R p + j)] = w_N^{j p s} sum_k x[q + s (p + k m)] w_R^{j k},
+// with w_M = exp(sign j 2 pi / M); a thread reads its R inputs into registers, the block
+// waits, then each thread writes its outputs in place (one buffer).  The rows sit in shared
+// memory with one spare element after every 16 (index pad16), which puts the strided
+// accesses of every pass in distinct banks.  Row r starts at r * padded_len(N).
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+
+// exp(sign j 2 pi m / 16) for the m the radix-16 and radix-8 steps use
+__device__ __forceinline__ float2 w16(int m, float sign) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f;  // cos, sin pi/8
+    constexpr float h = 0.70710678118654752f;                                // sqrt(1/2)
+    float c, s;
+    switch (m) {
+        case 1: c = c1; s = s1; break;
+        case 2: c = h; s = h; break;
+        case 3: c = s1; s = c1; break;
+        case 4: c = 0.0f; s = 1.0f; break;
+        case 6: c = -h; s = h; break;
+        case 9: c = -c1; s = -s1; break;
+        default: c = 1.0f; s = 0.0f; break;
+    }
+    return make_float2(c, sign * s);
+}
+
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3, float sign) {
+    const float2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), d = csub(x1, x3);
+    const float2 t3 = make_float2(-sign * d.y, sign * d.x);  // sign j (x1 - x3)
+    x0 = cadd(t0, t2);
+    x1 = cadd(t1, t3);
+    x2 = csub(t0, t2);
+    x3 = csub(t1, t3);
+}
+
+// In-register DFTs, natural order in and out.  16 = 4 x 4 (n = 4 n1 + n2, k = k1 + 4 k2):
+// 4-point DFTs over n1, twiddles w_16^{n2 k1}, 4-point DFTs over n2.  8 = 4 x 2 likewise.
+template <int R> __device__ __forceinline__ void dft_reg(float2 (&x)[R], float sign);
+
+template <> __device__ __forceinline__ void dft_reg<16>(float2 (&x)[16], float sign) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4(x[n2], x[4 + n2], x[8 + n2], x[12 + n2], sign);
+    // x[4 k1 + n2] now holds the k1-th output of the n2-th transform
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+        for (int n2 = 1; n2 < 4; ++n2) x[4 * k1 + n2] = cmul(x[4 * k1 + n2], w16(n2 * k1, sign));
+    float2 y[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 a0 = x[4 * k1], a1 = x[4 * k1 + 1], a2 = x[4 * k1 + 2], a3 = x[4 * k1 + 3];
+        dft4(a0, a1, a2, a3, sign);
+        y[k1] = a0;
+        y[k1 + 4] = a1;
+        y[k1 + 8] = a2;
+        y[k1 + 12] = a3;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = y[j];
+}
+
+template <> __device__ __forceinline__ void dft_reg<8>(float2 (&x)[8], float sign) {
+    dft4(x[0], x[2], x[4], x[6], sign);
+    dft4(x[1], x[3], x[5], x[7], sign);
+    // x[2 k1 + n2]: k1-th output of the n2-th transform; w_8^{k1} on the odd one
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) x[2 * k1 + 1] = cmul(x[2 * k1 + 1], w16(2 * k1, sign));
+    float2 y[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        y[k1] = cadd(x[2 * k1], x[2 * k1 + 1]);
+        y[k1 + 4] = csub(x[2 * k1], x[2 * k1 + 1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = y[j];
+}
+
+template <> __device__ __forceinline__ void dft_reg<4>(float2 (&x)[4], float sign) {
+    dft4(x[0], x[1], x[2], x[3], sign);
+}
+
+template <> __device__ __forceinline__ void dft_reg<2>(float2 (&x)[2], float) {
+    const float2 t = x[0];
+    x[0] = cadd(t, x[1]);
+    x[1] = csub(t, x[1]);
+}
+
+// One pass of radix R over `rows` padded rows; U = work units per thread (the caller
+// guarantees rows * N / R <= U * blockDim.x).
+template <int R, int U>
+__device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, int log2N, int log2s,
+                                                  const float2* __restrict__ tw, float sign) {
+    constexpr int log2R = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
+    const int log2nb = log2N - log2R;           // butterflies per row: N / R
+    const int nb = 1 << log2nb;
+    const int s = 1 << log2s;
+    const int m = nb >> log2s;                  // N / (R s)
+    const int total = rows << log2nb;
+    const int NP = padded_len(N);
+    float2 x[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = threadIdx.x + u * blockDim.x;
+        if (idx < total) {
+            const int bi = idx & (nb - 1);
+            const int p = bi >> log2s, q = bi & (s - 1);
+            const float2* ar = a + (idx >> log2nb) * NP;
+#pragma unroll
+            for (int k = 0; k < R; ++k) x[u][k] = ar[pad16(q + s * (p + k * m))];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = threadIdx.x + u * blockDim.x;
+        if (idx < total) {
+            const int bi = idx & (nb - 1);
+            const int p = bi >> log2s, q = bi & (s - 1);
+            float2* ar = a + (idx >> log2nb) * NP;
+            dft_reg<R>(x[u], sign);
+            const int e = p * s;
+            const int o = q + s * (R * p);
+            ar[pad16(o)] = x[u][0];
+#pragma unroll
+            for (int j = 1; j < R; ++j) ar[pad16(o + s * j)] = cmul(x[u][j], tw_full(tw, j * e, N));
+        }
+    }
+    __syncthreads();
+}
+
+// The whole transform of `rows` padded rows of N = 2^log2N points (N >= 2).  MAXE bounds
+// the elements per thread: rows * N <= MAXE * blockDim.x (MAXE a multiple of 16).
+// tw[n] = exp(sign j 2 pi n / N) for n < N / 2.  Result in place, natural order.
+template <int MAXE>
+__device__ void fft_rows_reg(float2* a, int rows, int N, int log2N, const float2* __restrict__ tw,
+                             float sign) {
+    static_assert(MAXE % 16 == 0, "elements per thread");
+    int log2s = 0;
+    while (log2N - log2s >= 4) {
+        stockham_pass_reg<16, MAXE / 16>(a, rows, N, log2N, log2s, tw, sign);
+        log2s += 4;
+    }
+    switch (log2N - log2s) {
+        case 3: stockham_pass_reg<8, MAXE / 8>(a, rows, N, log2N, log2s, tw, sign); break;
+        case 2: stockham_pass_reg<4, MAXE / 4>(a, rows, N, log2N, log2s, tw, sign); break;
+        case 1: stockham_pass_reg<2, MAXE / 2>(a, rows, N, log2N, log2s, tw, sign); break;
+        default: break;
+    }
+}
+
 }  // namespace fft
 }  // namespace rsim

@@ -13,8 +13,8 @@
 //                  phase e^{-j omega t}, and transforms them along x (shared memory);
 //   columns pass : one CTA per block of columns (32 bytes of every row) transforms along y
 //                  and writes the fields.
-// Both passes use the single-buffer radix-4 transform (one shared-memory copy of the data,
-// three CTAs per SM).
+// Both passes use the register mixed-radix transform (radix-16 passes, one shared-memory
+// copy of the data in a padded layout: three passes over shared memory for L = 2048).
 // omega / (2 pi) is tabulated once per spectrum (FP64, stored as hi + lo floats) so that
 // the phase omega t stays accurate to ~1e-7 cycles for t of hours.
 #include "rsim_internal.cuh"
@@ -44,17 +44,22 @@ __global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega) {
     }
 }
 
-__global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2* __restrict__ coef,
+constexpr int kRowsThreads = 512;   // two rows of at most 4096 points: 16 per thread
+constexpr int kColsThreads = 512;   // at most 8192 points: 16 per thread
+
+__global__ void __launch_bounds__(kRowsThreads) surf_rows_kernel(SurfArgs a, const float2* __restrict__ coef,
                                                         const float2* __restrict__ omega,
                                                         float2* __restrict__ tmp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = a.L;
+    const int L = a.L, NP = padded_len(L);
     float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L)
     float2* buf0 = tw + (L >> 1);
     const int iy = blockIdx.x;
     const int iyn = (L - iy) & (L - 1);                     // row of -k
     for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
     const float ky = (float)wave_number(iy, L, a.dk);
+    // unrolled so that several iterations' global loads are in flight per thread
+#pragma unroll 4
     for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
         const int ixn = (L - ix) & (L - 1);
         const float kx = (float)wave_number(ix, L, a.dk);
@@ -86,41 +91,43 @@ __global__ void __launch_bounds__(512) surf_rows_kernel(SurfArgs a, const float2
                                       0.5f * om * fmaf(ux, F1.y, -uxn * F2.y));
         const float2 hy = make_float2(0.5f * om * fmaf(uy, F1.x, uyn * F2.x),
                                       0.5f * om * fmaf(uy, F1.y, -uyn * F2.y));
-        buf0[ix] = make_float2(he.x - hz.y, he.y + hz.x);   // H_eta + j H_vz
-        buf0[L + ix] = make_float2(hx.x - hy.y, hx.y + hy.x); // H_vx + j H_vy
+        buf0[pad16(ix)] = make_float2(he.x - hz.y, he.y + hz.x);       // H_eta + j H_vz
+        buf0[NP + pad16(ix)] = make_float2(hx.x - hy.y, hx.y + hy.x);  // H_vx + j H_vy
     }
     __syncthreads();
-    stockham4_1buf<float2, 4>(buf0, 2, L, a.log2L, tw, 1);   // 2 L / 4 <= 4 x 512
-    const float2* res = buf0;
+    fft_rows_reg<16>(buf0, 2, L, a.log2L, tw, 1.0f);   // 2 L <= 16 x 512
+#pragma unroll 4
     for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
-        tmp[(int64_t)iy * L + ix] = res[ix];
-        tmp[(int64_t)L * L + (int64_t)iy * L + ix] = res[L + ix];
+        tmp[(int64_t)iy * L + ix] = buf0[pad16(ix)];
+        tmp[(int64_t)L * L + (int64_t)iy * L + ix] = buf0[NP + pad16(ix)];
     }
 }
 
-__global__ void __launch_bounds__(512) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
+__global__ void __launch_bounds__(kColsThreads) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
                                                         float* __restrict__ z, float* __restrict__ vx,
                                                         float* __restrict__ vy, float* __restrict__ vz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = a.L, C = a.cols;
+    const int L = a.L, C = a.cols, NP = padded_len(L);
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* buf0 = tw + (L >> 1);
     const int ix0 = blockIdx.x * C;
     const int pair = blockIdx.y;
     const float2* src = tmp + (int64_t)pair * L * L;
     for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
         const int iy = idx / C, c = idx - iy * C;
-        buf0[c * L + iy] = __ldg(src + (int64_t)iy * L + ix0 + c);
+        buf0[c * NP + pad16(iy)] = __ldg(src + (int64_t)iy * L + ix0 + c);
     }
     __syncthreads();
-    stockham4_1buf<float2, 4>(buf0, C, L, a.log2L, tw, 1);   // C L / 4 <= 4 x 512
+    fft_rows_reg<16>(buf0, C, L, a.log2L, tw, 1.0f);   // C L <= 16 x 512
     const float2* res = buf0;
     float* fa = pair == 0 ? z : vx;
     float* fb = pair == 0 ? vz : vy;
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
         const int iy = idx / C, c = idx - iy * C;
-        const float2 v = res[c * L + iy];
+        const float2 v = res[c * NP + pad16(iy)];
         const int64_t o = (int64_t)iy * L + ix0 + c;
         fa[o] = v.x * a.scale_over_L2;
         fb[o] = v.y * a.scale_over_L2;
@@ -129,9 +136,11 @@ __global__ void __launch_bounds__(512) surf_cols_kernel(SurfArgs a, const float2
 
 }  // namespace
 
-size_t surf_rows_smem(int L) { return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)L); }
+size_t surf_rows_smem(int L) {
+    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)padded_len(L));
+}
 size_t surf_cols_smem(int L, int cols) {
-    return sizeof(float2) * ((size_t)(L / 2) + (size_t)cols * L);
+    return sizeof(float2) * ((size_t)(L / 2) + (size_t)cols * padded_len(L));
 }
 
 cudaError_t launch_surf_prepare(const SurfArgs& a, float2* omega, int n_sms, cudaStream_t stream) {
@@ -154,9 +163,9 @@ cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const float2* om
         (e = cudaFuncSetAttribute(surf_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)s2)) != cudaSuccess)
         return e;
-    surf_rows_kernel<<<(unsigned)a.L, 512, s1, stream>>>(a, static_cast<const float2*>(coef), omega, tmp);
+    surf_rows_kernel<<<(unsigned)a.L, kRowsThreads, s1, stream>>>(a, static_cast<const float2*>(coef), omega, tmp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), 512, s2, stream>>>(a, tmp, z, vx, vy, vz);
+    surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), kColsThreads, s2, stream>>>(a, tmp, z, vx, vy, vz);
     return cudaGetLastError();
 }
 
