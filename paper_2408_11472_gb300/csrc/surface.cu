@@ -31,6 +31,16 @@ __device__ __forceinline__ double wave_number(int i, int L, double dk) {
     return (double)(i < L / 2 ? i : i - L) * dk;      // 2 pi fftfreq(L, spacing)[i]
 }
 
+// Asynchronous global -> shared copies (cp.async, 8 bytes; both addresses 8-byte aligned).
+__device__ __forceinline__ void cp_async8(float2* smem_dst, const float2* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                 :: "r"(d), "l"((unsigned long long)__cvta_generic_to_global(gmem_src)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
 // omega / (2 pi) as hi + lo floats for every grid point.
 __global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega) {
     const int64_t n = (int64_t)a.L * a.L;
@@ -54,19 +64,29 @@ __global__ void __launch_bounds__(kRowsThreads) surf_rows_kernel(SurfArgs a, con
     const int L = a.L, NP = padded_len(L);
     float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L)
     float2* buf0 = tw + (L >> 1);
+    float2* sA = buf0 + 2 * NP;    // A(k) on row iy, A on row -iy, omega / 2 pi on row iy
+    float2* sB = sA + L;
+    float2* sW = sB + L;
     const int iy = blockIdx.x;
     const int iyn = (L - iy) & (L - 1);                     // row of -k
+    // the three input rows are copied asynchronously, all in flight at once
+    for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
+        cp_async8(sA + ix, coef + (int64_t)iy * L + ix);
+        cp_async8(sB + ix, coef + (int64_t)iyn * L + ix);
+        cp_async8(sW + ix, omega + (int64_t)iy * L + ix);
+    }
+    cp_async_commit();
     for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
     const float ky = (float)wave_number(iy, L, a.dk);
-    // unrolled so that several iterations' global loads are in flight per thread
-#pragma unroll 4
+    cp_async_wait<0>();
+    __syncthreads();
     for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
         const int ixn = (L - ix) & (L - 1);
         const float kx = (float)wave_number(ix, L, a.dk);
-        const float2 A1 = __ldg(coef + (int64_t)iy * L + ix);
-        const float2 A2 = __ldg(coef + (int64_t)iyn * L + ixn);
+        const float2 A1 = sA[ix];
+        const float2 A2 = sB[ixn];
         // e^{-j omega t}: omega t / 2 pi = w t with w = hi + lo, t = t_hi + t_lo
-        const float2 w = __ldg(omega + (int64_t)iy * L + ix);
+        const float2 w = sW[ix];
         const float p = w.x * a.t_hi;
         const float pe = fmaf(w.x, a.t_hi, -p);
         float f = (p - rintf(p)) + (pe + fmaf(w.x, a.t_lo, w.y * a.t_hi));
@@ -103,6 +123,9 @@ __global__ void __launch_bounds__(kRowsThreads) surf_rows_kernel(SurfArgs a, con
     }
 }
 
+// Columns pass: one CTA per block of C columns of one packed transform (gridDim.y); the
+// column pieces (32 bytes of every row for C = 4) are copied asynchronously, all of a
+// thread's copies in flight at once.
 __global__ void __launch_bounds__(kColsThreads) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
                                                         float* __restrict__ z, float* __restrict__ vx,
                                                         float* __restrict__ vy, float* __restrict__ vz) {
@@ -112,22 +135,22 @@ __global__ void __launch_bounds__(kColsThreads) surf_cols_kernel(SurfArgs a, con
     float2* buf0 = tw + (L >> 1);
     const int ix0 = blockIdx.x * C;
     const int pair = blockIdx.y;
-    const float2* src = tmp + (int64_t)pair * L * L;
-    for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
-#pragma unroll 8
+    const float2* src = tmp + (int64_t)pair * L * L + ix0;
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
         const int iy = idx / C, c = idx - iy * C;
-        buf0[c * NP + pad16(iy)] = __ldg(src + (int64_t)iy * L + ix0 + c);
+        cp_async8(buf0 + c * NP + pad16(iy), src + (int64_t)iy * L + c);
     }
+    cp_async_commit();
+    for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
+    cp_async_wait<0>();
     __syncthreads();
     fft_rows_reg<16>(buf0, C, L, a.log2L, tw, 1.0f);   // C L <= 16 x 512
-    const float2* res = buf0;
     float* fa = pair == 0 ? z : vx;
     float* fb = pair == 0 ? vz : vy;
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
         const int iy = idx / C, c = idx - iy * C;
-        const float2 v = res[c * NP + pad16(iy)];
+        const float2 v = buf0[c * NP + pad16(iy)];
         const int64_t o = (int64_t)iy * L + ix0 + c;
         fa[o] = v.x * a.scale_over_L2;
         fb[o] = v.y * a.scale_over_L2;
@@ -137,7 +160,7 @@ __global__ void __launch_bounds__(kColsThreads) surf_cols_kernel(SurfArgs a, con
 }  // namespace
 
 size_t surf_rows_smem(int L) {
-    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)padded_len(L));
+    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)padded_len(L) + 3 * (size_t)L);
 }
 size_t surf_cols_smem(int L, int cols) {
     return sizeof(float2) * ((size_t)(L / 2) + (size_t)cols * padded_len(L));
