@@ -65,7 +65,9 @@ __device__ T* stockham(T* a, T* b, int rows, int N, int L, const T* __restrict__
 // Radix-4 Stockham autosort (a final radix-2 stage when log2 N is odd) over `rows`
 // independent N-point rows in shared memory: half the passes over the data of the radix-2
 // version.  tw[n] = exp(sign j 2 pi n / N) for n < N/2 (the other half by W^{n+N/2} = -W^n);
-// `sign` (+1 or -1) is the transform's.  Returns the buffer holding the natural-order result.
+// `sign` (+1 or -1) is the transform's.  Row r starts at element r * stride of each buffer
+// (stride 0 means N; an odd stride lets a later pass read down a column without bank
+// conflicts).  Returns the buffer holding the natural-order result.
 template <typename T>
 __device__ __forceinline__ T tw_full(const T* tw, int e, int N) {
     const int h = N >> 1;
@@ -78,17 +80,19 @@ __device__ __forceinline__ T tw_full(const T* tw, int e, int N) {
 }
 
 template <typename T>
-__device__ T* stockham4(T* a, T* b, int rows, int N, int L, const T* __restrict__ tw, int sign) {
+__device__ T* stockham4(T* a, T* b, int rows, int N, int L, const T* __restrict__ tw, int sign,
+                        int stride = 0) {
     int s = 1, lg = 0;
     const int quarter = N >> 2;
+    const int rs = stride > 0 ? stride : N;
     while (lg + 2 <= L) {                       // radix-4 stages: s = 4^(lg/2) = 2^lg
         const int m = quarter >> lg;
         for (int idx = threadIdx.x; idx < rows * quarter; idx += blockDim.x) {
             const int row = idx >> (L - 2);
             const int bi = idx & (quarter - 1);
             const int p = bi >> lg, q = bi & (s - 1);
-            const T* ar = a + row * N;
-            T* br = b + row * N;
+            const T* ar = a + row * rs;
+            T* br = b + row * rs;
             const T x0 = ar[q + s * p], x1 = ar[q + s * (p + m)];
             const T x2 = ar[q + s * (p + 2 * m)], x3 = ar[q + s * (p + 3 * m)];
             const T t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), d = csub(x1, x3);
@@ -111,8 +115,8 @@ __device__ T* stockham4(T* a, T* b, int rows, int N, int L, const T* __restrict_
         for (int idx = threadIdx.x; idx < rows * half; idx += blockDim.x) {
             const int row = idx >> (L - 1);
             const int q = idx & (half - 1);
-            const T* ar = a + row * N;
-            T* br = b + row * N;
+            const T* ar = a + row * rs;
+            T* br = b + row * rs;
             const T x0 = ar[q], x1 = ar[q + half];
             br[q] = cadd(x0, x1);
             br[q + half] = csub(x0, x1);

@@ -36,46 +36,71 @@ __device__ __forceinline__ double window_w(int w, double d) {
     return 1.0 - d;
 }
 
+// Window table size: W(d / n_fast) for d = 0 .. n_fast is tabulated per CTA when
+// n_fast < kWinTable (the blend then reads both weights of a pulse from shared memory).
+constexpr int kWinTable = 1024;
+// Forward synthesis CTA: kSynthThreads threads stage at most 2048 complex elements
+// (2 spectra x gates per CTA x n_doppler), kSynthStage per thread.
+constexpr int kSynthThreads = 256;
+constexpr int kSynthStage = 8;
+
 template <typename R>
-__global__ void __launch_bounds__(256) synth_kernel(SynthArgs a, int64_t seg0, int gpc,
+__global__ void __launch_bounds__(kSynthThreads) synth_kernel(SynthArgs a, int64_t seg0, int lg_gpc,
                                                     const typename Cplx<R>::T* __restrict__ spec,
                                                     typename Cplx<R>::T* __restrict__ iq) {
     using T = typename Cplx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.n_doppler;
+    const int N = a.n_doppler, L = a.log2_nd;
+    const int gpc = 1 << lg_gpc;                    // gates per CTA (a power of two <= 32)
+    const int NS = N + 1;                           // odd row stride: the blend reads columns
     T* tw = reinterpret_cast<T*>(smem_raw);
     T* buf0 = tw + (N >> 1);
-    T* buf1 = buf0 + 2 * gpc * N;
+    T* buf1 = buf0 + 2 * gpc * NS;
+    R* wt = reinterpret_cast<R*>(buf1 + 2 * gpc * NS);
     const int64_t i = seg0 + blockIdx.x;            // segment between updates i and i + 1
     const int g0 = blockIdx.y * gpc;
+    // Rows of buf0: [spectrum i | spectrum i + 1] x [gate g0 .. g0 + gpc), N bins each:
+    // at most kSynthStage elements per thread (the launch guarantees it), all loaded into
+    // registers before any is stored so that the loads are in flight together.
+    const int total = (2 * gpc) << L;
+    T v[kSynthStage];
+#pragma unroll
+    for (int u = 0; u < kSynthStage; ++u) {
+        const int idx = threadIdx.x + u * kSynthThreads;
+        const int row = idx >> L, k = idx & (N - 1);
+        const int g = g0 + (row & (gpc - 1));
+        const int64_t si = i + (row >> lg_gpc) - a.update0;
+        v[u].x = R(0); v[u].y = R(0);
+        if (idx < total && g < a.n_gates && si >= 0 && si < a.n_spectra)
+            v[u] = spec[(si * a.n_gates + g) * N + k];
+    }
+    const R inv_nf = R(1) / R(a.n_fast);
+    const bool table = a.n_fast < kWinTable;
     for (int r = threadIdx.x; r < (N >> 1); r += blockDim.x) twiddle(r, N, R(1), tw[r]);
-    for (int idx = threadIdx.x; idx < 2 * gpc * N; idx += blockDim.x) {
-        const int row = idx / N, k = idx - row * N;
-        const int sp = row / gpc, gg = row - sp * gpc;
-        const int g = g0 + gg;
-        const int64_t si = i + sp - a.update0;
-        T v;
-        v.x = R(0); v.y = R(0);
-        if (g < a.n_gates && si >= 0 && si < a.n_spectra) v = spec[(si * a.n_gates + g) * N + k];
-        buf0[idx] = v;
+    if (table)
+        for (int d = threadIdx.x; d <= a.n_fast; d += blockDim.x) wt[d] = window_w(a.window, R(d) * inv_nf);
+#pragma unroll
+    for (int u = 0; u < kSynthStage; ++u) {
+        const int idx = threadIdx.x + u * kSynthThreads;
+        if (idx < total) buf0[(idx >> L) * NS + (idx & (N - 1))] = v[u];
     }
     __syncthreads();
-    const T* res = stockham4(buf0, buf1, 2 * gpc, N, a.log2_nd, tw, 1);
+    const T* res = stockham4(buf0, buf1, 2 * gpc, N, L, tw, 1, NS);
     const int64_t p_i = i * a.n_fast;
     const int64_t x_lo = max(p_i, a.pulse0);
     const int64_t x_hi = min(p_i + a.n_fast, a.pulse0 + a.n_pulses);
-    const int64_t count = (x_hi - x_lo) * gpc;
-    const R inv_nf = R(1) / R(a.n_fast);
-    for (int64_t idx = threadIdx.x; idx < count; idx += blockDim.x) {
-        const int gg = (int)(idx % gpc);
-        const int64_t x = x_lo + idx / gpc;
-        const int g = g0 + gg;
-        if (g >= a.n_gates) continue;
-        const R w0 = window_w(a.window, R(x - p_i) * inv_nf);
-        const R w1 = window_w(a.window, R(p_i + a.n_fast - x) * inv_nf);
-        const int m0 = (int)((x - p_i) & (N - 1));
-        const int m1 = (int)((x - p_i - a.n_fast) & (N - 1));
-        const T y = cadd(cscale(res[gg * N + m0], w0), cscale(res[(gpc + gg) * N + m1], w1));
+    // Thread -> (gate gg, pulse offset): gpc consecutive threads write one pulse's gates.
+    const int gg = threadIdx.x & (gpc - 1);
+    const int g = g0 + gg;
+    if (g >= a.n_gates) return;
+    const T* r0 = res + gg * NS;
+    const T* r1 = res + (gpc + gg) * NS;
+    const int xs = blockDim.x >> lg_gpc;
+    for (int64_t x = x_lo + (threadIdx.x >> lg_gpc); x < x_hi; x += xs) {
+        const int d = (int)(x - p_i);               // 0 <= d < n_fast
+        const R w0 = table ? wt[d] : window_w(a.window, R(d) * inv_nf);
+        const R w1 = table ? wt[a.n_fast - d] : window_w(a.window, R(a.n_fast - d) * inv_nf);
+        const T y = cadd(cscale(r0[d & (N - 1)], w0), cscale(r1[(d - a.n_fast) & (N - 1)], w1));
         iq[(x - a.pulse0) * a.n_gates + g] = y;
     }
 }
@@ -121,13 +146,14 @@ __global__ void __launch_bounds__(256) synth_backward_kernel(
     }
 }
 
-int gates_per_cta(int n_gates, int N, bool fp64) {
+// Gates per CTA: a power of two (so it divides the 256 threads), at most 32, about
+// 1024 (FP32) or 512 (FP64) staged complex elements per spectrum, and no more than the
+// smallest power of two >= n_gates.
+int lg_gates_per_cta(int n_gates, int N, bool fp64) {
     const int elems = fp64 ? 512 : 1024;  // complex elements per staged spectrum tile
-    int gpc = elems / N;
-    if (gpc < 1) gpc = 1;
-    if (gpc > 32) gpc = 32;
-    if (gpc > n_gates) gpc = n_gates;
-    return gpc;
+    int lg = 0;
+    while (lg < 5 && (2 << lg) * N <= elems && (1 << lg) < n_gates) ++lg;
+    return lg;
 }
 
 }  // namespace
@@ -135,29 +161,32 @@ int gates_per_cta(int n_gates, int N, bool fp64) {
 cudaError_t launch_synth(const SynthArgs& a, bool fp64, const void* spectra, void* iq,
                          cudaStream_t stream) {
     const int N = a.n_doppler;
-    const int gpc = gates_per_cta(a.n_gates, N, fp64);
+    const int lg_gpc = lg_gates_per_cta(a.n_gates, N, fp64);
+    const int gpc = 1 << lg_gpc;
     const int64_t seg0 = a.pulse0 / a.n_fast;
     const int64_t seg1 = (a.pulse0 + a.n_pulses - 1) / a.n_fast;
     const dim3 grid((unsigned)(seg1 - seg0 + 1), (unsigned)((a.n_gates + gpc - 1) / gpc));
     const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);
-    const size_t smem = esz * ((size_t)(N >> 1) + 4 * (size_t)gpc * N);
+    const size_t win = a.n_fast < kWinTable ? (size_t)(a.n_fast + 1) * (esz / 2) : 0;
+    const size_t smem = esz * ((size_t)(N >> 1) + 4 * (size_t)gpc * (N + 1)) + win;
     if (smem > 48 * 1024) {
         const cudaError_t e = fp64
             ? cudaFuncSetAttribute(synth_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
             : cudaFuncSetAttribute(synth_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (fp64) synth_kernel<double><<<grid, 256, smem, stream>>>(
-        a, seg0, gpc, static_cast<const double2*>(spectra), static_cast<double2*>(iq));
-    else synth_kernel<float><<<grid, 256, smem, stream>>>(
-        a, seg0, gpc, static_cast<const float2*>(spectra), static_cast<float2*>(iq));
+    if (((2 * gpc) << a.log2_nd) > kSynthThreads * kSynthStage) return cudaErrorInvalidValue;
+    if (fp64) synth_kernel<double><<<grid, kSynthThreads, smem, stream>>>(
+        a, seg0, lg_gpc, static_cast<const double2*>(spectra), static_cast<double2*>(iq));
+    else synth_kernel<float><<<grid, kSynthThreads, smem, stream>>>(
+        a, seg0, lg_gpc, static_cast<const float2*>(spectra), static_cast<float2*>(iq));
     return cudaGetLastError();
 }
 
 cudaError_t launch_synth_backward(const SynthArgs& a, bool fp64, const void* grad_iq,
                                   void* grad_spectra, cudaStream_t stream) {
     const int N = a.n_doppler;
-    const int gpc = gates_per_cta(a.n_gates, N, fp64);
+    const int gpc = 1 << lg_gates_per_cta(a.n_gates, N, fp64);
     const dim3 grid((unsigned)a.n_spectra, (unsigned)((a.n_gates + gpc - 1) / gpc));
     const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);
     const size_t smem = esz * ((size_t)(N >> 1) + 2 * (size_t)gpc * N);
