@@ -25,6 +25,8 @@ CASES = [
     (20, 128, 64, 64, 129),      # N_d > n_fast, range ending on an update pulse
     (3, 1024, 100, 250, 333),    # largest transform
     (1, 2, 1, 0, 17),            # smallest transform, n_fast = 1
+    (7, 4, 1023, 1, 2100),       # largest n_fast whose window the kernel tabulates
+    (5, 64, 1024, 700, 2500),    # n_fast past the table: window evaluated per pulse
 ]
 CDT = {"fp64": torch.complex128, "split": torch.complex64}
 
