@@ -448,7 +448,13 @@ class HostStreamer:
     copied while block i is summed (the summation
     adds, so the blocks' sums make the set's; every scatterer keeps its FP64 reference
     point).  All blocks add into one exact workspace, so the spectra are bit-identical to a
-    single call on the whole set.  Buffers and workspace are allocated once."""
+    single call on the whole set.  Buffers and workspace are allocated once.
+
+    ``run(..., host_out=pinned)`` also reads the IQ back into a pinned host tensor on a
+    read-back stream of its own, so the copy overlaps the scatterer pass of the next run; the
+    next run's post-processing waits for it before it rewrites the device IQ.  The host
+    tensor holds the result once ``readback_done`` has completed (``synchronize()`` it, or
+    ``wait_readback(stream)`` to order a stream after it)."""
 
     def __init__(self, n: int, n_gates: int, n_doppler: int, max_spectra: int,
                  chunks=None, device="cuda", precision: str = "split"):
@@ -479,12 +485,28 @@ class HostStreamer:
             edges = [min(self.n, i * per * blk) for i in range(self.chunks + 1)]
         self.ranges = [(a, b) for a, b in zip(edges[:-1], edges[1:]) if b > a]
         self.events = [torch.cuda.Event() for _ in self.ranges]
+        self.readback_stream = torch.cuda.Stream(device=self.dev)
+        self.readback_done = None      # event after the last IQ read-back, if any
+
+    def wait_readback(self, stream=None):
+        """Order ``stream`` (default: the current one) after the last IQ read-back."""
+        if self.readback_done is not None:
+            (stream or torch.cuda.current_stream(self.dev)).wait_event(self.readback_done)
 
     def run(self, radar, platform, host: dict, n_pulses: int, n_fast: int, n_doppler: int,
-            window: str = "sqrt_raised_cosine", pulse0: int = 0, spectra=None, out=None):
+            window: str = "sqrt_raised_cosine", pulse0: int = 0, spectra=None, out=None,
+            host_out=None):
         """host: pinned CPU float32 arrays x, y, z, vx, vy, vz, nrcs [n] (+ origin, area, t0).
-        Returns (spectra, iq) on the device, enqueued on the current stream."""
+        Returns (spectra, iq) on the device, enqueued on the current stream.  host_out: an
+        optional pinned CPU tensor [n_pulses, n_gates] of the IQ dtype that receives the IQ
+        through the read-back stream (complete once ``readback_done`` has completed)."""
         u0, S = spectra_range(pulse0, n_pulses, n_fast)
+        if host_out is not None:
+            if (host_out.device.type != "cpu" or not host_out.is_pinned()
+                    or tuple(host_out.shape) != (n_pulses, radar.n_gates)
+                    or host_out.dtype != _cdtype(self.precision) or not host_out.is_contiguous()):
+                raise ValueError("host_out must be a contiguous pinned CPU tensor [n_pulses, "
+                                 "n_gates] of the IQ dtype")
         cur = torch.cuda.current_stream(self.dev)
         T = spectra
         if T is None:
@@ -517,7 +539,17 @@ class HostStreamer:
         rel.record(cur)
         _lib.check(_lib.lib.rsim_workspace_finalize(S, G, n_doppler, prec, _ptr(self.ws), nbytes,
                                                     _ptr(T), st))
+        self.wait_readback(cur)                   # the last read-back has left the device IQ
         Y = synth_pulses(radar, T, u0, n_fast, pulse0, n_pulses, window, out=out)
+        if host_out is not None:
+            ready = torch.cuda.Event()
+            ready.record(cur)
+            self.readback_stream.wait_event(ready)
+            with torch.cuda.stream(self.readback_stream):
+                host_out.copy_(Y, non_blocking=True)
+            Y.record_stream(self.readback_stream)   # Y stays allocated until the copy is done
+            self.readback_done = torch.cuda.Event()
+            self.readback_done.record(self.readback_stream)
         return T, Y
 
 

@@ -154,7 +154,8 @@ def test_full_cfg1_sampled(rsim, orc):
 
 def test_host_streamer_overlaps_copies_and_matches(rsim):
     """Scatterers streamed from pinned host memory in blocks (copies overlapped with the
-    summation, exact sums in one workspace) give the spectra of one call on the whole set."""
+    summation, exact sums in one workspace) give the spectra of one call on the whole set;
+    the IQ read back on the streamer's side stream is each run's own result."""
     import scenegen as sg_
     c = sg_.config(1)
     rd, pf, fp = c["radar"], c["platform"], c["fast"]
@@ -182,3 +183,24 @@ def test_host_streamer_overlaps_copies_and_matches(rsim):
     assert len(one.ranges) == 1
     T4, _ = one.run(rd, pf, host, P, fp.n_fast, fp.n_doppler, fp.window)
     assert torch.equal(T4, T)
+    # IQ read back on the side stream into alternating pinned buffers, three runs in a row
+    # writing the same device IQ: each host copy holds its own run's result
+    yh = [torch.empty((P, rd.n_gates), dtype=torch.complex64).pin_memory() for _ in range(2)]
+    Yd = torch.empty((P, rd.n_gates), dtype=torch.complex64, device="cuda")
+    host2 = dict(host, t0=0.5)                           # a different state epoch: other IQ
+    for r, h in enumerate((host, host2, host)):
+        one.run(rd, pf, h, P, fp.n_fast, fp.n_doppler, fp.window, out=Yd, host_out=yh[r % 2])
+        if r == 1:
+            one.readback_done.synchronize()
+            Y2 = yh[1].clone()
+    one.wait_readback()
+    torch.cuda.synchronize()
+    assert torch.equal(yh[0], Y1.cpu())
+    assert not torch.equal(Y2, Y1.cpu())
+    dev2 = rsim.Scatterers(*[getattr(dev, k) for k in ("x", "y", "z", "vx", "vy", "vz", "nrcs")],
+                           origin=dev.origin, area=dev.area, t0=0.5)
+    _, Y5 = rsim.simulate_fast(rd, pf, dev2, P, fp.n_fast, fp.n_doppler, fp.window)
+    assert torch.equal(Y2, Y5.cpu())
+    with pytest.raises(ValueError):
+        one.run(rd, pf, host, P, fp.n_fast, fp.n_doppler, fp.window,
+                host_out=torch.empty((P, rd.n_gates), dtype=torch.complex64))   # not pinned
