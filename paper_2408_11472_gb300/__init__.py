@@ -636,24 +636,95 @@ class EvolvingSurface:
                           origin=self.origin, area=self.area, t0=float(t))
 
 
+def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int, n_fast: int,
+                      n_doppler: int, precision: str, T: torch.Tensor, ws: torch.Tensor,
+                      stream=None):
+    """Spectra T[s] (+=) of updates u0 + s, the surface regenerated at each update: one
+    workspace clear, per update a synthesis and a summation into that update's slot of the
+    exact fixed-point workspace, one conversion of all slots at the end."""
+    G = radar.n_gates
+    nbytes = ws.numel() * ws.element_size()
+    st, prec = _stream(stream), _prec(precision)
+    rd, pf = _lib.make_radar(radar), _lib.make_platform(platform)
+    _lib.check(_lib.lib.rsim_workspace_clear(S, G, n_doppler, _ptr(ws), nbytes, st))
+    slot = workspace_size(1, G, n_doppler)
+    for s in range(S):
+        sc = surface.at((u0 + s) * n_fast / radar.prf_hz, stream=stream).c_struct()
+        _lib.check(_lib.lib.rsim_doppler_accumulate_partial(
+            ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(u0 + s), 1, int(n_fast),
+            int(n_doppler), prec, ctypes.c_void_p(_ptr(ws) + s * slot), nbytes - s * slot, st))
+    _lib.check(_lib.lib.rsim_workspace_finalize(S, G, n_doppler, prec, _ptr(ws), nbytes, _ptr(T),
+                                                st))
+
+
 def simulate_fast_evolving(radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
                            n_doppler: int, window: str = "sqrt_raised_cosine",
                            precision: str = "split", pulse0: int = 0,
                            workspace: Optional[torch.Tensor] = None, stream=None):
     """Fast mode with the surface regenerated at every update (Algorithm 1 in full): for each
     update i the surface at t_i = p_i / PRF, its Doppler spectrum, then the post-processing.
+    ``workspace``: at least workspace_size(S, n_gates, n_doppler) bytes for the S spectra.
     Returns (spectra, iq)."""
     u0, S = spectra_range(pulse0, n_pulses, n_fast)
     G = radar.n_gates
     dev = surface.coef.device
     T = torch.zeros((S, G, n_doppler), dtype=_cdtype(precision), device=dev)
-    ws = _workspace(workspace, workspace_size(1, G, n_doppler), dev)
-    for s in range(S):
-        sc = surface.at((u0 + s) * n_fast / radar.prf_hz, stream=stream)
-        doppler_accumulate(radar, platform, sc, u0 + s, 1, n_fast, n_doppler, precision,
-                           out=T[s:s + 1], workspace=ws, stream=stream)
+    ws = _workspace(workspace, workspace_size(S, G, n_doppler), dev)
+    _evolving_spectra(radar, platform, surface, u0, S, n_fast, n_doppler, precision, T, ws, stream)
     Y = synth_pulses(radar, T, u0, n_fast, pulse0, n_pulses, window, stream=stream)
     return T, Y
+
+
+class EvolvingFastMode:
+    """simulate_fast_evolving with every buffer allocated once, so the whole update loop
+    (per update a surface synthesis and a summation, then the post-processing) can be
+    captured into a CUDA graph (``capture()``) and replayed (``replay()``).  ``spectra`` and
+    ``iq`` hold the results; ``run()`` enqueues the same work eagerly."""
+
+    def __init__(self, radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
+                 n_doppler: int, window: str = "sqrt_raised_cosine", precision: str = "split",
+                 pulse0: int = 0):
+        self.radar, self.platform, self.surface = radar, platform, surface
+        self.n_pulses, self.n_fast, self.n_doppler = n_pulses, n_fast, n_doppler
+        self.window, self.precision, self.pulse0 = window, precision, pulse0
+        self.u0, self.S = spectra_range(pulse0, n_pulses, n_fast)
+        dev = surface.coef.device
+        G, cdt = radar.n_gates, _cdtype(precision)
+        self.spectra = torch.zeros((self.S, G, n_doppler), dtype=cdt, device=dev)
+        self.iq = torch.empty((n_pulses, G), dtype=cdt, device=dev)
+        self.workspace = torch.empty(max(16, workspace_size(self.S, G, n_doppler)),
+                                     dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def _run(self):
+        self.spectra.zero_()
+        _evolving_spectra(self.radar, self.platform, self.surface, self.u0, self.S, self.n_fast,
+                          self.n_doppler, self.precision, self.spectra, self.workspace)
+        synth_pulses(self.radar, self.spectra, self.u0, self.n_fast, self.pulse0, self.n_pulses,
+                     self.window, out=self.iq)
+
+    def run(self):
+        self._run()
+        return self.spectra, self.iq
+
+    def capture(self):
+        """Record the whole update loop into a CUDA graph (after one eager warm-up run)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._run()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._run()
+        self.graph = g
+        return self
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+        return self.spectra, self.iq
 
 
 class BatchedFastMode:
