@@ -628,31 +628,69 @@ class EvolvingSurface:
         _lib.check(_lib.lib.rsim_surface_prepare(ctypes.byref(self.spec), _ptr(self.workspace),
                                                  n, _stream(None)))
 
-    def at(self, t: float, stream=None) -> Scatterers:
+    def at(self, t: float, stream=None, fields=None) -> Scatterers:
+        """The surface at t; ``fields``: optional (z, vx, vy, vz) float32 [L*L] tensors to
+        write instead of the surface's own (e.g. a second set from ``new_fields()``, so
+        one update can be synthesised while the last one is still being read)."""
+        z, vx, vy, vz = fields if fields is not None else (self.z, self.vx, self.vy, self.vz)
+        for f in (z, vx, vy, vz):
+            if f.dtype != torch.float32 or f.numel() != self.L * self.L or f.device != self.z.device \
+                    or not f.is_contiguous():
+                raise ValueError("fields must be contiguous float32 [L*L] tensors on the surface's device")
         _lib.check(_lib.lib.rsim_surface_at(
-            ctypes.byref(self.spec), float(t), _ptr(self.z), _ptr(self.vx), _ptr(self.vy),
-            _ptr(self.vz), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
-        return Scatterers(self.x, self.y, self.z, self.vx, self.vy, self.vz, self.nrcs,
+            ctypes.byref(self.spec), float(t), _ptr(z), _ptr(vx), _ptr(vy),
+            _ptr(vz), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
+        return Scatterers(self.x, self.y, z, vx, vy, vz, self.nrcs,
                           origin=self.origin, area=self.area, t0=float(t))
+
+    def new_fields(self):
+        """A second (z, vx, vy, vz) set of buffers for ``at(..., fields=...)``."""
+        return tuple(torch.empty_like(self.z) for _ in range(4))
 
 
 def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int, n_fast: int,
                       n_doppler: int, precision: str, T: torch.Tensor, ws: torch.Tensor,
-                      stream=None):
+                      stream=None, fields2=None, side=None):
     """Spectra T[s] (+=) of updates u0 + s, the surface regenerated at each update: one
     workspace clear, per update a synthesis and a summation into that update's slot of the
-    exact fixed-point workspace, one conversion of all slots at the end."""
+    exact fixed-point workspace, one conversion of all slots at the end.
+
+    With a second field set ``fields2`` and a ``side`` stream, the syntheses run on the side
+    stream into alternating field sets, so update s + 1 is synthesised while update s is
+    summed (same kernels and inputs: the same bits)."""
     G = radar.n_gates
     nbytes = ws.numel() * ws.element_size()
-    st, prec = _stream(stream), _prec(precision)
+    cur = stream if stream is not None else torch.cuda.current_stream()
+    st, prec = _stream(cur), _prec(precision)
     rd, pf = _lib.make_radar(radar), _lib.make_platform(platform)
     _lib.check(_lib.lib.rsim_workspace_clear(S, G, n_doppler, _ptr(ws), nbytes, st))
     slot = workspace_size(1, G, n_doppler)
+    overlap = fields2 is not None and side is not None
+    if overlap:
+        sets = ((surface.z, surface.vx, surface.vy, surface.vz), tuple(fields2))
+        read = [None, None]                 # event after the summation that last read a set
+        fork = torch.cuda.Event()
+        fork.record(cur)
+        side.wait_event(fork)
     for s in range(S):
-        sc = surface.at((u0 + s) * n_fast / radar.prf_hz, stream=stream).c_struct()
+        t = (u0 + s) * n_fast / radar.prf_hz
+        if overlap:
+            k = s & 1
+            if read[k] is not None:
+                side.wait_event(read[k])    # the summation two updates back has read it
+            scat = surface.at(t, stream=side, fields=sets[k])
+            made = torch.cuda.Event()
+            made.record(side)
+            cur.wait_event(made)
+        else:
+            scat = surface.at(t, stream=cur)
+        sc = scat.c_struct()
         _lib.check(_lib.lib.rsim_doppler_accumulate_partial(
             ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(u0 + s), 1, int(n_fast),
             int(n_doppler), prec, ctypes.c_void_p(_ptr(ws) + s * slot), nbytes - s * slot, st))
+        if overlap:
+            read[k] = torch.cuda.Event()
+            read[k].record(cur)
     _lib.check(_lib.lib.rsim_workspace_finalize(S, G, n_doppler, prec, _ptr(ws), nbytes, _ptr(T),
                                                 st))
 
@@ -678,8 +716,10 @@ def simulate_fast_evolving(radar, platform, surface: EvolvingSurface, n_pulses: 
 class EvolvingFastMode:
     """simulate_fast_evolving with every buffer allocated once, so the whole update loop
     (per update a surface synthesis and a summation, then the post-processing) can be
-    captured into a CUDA graph (``capture()``) and replayed (``replay()``).  ``spectra`` and
-    ``iq`` hold the results; ``run()`` enqueues the same work eagerly."""
+    captured into a CUDA graph (``capture()``) and replayed (``replay()``).  The syntheses
+    run on a side stream into two alternating field sets, overlapped with the summations;
+    the results are those of simulate_fast_evolving bit for bit.  ``spectra`` and ``iq``
+    hold the results; ``run()`` enqueues the same work eagerly."""
 
     def __init__(self, radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
                  n_doppler: int, window: str = "sqrt_raised_cosine", precision: str = "split",
@@ -694,12 +734,17 @@ class EvolvingFastMode:
         self.iq = torch.empty((n_pulses, G), dtype=cdt, device=dev)
         self.workspace = torch.empty(max(16, workspace_size(self.S, G, n_doppler)),
                                      dtype=torch.uint8, device=dev)
+        # a second field set and a side stream: update s + 1 is synthesised while update s
+        # is summed
+        self.fields2 = surface.new_fields()
+        self.side = torch.cuda.Stream(device=dev)
         self.graph = None
 
     def _run(self):
         self.spectra.zero_()
         _evolving_spectra(self.radar, self.platform, self.surface, self.u0, self.S, self.n_fast,
-                          self.n_doppler, self.precision, self.spectra, self.workspace)
+                          self.n_doppler, self.precision, self.spectra, self.workspace,
+                          fields2=self.fields2, side=self.side)
         synth_pulses(self.radar, self.spectra, self.u0, self.n_fast, self.pulse0, self.n_pulses,
                      self.window, out=self.iq)
 
