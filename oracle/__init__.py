@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
 and by the CPU-baseline leg of ``bench.py``; the library's product path never
 imports, links or runs anything here, and nothing here imports the library.
 
-Two independent restatements of the paper's method live here:
+Independent restatements of the paper's method live here:
 
 * ``rsim_oracle.c`` (plain C, OpenMP over fixed chunks, compensated sums,
   direct O(N_d^2) DFT), wrapped by :class:`Oracle` through ctypes;
