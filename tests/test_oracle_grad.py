@@ -85,3 +85,32 @@ def test_gradient_vs_central_differences(orc, mode):
         Lm, _ = _loss_and_grad_y(forward(_perturbed(sc, "nrcs", n, sm)), target)
         fd = (Lp - Lm) / (float(sp) - float(sm))
         assert gs[n] == pytest.approx(fd, rel=2e-4, abs=1e-6 * np.abs(gs).max())
+
+
+@pytest.mark.parametrize("x0", [0.0, 6000.0, 10000.0])
+def test_amplitude_derivative_of_a_lone_scatterer(orc, x0):
+    """The amplitude part of dC/dz is about 1e-8 of the phase part, so the waveform-power
+    finite differences above cannot see it.  For one scatterer alone in its gate the loss
+    L = |Y|^2 = a^2 carries no phase: the adjoint with dL/dY = 2 Y returns 2 a^2 d ln a / dz
+    exactly, which central differences of L check here -- at nadir (range factor
+    (r_ref / R)^2 alone) and 6 and 10 km off nadir, where the beam term
+    d ln w / dz = -4 ln2 theta rho / (theta_b^2 R^2) reaches 15 % and 40 % of it."""
+    rd = sg.RadarParams()
+    H = 800e3
+    z0, h = 0.25, 2.0 ** -8                              # z0 +- h exact in float32
+    R = float(np.hypot(x0, H - z0))
+    pf = sg.PlatformParams(p0=(0.0, 0.0, H), v=(0.0, 0.0, 0.0), r_ref0=R + 0.2, r_ref_rate=0.0)
+
+    def scene(z):
+        return sg.point_scene([(x0, 0.0, z, 0.0, 0.0, 0.0, 0.3)])
+
+    def loss(z):
+        return float((np.abs(orc.direct_sum(rd, pf, scene(z), 0, 1)) ** 2).sum())
+
+    Y = orc.direct_sum(rd, pf, scene(z0), 0, 1)
+    assert np.count_nonzero(Y) == 1                       # one gate, mid-gate
+    gz, gs = orc.direct_grad(rd, pf, scene(z0), 0, 2.0 * Y)
+    fd = (loss(z0 + h) - loss(z0 - h)) / (2.0 * h)
+    assert gz[0] == pytest.approx(fd, rel=1e-4)
+    # and d L / d sigma = L / sigma for L = a^2, a proportional to sqrt(sigma)
+    assert gs[0] == pytest.approx(loss(z0) / 0.3, rel=1e-6)
