@@ -1,5 +1,5 @@
 """Multi-rank split of one realization (Section II.B): scatterer shards per rank and one
-sum-reduce of the spectra, run as 2 CPU ranks over gloo (the oracle computes each rank's
+sum-reduce of the spectra, run as 2 and 3 CPU ranks over gloo (the oracle computes each rank's
 partial spectra, so no GPU is needed)."""
 import os
 import socket
@@ -75,3 +75,23 @@ def test_two_rank_tile_split_equals_single_realization(tmp_path):
                                          c["fast"].n_doppler)
     assert np.abs(T1).max() > 0
     np.testing.assert_allclose(T2, T1, rtol=0, atol=1e-12 * np.abs(T1).max())
+
+
+def test_three_rank_ragged_split_equals_single_realization(tmp_path):
+    """6400 scatterers are 6.25 blocks: three ranks get 3, 2 and 1.25 blocks (a ragged
+    last shard); the all-reduced spectra still equal the single-rank ones."""
+    import oracle
+    import scenegen as sg
+    from paper_2408_11472_gb300.sharding import shard_range
+
+    n = 80 * 80
+    spans = [shard_range(n, 3, r) for r in range(3)]
+    assert len({e - s for s, e in spans}) == 3               # three different shard sizes
+    out = str(tmp_path / "T3.npy")
+    mp.start_processes(_rank_main, args=(3, _free_port(), out), nprocs=3, join=True,
+                       start_method="spawn")
+    T3 = np.load(out)
+    c = sg.config(1)
+    T1 = oracle.Oracle().doppler_spectra(c["radar"], c["platform"], sg.sea_surface(80, 13), 31, 3,
+                                         c["fast"].n_fast, c["fast"].n_doppler)
+    np.testing.assert_allclose(T3, T1, rtol=0, atol=1e-12 * np.abs(T1).max())
