@@ -126,3 +126,10 @@ def test_python_layer_requires_cuda_tensors():
     assert rsim.spectra_range(100, 28, 64) == (1, 2)
     assert rsim.spectra_range(100, 29, 64) == (1, 3)
     del np
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built CUDA library the binding refuses to load: there is no CPU fallback."""
+    from paper_2408_11472_gb300 import _lib
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        _lib.load(str(tmp_path / "librsim.so"))
