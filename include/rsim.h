@@ -74,7 +74,7 @@ typedef enum {
     RSIM_OK = 0,
     RSIM_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, size or value out of range     */
     RSIM_ERR_CUDA = 2,         /* a CUDA launch or stream operation failed                 */
-    RSIM_ERR_UNSUPPORTED = 3,  /* valid request this build does not implement             */
+    RSIM_ERR_UNSUPPORTED = 3,  /* valid request the library does not implement           */
     RSIM_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                       */
     RSIM_ERR_WORKSPACE = 5     /* workspace missing, misaligned or smaller than required   */
 } rsim_status;

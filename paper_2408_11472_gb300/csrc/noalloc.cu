@@ -41,7 +41,7 @@ rsim_status scratch_for_current_device(void** out) {
         return RSIM_ERR_CUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) {
-        rsim::set_last_error("device index %d beyond the %d devices this build tracks", dev, kMaxDevices);
+        rsim::set_last_error("device index %d beyond the %d devices the library tracks", dev, kMaxDevices);
         return RSIM_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);

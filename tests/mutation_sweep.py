@@ -96,11 +96,23 @@ MUTANTS = {
 }
 
 
+# what a scratch copy needs: the package (with its built library), the oracle, the input
+# generator, the tests and the scripts they run
+_ENTRIES = ("paper_2408_11472_gb300", "include", "oracle", "scenegen", "tests", "bench.py",
+            "bench_configs.py", "__graft_entry__.py")
+
+
 def copy_repo(dst):
     if os.path.exists(dst):
         shutil.rmtree(dst)
-    shutil.copytree(SRC, dst, ignore=shutil.ignore_patterns(".git", "_work", "gpurun_out", "_build",
-                                                             "__pycache__", ".pytest_cache"))
+    os.makedirs(dst)
+    skip = shutil.ignore_patterns("__pycache__", ".pytest_cache")
+    for e in _ENTRIES:
+        src = os.path.join(SRC, e)
+        if os.path.isdir(src):
+            shutil.copytree(src, os.path.join(dst, e), ignore=skip)
+        else:
+            shutil.copy2(src, os.path.join(dst, e))
 
 
 def run_tests(dst):
