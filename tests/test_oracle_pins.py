@@ -347,3 +347,26 @@ def test_galilean_invariance_of_the_stop_and_hop_geometry(orc):
     assert np.linalg.norm(Ta - Tb) < 1e-6 * np.linalg.norm(Ta)
     # the platform's motion is really seen: the echo changes along the run
     assert np.linalg.norm(Ya[0] - Ya[-1]) > 0.1 * np.linalg.norm(Ya[0])
+
+
+def test_sums_do_not_depend_on_the_thread_count():
+    """The oracle sums over a fixed number of scatterer chunks and merges them in chunk
+    order, so its results are the same bits however many threads run."""
+    import oracle
+    c = sg.config(1)
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    sc = sg.sea_surface(150, 17)                      # 22,500 scatterers over all the chunks
+    orc = oracle.Oracle()
+    before = orc.threads                              # the thread count is process-wide
+    out = []
+    try:
+        for threads in (1, 4):
+            orc.set_threads(threads)
+            assert orc.threads == threads
+            out.append((orc.direct_sum(rd, pf, sc, 2040, 3),
+                        orc.doppler_spectra(rd, pf, sc, 31, 2, fp.n_fast, fp.n_doppler)))
+    finally:
+        orc.set_threads(before)
+    assert np.abs(out[0][0]).max() > 0 and np.abs(out[0][1]).max() > 0
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
