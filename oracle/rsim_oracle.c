@@ -18,7 +18,7 @@
  *   t_p      = p / PRF                                   (stop-and-hop)
  *   s(t)     = O + r + v (t - t0),  P(t) = p0 + V t,  d = P - s   (Alg. 1 update_simulation, linear
  *              kinematics from the state given at epoch t0)
- *   R        = |d|,  dR = R - r_ref(t)
+ *   R        = |d|,  dR = R - r_ref(t)  (evaluated without cancellation, see echo_at)
  *   theta    = atan2(|d_xy|, d_z)                          (nadir-pointing antenna)
  *   w        = exp(-2 ln2 theta^2/theta_b^2)               (analytic two-way pattern), or
  *            = the complex two-way pattern G(u, v) tabulated on a u-v grid and interpolated
@@ -32,6 +32,8 @@
  *                C_i, R_i at t(p_i);  C_{i+1} at t(p_i + 1);
  *                D_i = arg(conj(C_{i+1}) C_i) PRF              [rad/s]
  *                nu  = -D_i / (2 pi PRF)                      [cycles/pulse, in [-1/2, 1/2)]
+ *                      (the phase change of C over the pair, its geometric part taken
+ *                      from the range change R_{i+1} - R_i written without cancellation)
  *                bin = floor(nu N_d + 1/2) mod N_d            (nearest DFT bin)
  *                T[i, gate(R_i), bin] += C_i                  (rasterize)
  *              then post-processing (Sec. III.B): unnormalised inverse DFT along
@@ -75,7 +77,8 @@ typedef struct {
 } or_scene;
 
 typedef struct {
-    double R, dR, rho, dz, theta, amp, psi, re, im;
+    double R, dR, rho, dx, dy, dz, theta, amp, psi, re, im;
+    double g_re, g_im;   /* complex two-way gain G of the pattern (the Gaussian pattern: real) */
     /* tabulated pattern only: base = sqrt(sigma A) (r_ref/R)^2, phase factor (cr, ci),
      * direction cosines (u, v) and dG/du, dG/dv (complex) */
     double base, cr, ci, u, v, gu_re, gu_im, gv_re, gv_im;
@@ -139,14 +142,21 @@ static void echo_at(const or_radar *rd, const or_platform *pf, const or_scene *s
     double rho = sqrt(dx * dx + dy * dy);
     double R = sqrt(dx * dx + dy * dy + dz * dz);
     double rref = pf->r_ref0 + pf->r_ref_rate * t;
+    /* dR = R - r_ref = (|d|^2 - r_ref^2) / (R + r_ref), with d_z - r_ref taken as
+     * (P_z - r_ref) - s_z: the same number as the difference of the two ~8e5 m ranges,
+     * without the ~1e-10 m their FP64 rounding leaves in it */
+    double dzr = (pz - rref) - sz;
+    double dR = (dx * dx + dy * dy + dzr * (dz + rref)) / (R + rref);
     double lambda = rd->c_mps / rd->carrier_hz;
     double theta = atan2(rho, dz);
     double base = sqrt((double)sc->nrcs[n] * sc->area) * (rref / R) * (rref / R);
     double psi = 2.0 * R / lambda;
     double phi = -2.0 * OR_PI * (psi - rint(psi));
     e->R = R;
-    e->dR = R - rref;
+    e->dR = dR;
     e->rho = rho;
+    e->dx = dx;
+    e->dy = dy;
     e->dz = dz;
     e->theta = theta;
     e->psi = psi;
@@ -158,6 +168,8 @@ static void echo_at(const or_radar *rd, const or_platform *pf, const or_scene *s
         e->u = -dx / R;
         e->v = -dy / R;
         antenna_gain(rd, e->u, e->v, g, gu, gv);
+        e->g_re = g[0];
+        e->g_im = g[1];
         e->gu_re = gu[0];
         e->gu_im = gu[1];
         e->gv_re = gv[0];
@@ -168,6 +180,8 @@ static void echo_at(const or_radar *rd, const or_platform *pf, const or_scene *s
     } else {
         double tb = rd->beamwidth_rad;
         double w = exp(-2.0 * OR_LN2 * theta * theta / (tb * tb));
+        e->g_re = w;
+        e->g_im = 0.0;
         e->u = e->v = e->gu_re = e->gu_im = e->gv_re = e->gv_im = 0.0;
         e->amp = base * w;
         e->re = e->amp * e->cr;
@@ -179,13 +193,30 @@ static double gate_coord_of(const or_radar *rd, double dR) {
     return dR / rd->gate_width_m + 0.5 * (double)rd->n_gates;
 }
 
-/* Pulse-pair Doppler of Algorithm 1, D = arg(conj(C2) C1) PRF, mapped to the
- * pre-floor bin coordinate nu N_d + 1/2 (nu in cycles per pulse). */
-static double bin_coord_of(const or_radar *rd, const or_echo *c1, const or_echo *c2, int n_doppler) {
-    double pr = c2->re * c1->re + c2->im * c1->im;   /* Re(conj(C2) C1) */
-    double pi_ = c2->re * c1->im - c2->im * c1->re;  /* Im(conj(C2) C1) */
-    double D = atan2(pi_, pr) * rd->prf_hz;
-    double nu = -D / (2.0 * OR_PI * rd->prf_hz);
+/* Pulse-pair Doppler of Algorithm 1, D = arg(conj(C2) C1) PRF, as the pre-floor bin
+ * coordinate nu N_d + 1/2, nu = -D / (2 pi PRF) in cycles per pulse, in [-1/2, 1/2).
+ * With C = |C| G e^{-j 2 pi psi}, psi = 2 R / lambda (G the pattern's complex gain):
+ *   arg(conj(C2) C1) = 2 pi (psi2 - psi1) + arg(conj(G2) G1)        (mod 2 pi),
+ * so nu = (psi1 - psi2) - arg(conj(G2) G1) / (2 pi), wrapped.  psi1 - psi2 = -2 (R2 - R1) /
+ * lambda is taken from the range change over the pair,
+ *   R2 - R1 = (|d2|^2 - |d1|^2) / (R1 + R2) = e . (2 d1 + e) / (R1 + R2),
+ * e = d2 - d1 = (V - v) / PRF (both ends move linearly over the PRI): the same number as
+ * the difference of the two ~7e7-cycle phases, without the ~1e-8 cycles that their FP64
+ * rounding leaves in that difference. */
+static double bin_coord_of(const or_radar *rd, const or_platform *pf, const or_scene *sc,
+                           int64_t n, const or_echo *c1, const or_echo *c2, int n_doppler) {
+    double dt = 1.0 / rd->prf_hz;
+    double ex = (pf->v[0] - (double)sc->vx[n]) * dt;
+    double ey = (pf->v[1] - (double)sc->vy[n]) * dt;
+    double ez = (pf->v[2] - (double)sc->vz[n]) * dt;
+    double dR21 = (ex * (2.0 * c1->dx + ex) + ey * (2.0 * c1->dy + ey) + ez * (2.0 * c1->dz + ez))
+                  / (c1->R + c2->R);
+    double lambda = rd->c_mps / rd->carrier_hz;
+    double nu = -2.0 * dR21 / lambda;                        /* psi1 - psi2 */
+    double gr = c2->g_re * c1->g_re + c2->g_im * c1->g_im;   /* conj(G2) G1 */
+    double gi = c2->g_re * c1->g_im - c2->g_im * c1->g_re;
+    nu -= atan2(gi, gr) / (2.0 * OR_PI);
+    nu -= floor(nu + 0.5);
     return nu * (double)n_doppler + 0.5;
 }
 
@@ -229,7 +260,7 @@ void or_cells(const or_radar *rd, const or_platform *pf, const or_scene *sc, int
         echo_at(rd, pf, sc, n, t1, &e1);
         echo_at(rd, pf, sc, n, t2, &e2);
         double gc = gate_coord_of(rd, e1.dR);
-        double bc = bin_coord_of(rd, &e1, &e2, n_doppler);
+        double bc = bin_coord_of(rd, pf, sc, n, &e1, &e2, n_doppler);
         if (gate_coord) gate_coord[n] = gc;
         if (bin_coord) bin_coord[n] = bc;
         if (gate) gate[n] = (int32_t)floor(gc);
@@ -304,7 +335,7 @@ void or_doppler_spectra(const or_radar *rd, const or_platform *pf, const or_scen
                 echo_at(rd, pf, sc, n, t_n, &cn);   /* C_{i+1} */
                 double g = floor(gate_coord_of(rd, ci.dR));
                 if (g < 0.0 || g >= (double)G) continue;
-                int64_t k = pmod64((int64_t)floor(bin_coord_of(rd, &ci, &cn, K)), K);
+                int64_t k = pmod64((int64_t)floor(bin_coord_of(rd, pf, sc, n, &ci, &cn, K)), K);
                 int64_t cell = (int64_t)g * K + k;   /* rasterize(C_i, T, i, R_i, D_i) */
                 neu_add(&pp[cell * 4 + 0], &pp[cell * 4 + 1], ci.re);
                 neu_add(&pp[cell * 4 + 2], &pp[cell * 4 + 3], ci.im);
@@ -487,7 +518,7 @@ void or_fast_grad(const or_radar *rd, const or_platform *pf, const or_scene *sc,
             echo_at(rd, pf, sc, n, (double)(p_i + 1) / rd->prf_hz, &cn);
             double g = floor(gate_coord_of(rd, ci.dR));
             if (g < 0.0 || g >= (double)G) continue;
-            int64_t k = pmod64((int64_t)floor(bin_coord_of(rd, &ci, &cn, K)), K);
+            int64_t k = pmod64((int64_t)floor(bin_coord_of(rd, pf, sc, n, &ci, &cn, K)), K);
             const double *gt = G_T + (((size_t)u * G + (int64_t)g) * K + k) * 2;
             double dre, dim;
             dC_dz(rd, &ci, &dre, &dim);

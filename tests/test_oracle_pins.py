@@ -370,3 +370,65 @@ def test_sums_do_not_depend_on_the_thread_count():
     assert np.abs(out[0][0]).max() > 0 and np.abs(out[0][1]).max() > 0
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+# --------------------------------------------------------------------------- index coordinates
+def _decimal_coords(radar, platform, scene, idx, pulse, n_doppler):
+    """Gate coordinate dR / gate_width + N_g / 2 at `pulse` and pulse-pair bin coordinate
+    nu N_d + 1/2 of Algorithm 1 (nu = phase advance of C over the pair (pulse, pulse + 1),
+    cycles, wrapped to [-1/2, 1/2)) for the scatterers `idx`, in 60-digit decimal arithmetic
+    straight from the definitions: positions, ranges and phases psi = 2 R / lambda at both
+    pulses, and the difference psi1 - psi2 of the two phases.  The float inputs convert to
+    decimal exactly."""
+    import decimal
+    from decimal import Decimal as D
+    ctx = decimal.Context(prec=60)
+    prf, lam = D(radar.prf_hz), ctx.divide(D(radar.c_mps), D(radar.carrier_hz))
+    t0 = D(float(scene.get("t0", 0.0)))
+    org = [D(float(v)) for v in scene.get("origin", (0.0, 0.0, 0.0))]
+
+    def state(n, p):
+        t = ctx.divide(D(p), prf)
+        ts = t - t0
+        s = [org[0] + D(float(scene["x"][n])) + D(float(scene["vx"][n])) * ts,
+             org[1] + D(float(scene["y"][n])) + D(float(scene["vy"][n])) * ts,
+             org[2] + D(float(scene["z"][n])) + D(float(scene["vz"][n])) * ts]
+        P = [D(platform.p0[i]) + D(platform.v[i]) * t for i in range(3)]
+        R = ctx.sqrt(sum((P[i] - s[i]) * (P[i] - s[i]) for i in range(3)))
+        rref = D(platform.r_ref0) + D(platform.r_ref_rate) * t
+        return R, rref
+
+    gc, bc = [], []
+    for n in idx:
+        R1, rref = state(n, pulse)
+        R2, _ = state(n, pulse + 1)
+        gc.append(float(ctx.divide(R1 - rref, D(radar.gate_width_m)) + D(radar.n_gates) / 2))
+        nu = ctx.divide(2 * (R1 - R2), lam)                 # psi1 - psi2
+        nu -= (nu + D("0.5")).to_integral_value(rounding=decimal.ROUND_FLOOR)
+        bc.append(float(nu * n_doppler + D("0.5")))
+    return np.array(gc), np.array(bc)
+
+
+@pytest.mark.parametrize("pulse", [0, 1984, 4095])
+def test_index_coordinates_against_high_precision(orc, pulse):
+    """The oracle's pre-floor gate and Doppler-bin coordinates (the quantities whose floors
+    are Algorithm 1's rasterisation indices) against a 60-digit evaluation of their
+    definitions on a moving sea surface seen along the cfg1 track: gate to 1e-11, bin to
+    1e-10 (mod N_d).  A dropped velocity component, a flipped or halved phase difference,
+    or a range change taken over the wrong interval fails it; so would the rounding noise
+    of a difference of two FP64 ranges of ~8e5 m (~5e-10 gates) or of the two ~7e7-cycle
+    phases (~1e-6 bins), which the oracle's rewritten differences avoid."""
+    c = sg.config(1)
+    rd, pf, nd = c["radar"], c["platform"], c["fast"].n_doppler
+    sc = sg.sea_surface(64, 31)
+    g, b, gc, bc = orc.cells(rd, pf, sc, pulse, nd)
+    idx = np.random.Generator(np.random.PCG64(pulse + 5)).choice(sc["x"].size, 60, replace=False)
+    gx, bx = _decimal_coords(rd, pf, sc, idx, pulse, nd)
+    assert np.abs(gc[idx] - gx).max() < 1e-11
+    db = np.abs(bc[idx] - bx)
+    db = np.minimum(db, nd - db)
+    assert db.max() < 1e-10
+    assert np.array_equal(g[idx], np.floor(gx).astype(np.int64))
+    assert np.array_equal(b[idx], np.mod(np.floor(bx).astype(np.int64), nd))
+    # the scene's Doppler spreads over several bins, so the bin coordinate is exercised
+    assert np.ptp(np.mod(np.floor(bx), nd)) >= 1
