@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import scenegen as sg
-from helpers import TOL, gpu_cells, np_, rel_l2
+from helpers import TOL, check_decisions, np_, rel_l2
 
 pytestmark = pytest.mark.gpu
 PRECISIONS = ["split", "fp64"]
@@ -123,12 +123,14 @@ def test_culling_on_a_long_track(rsim, orc, precision):
              mid + 1500]
     for u in probe:
         T = np_(rsim.doppler_accumulate(rd, pf, dev, u, 1, nf, nd, precision))
-        G, B = gpu_cells(rsim, rd, pf, dev, [u * nf], nd, precision)
-        Tref = orc.doppler_spectra_cells(rd, pf, sc, u, nf, nd, G, B)
+        g, b, _, _ = check_decisions(rsim, orc, rd, pf, dev, sc, u * nf, nd, precision)
+        Tref = orc.doppler_spectra_cells(rd, pf, sc, u, nf, nd, g[None], b[None])
+        Tor = orc.doppler_spectra(rd, pf, sc, u, 1, nf, nd)
         if np.abs(Tref).max() == 0:
-            assert np.abs(T).max() == 0
+            assert np.abs(T).max() == 0 and np.abs(Tor).max() == 0
         else:
             assert rel_l2(T, Tref) <= TOL[precision]
+            assert rel_l2(T, Tor) <= TOL[precision]
     T_far = np_(rsim.doppler_accumulate(rd, pf, dev, mid - 1500, 3, nf, nd, precision))
     assert np.abs(T_far).max() == 0
     T_in = np_(rsim.doppler_accumulate(rd, pf, dev, mid, 1, nf, nd, precision))

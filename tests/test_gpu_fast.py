@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import scenegen as sg
-from helpers import TOL, gpu_cells, index_agreement, np_, rel_l2
+from helpers import TOL, check_decisions, gpu_cells, np_, rel_l2
 
 pytestmark = pytest.mark.gpu
 PRECISIONS = ["fp64", "split"]
@@ -26,23 +26,26 @@ def small():
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_spectra_parity_small(rsim, orc, small, precision):
     """256 x 256 surface on the cfg1 track; 9 updates from update 30 (several CTAs, ragged
-    sample blocks, Doppler on both sides of zero)."""
+    sample blocks, Doppler on both sides of zero).  Every update's index decisions against
+    the oracle's; the spectra against the oracle summed over the GPU's decisions and, end to
+    end, against the oracle with its own decisions, both at the path's tolerance."""
     c, sc = small
     rd, pf, fp = c["radar"], c["platform"], c["fast"]
     dev = rsim.Scatterers.from_arrays(sc)
     u0, S = 30, 9
     T = np_(rsim.doppler_accumulate(rd, pf, dev, u0, S, fp.n_fast, fp.n_doppler, precision))
-    pulses = [(u0 + s) * fp.n_fast for s in range(S)]
-    G, B = gpu_cells(rsim, rd, pf, dev, pulses, fp.n_doppler, precision)
-    for j, p in enumerate(pulses[::4]):
-        g_o, b_o, gc_o, bc_o = orc.cells(rd, pf, sc, p, fp.n_doppler)
-        index_agreement(G[4 * j], B[4 * j], gc_o, bc_o, g_o, b_o, fp.n_doppler)
-    Tref = orc.doppler_spectra_cells(rd, pf, sc, u0, fp.n_fast, fp.n_doppler, G, B)
-    err = rel_l2(T, Tref)
-    assert err <= TOL[precision], err
-    # honest end-to-end error against the oracle's own decisions (bin flips included)
+    G, B = [], []
+    for s in range(S):
+        g, b, fg, fb = check_decisions(rsim, orc, rd, pf, dev, sc, (u0 + s) * fp.n_fast,
+                                       fp.n_doppler, precision)
+        assert fg < 1e-6 and fb < 1e-6
+        G.append(g)
+        B.append(b)
+    Tref = orc.doppler_spectra_cells(rd, pf, sc, u0, fp.n_fast, fp.n_doppler, np.stack(G),
+                                     np.stack(B))
+    assert rel_l2(T, Tref) <= TOL[precision]
     Tor = orc.doppler_spectra(rd, pf, sc, u0, S, fp.n_fast, fp.n_doppler)
-    assert rel_l2(T, Tor) <= 3e-2
+    assert rel_l2(T, Tor) <= TOL[precision]
 
 
 def test_spectra_deterministic(rsim, small):
@@ -73,7 +76,8 @@ def test_single_bin_spectra_equal_regular_mode_bitwise(rsim, small):
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_simulate_fast_ragged_pulse_range(rsim, orc, small, precision):
-    """A pulse range that starts and ends mid-segment: spectra and blended pulses."""
+    """A pulse range that starts and ends mid-segment: spectra and blended pulses, against
+    the oracle with the GPU's checked decisions and end to end with its own."""
     c, sc = small
     rd, pf, fp = c["radar"], c["platform"], c["fast"]
     dev = rsim.Scatterers.from_arrays(sc)
@@ -81,12 +85,20 @@ def test_simulate_fast_ragged_pulse_range(rsim, orc, small, precision):
     T, Y = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, precision, p0)
     u0, S = rsim.spectra_range(p0, P, fp.n_fast)
     Tn = np_(T)
-    G, B = gpu_cells(rsim, rd, pf, dev, [(u0 + s) * fp.n_fast for s in range(S)], fp.n_doppler,
-                     precision)
-    Tref = orc.doppler_spectra_cells(rd, pf, sc, u0, fp.n_fast, fp.n_doppler, G, B)
+    G, B = [], []
+    for s in range(S):
+        g, b, _, _ = check_decisions(rsim, orc, rd, pf, dev, sc, (u0 + s) * fp.n_fast,
+                                     fp.n_doppler, precision)
+        G.append(g)
+        B.append(b)
+    Tref = orc.doppler_spectra_cells(rd, pf, sc, u0, fp.n_fast, fp.n_doppler, np.stack(G),
+                                     np.stack(B))
     assert rel_l2(Tn, Tref) <= TOL[precision]
     Yref = orc.synth(Tref, u0, fp.n_fast, p0, P, fp.window)
     assert rel_l2(np_(Y), Yref) <= TOL[precision]
+    Tor, Yor = orc.simulate_fast(rd, pf, sc, P, fp.n_fast, fp.n_doppler, fp.window, p0)
+    assert rel_l2(Tn, Tor) <= TOL[precision]
+    assert rel_l2(np_(Y), Yor) <= TOL[precision]
 
 
 def test_fast_mode_equals_regular_at_update_pulses(rsim, small):
@@ -119,37 +131,39 @@ def test_large_cell_grids(rsim, orc):
         T = rsim.doppler_accumulate(rd, pf, dev, 10, 2, 64, 4096, precision)
         T1 = rsim.doppler_accumulate(rd, pf, dev, 10, 2, 64, 1, precision)
         assert rel_l2(np_(T.sum(-1)), np_(T1[..., 0])) < 1e-6
-        g, b, _, _ = rsim.scatterer_cells(rd, pf, dev, 640, 4096, precision)
-        g_o, b_o, gc_o, bc_o = orc.cells(rd, pf, sc, 640, 4096)
-        index_agreement(np_(g), np_(b), gc_o, bc_o, g_o, b_o, 4096)
+        check_decisions(rsim, orc, rd, pf, dev, sc, 640, 4096, precision)
 
 
-def test_full_cfg1_sampled(rsim, orc):
+def test_full_cfg1(rsim, orc):
     """cfg1 at full size in the benchmark's launch configuration: 4.19M scatterers,
-    65 spectra of 128 x 64, 4096 pulses, split precision.  Spectra checked on 5 sampled
-    updates against the oracle (GPU decisions) -- plus the index decisions and the honest
-    end-to-end error with the oracle's own decisions; the pulses checked against the
-    oracle's post-processing of the GPU spectra."""
+    65 spectra of 128 x 64, 4096 pulses, split precision.  Every update: the index
+    decisions against the oracle's, the spectrum against the oracle summed over those
+    decisions, and end to end against the oracle with its own decisions, all at the split
+    tolerance; the pulses against the oracle's post-processing of the GPU spectra and, end
+    to end, of its own."""
     c = sg.config(1)
     rd, pf, fp, P = c["radar"], c["platform"], c["fast"], c["n_pulses"]
     sc = sg.sea_surface(c["L"], c["seed"])
     dev = rsim.Scatterers.from_arrays(sc)
     T, Y = rsim.simulate_fast(rd, pf, dev, P, fp.n_fast, fp.n_doppler, fp.window, "split")
     Tn, Yn = np_(T), np_(Y)
+    S = Tn.shape[0]
     assert Tn.shape == (65, 128, 64) and Yn.shape == (4096, 128)
-    samp = [0, 16, 32, 48, 64]
-    G, B = gpu_cells(rsim, rd, pf, dev, [u * fp.n_fast for u in samp], fp.n_doppler, "split")
-    for j, u in enumerate(samp):
-        Tref = orc.doppler_spectra_cells(rd, pf, sc, u, fp.n_fast, fp.n_doppler, G[j:j + 1],
-                                         B[j:j + 1])
-        assert rel_l2(Tn[u:u + 1], Tref) <= TOL["split"]
-    g_o, b_o, gc_o, bc_o = orc.cells(rd, pf, sc, 32 * fp.n_fast, fp.n_doppler)
-    fg, fb = index_agreement(G[2], B[2], gc_o, bc_o, g_o, b_o, fp.n_doppler)
-    assert fg < 1e-4 and fb < 1e-3
-    Tor = orc.doppler_spectra(rd, pf, sc, 32, 1, fp.n_fast, fp.n_doppler)
-    assert rel_l2(Tn[32:33], Tor) <= 3e-2
+    exempt = 0.0
+    for u in range(S):
+        g, b, fg, fb = check_decisions(rsim, orc, rd, pf, dev, sc, u * fp.n_fast, fp.n_doppler,
+                                       "split")
+        exempt += fg + fb
+        Tref = orc.doppler_spectra_cells(rd, pf, sc, u, fp.n_fast, fp.n_doppler, g[None],
+                                         b[None])
+        assert rel_l2(Tn[u:u + 1], Tref) <= TOL["split"], u
+    assert exempt / S < 1e-6
+    Tor = orc.doppler_spectra(rd, pf, sc, 0, S, fp.n_fast, fp.n_doppler)
+    assert rel_l2(Tn, Tor) <= TOL["split"]
     Yref = orc.synth(Tn.astype(np.complex128), 0, fp.n_fast, 0, P, fp.window)
     assert rel_l2(Yn, Yref) <= 1e-5
+    Yor = orc.synth(Tor, 0, fp.n_fast, 0, P, fp.window)
+    assert rel_l2(Yn, Yor) <= TOL["split"]
 
 
 def test_host_streamer_overlaps_copies_and_matches(rsim):

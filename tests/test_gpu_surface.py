@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import scenegen as sg
-from helpers import TOL, gpu_cells, np_, rel_l2
+from helpers import check_decisions, np_, rel_l2
 from oracle import surface as sf
 
 pytestmark = pytest.mark.gpu
@@ -62,10 +62,16 @@ def test_fast_mode_with_evolving_surface_matches_oracle(rsim, orc, precision):
     for s in range(S):
         t = (u0 + s) * nf / rd.prf_hz
         sc_gpu = surf.at(t)
-        G, B = gpu_cells(rsim, rd, pf, sc_gpu, [(u0 + s) * nf], nd, precision)
-        Tref = orc.doppler_spectra_cells(rd, pf, sf.scene_at(spec, t), u0 + s, nf, nd, G, B)
-        # the surfaces differ by the FP32 transforms (~1e-7 m of height): 1e-4 of phase
+        sc_or = sf.scene_at(spec, t)
+        # the surfaces differ by the FP32 transforms (~1e-7 m of height, 2e-7 gates; the
+        # velocities' error moves the bin coordinate by ~1e-8): decisions are compared
+        # outside a band of 1e-5 gates and 1e-6 bins around the oracle's cell edges
+        G, B, _, _ = check_decisions(rsim, orc, rd, pf, sc_gpu, sc_or, (u0 + s) * nf, nd,
+                                     precision, band=(1e-5, 1e-6))
+        Tref = orc.doppler_spectra_cells(rd, pf, sc_or, u0 + s, nf, nd, G[None], B[None])
+        # ~1e-7 m of height is ~1e-4 of phase
         assert rel_l2(np_(T)[s], Tref[0]) <= 1e-3
+        assert rel_l2(np_(T)[s], orc.doppler_spectra(rd, pf, sc_or, u0 + s, 1, nf, nd)[0]) <= 1e-3
     # the surface moves: the spectra differ from those of the frozen t = 0 surface moved
     # along straight lines
     frozen = rsim.Scatterers.from_arrays(sg.sea_surface(128, 21))
