@@ -9,8 +9,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def pytest_addoption(parser):
+    parser.addoption("--mutation", action="store_true", default=False,
+                     help="run the oracle pins' mutation sweep (tests marked mutation)")
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built librsim")
+    config.addinivalue_line("markers", "mutation: mutation sweep of the oracle's pins "
+                                       "(opt-in: --mutation)")
     _ensure_library()
 
 
@@ -31,6 +38,11 @@ def _ensure_library():
 
 
 def pytest_collection_modifyitems(config, items):
+    if not config.getoption("--mutation"):
+        skip_mut = pytest.mark.skip(reason="mutation sweep: opt-in with --mutation")
+        for item in items:
+            if "mutation" in item.keywords:
+                item.add_marker(skip_mut)
     try:
         import torch
         has_gpu = torch.cuda.is_available()
