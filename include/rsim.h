@@ -53,9 +53,12 @@
  *     consecutive scatterers are spatially close (e.g. a row-major grid),
  *     because each block of rsim_block_scatterers() (1024) consecutive
  *     scatterers shares one FP64 reference point.
- *   - Accumulation is exact: contributions are summed in 64-bit fixed point
- *     (2^-32 resolution, |sum| < 2^31 per cell), so results are bitwise
- *     reproducible run to run regardless of scheduling.
+ *   - Accumulation is deterministic fixed point: each contribution is rounded to
+ *     a multiple of 2^-32 (a 64-bit integer) and the integers are summed, so results
+ *     are bitwise reproducible run to run regardless of scheduling.  Valid while every
+ *     contribution's |re|, |im| < 2^30 and every cell's sum stays within +-2^31; the
+ *     library does not check this, and beyond it the values saturate or wrap silently
+ *     (sea-surface facets give contributions of order sqrt(nrcs * area), a few units).
  */
 #ifndef RSIM_H
 #define RSIM_H
@@ -395,10 +398,12 @@ rsim_status rsim_direct_sum_backward(const rsim_radar *radar, const rsim_platfor
  * that loads the library until the process exits), so
  * rsim_workspace_size(n_updates, n_gates, n_doppler) must be <= 16 MiB, else
  * RSIM_ERR_WORKSPACE.  Nothing is allocated: no cudaMalloc/cudaFree or allocating library
- * call.  The first call on each device looks the array's device address up
- * (cudaGetSymbolAddress, with that device current): make that first call before any
- * stream capture.  All calls on a device share the array and each clears it on entry, so
- * calls that may overlap on the GPU race; order them (one stream, or events). */
+ * call.  The first call in each CUDA context looks the array's device address up
+ * (cudaGetSymbolAddress, with that context current) and keeps it under the context's ID,
+ * so a non-primary context, or a context made after cudaDeviceReset, gets its own address:
+ * make each context's first call before any stream capture.  All calls in a context share
+ * the array and each clears it on entry, so calls that may overlap on the GPU race; order
+ * them (one stream, or events). */
 rsim_status rsim_doppler_accumulate_noalloc(const rsim_radar *radar,
                                             const rsim_platform *platform,
                                             const rsim_scatterers *scat, int64_t update0,

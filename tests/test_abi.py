@@ -93,6 +93,21 @@ def test_workspace_errors(L):
     assert b"workspace" in lib.rsim_last_error()
 
 
+def test_noalloc_size_limit_is_checked_on_the_host(L):
+    """The allocation-free pass rejects a request just over its 16 MiB built-in scratch
+    (129 updates x 128 gates x 64 bins x 16 B) before any CUDA call, so this runs without a
+    GPU; exactly 16 MiB (128 updates) is accepted (checked on a GPU in test_zz_no_alloc)."""
+    B = ctypes.byref
+    rd, pf, sc = _structs(L)
+    lib = L.lib
+    assert lib.rsim_workspace_size(128, 128, 64) == 16 << 20
+    assert lib.rsim_doppler_accumulate_noalloc(B(rd), B(pf), B(sc), 0, 129, 64, 64, 1, 0x1000,
+                                               None) == 5
+    assert b"built-in" in lib.rsim_last_error()
+    assert lib.rsim_doppler_accumulate_noalloc(None, B(pf), B(sc), 0, 4, 64, 64, 1, 0x1000,
+                                               None) == 1
+
+
 def test_empty_work_is_a_noop(L):
     B = ctypes.byref
     rd, pf, sc = _structs(L, n=0)
