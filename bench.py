@@ -37,15 +37,15 @@ import scenegen as sg  # noqa: E402
 
 METRIC = "scatterer-pulse contribs/s & fast-mode IQ pulses/s at stated err vs FP64, % roofline"
 UNIT = "IQ pulses/s"
-# FP32-pipe operations of the split-path evaluation of one scatterer at one update
-# (two-way range excess, gate, antenna angle, amplitude exponent, phase, pulse-pair
-# Doppler bin, cell key), counted from the formulation; plus 3 MUFU (ex2, sin, cos).
-OPS_PER_UPDATE = 78
-OPS_PER_PULSE_REGULAR = 50
-SMS = 152
-LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+# FP32 operations of one scatterer at one update in the split-path formulation, counted from
+# its arithmetic: position at t 3, range excess 9, gate 4, amplitude (beam series, range
+# factor) 12, phase 8, C 3, pulse-pair Doppler bin 11, rasterising C into its cell 2 (re, im);
+# plus 3 MUFU operations (ex2, sin, cos).  Regular mode: no Doppler bin (41 + 3 MUFU).
+OPS_PER_UPDATE = 52
+MUFU_PER_UPDATE = 3
+OPS_PER_PULSE_REGULAR = 41
 L2_FLUSH_BYTES = 512 << 20
+PEAK_KINDS = {"ffma": 0, "ffma2": 1, "mufu_ex2": 2, "mufu_sin": 3, "mufu_cos": 4, "dfma": 5}
 
 
 def log(*a):
@@ -118,6 +118,71 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- ALU peaks
+def measure_alu_peaks(torch, dev_name):
+    """Throughput of the arithmetic pipes on this GPU (libalupeaks.so microbenchmarks: many
+    independent chains of one instruction kind on every SM, CUDA events), as lane-operations
+    per SM and clock (the clock the kernel ran at, from clock64 against the global timer), so
+    that the peak can be scaled to the clock sampled while the timed kernel ran."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2408_11472_gb300", "libalupeaks.so")
+    lib = ctypes.CDLL(path)
+    f = lib.alu_peak_run
+    f.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 2 + [ctypes.POINTER(ctypes.c_double)] * 3 \
+        + [ctypes.POINTER(ctypes.c_int)]
+    f.restype = ctypes.c_int
+    sms = torch.cuda.get_device_properties(dev_name).multi_processor_count
+    blocks_per_sm = 4
+    sink = torch.zeros(blocks_per_sm * sms, dtype=torch.float32, device=dev_name)
+    tim = torch.zeros(8, dtype=torch.int64, device=dev_name)
+    iters = {"ffma": 16000, "ffma2": 8000, "mufu_ex2": 2000, "mufu_sin": 2000, "mufu_cos": 2000,
+             "dfma": 500}
+    out = {}
+    for name, kind in PEAK_KINDS.items():
+        ops, mhz, per_clk = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int()
+        torch.cuda.synchronize()
+        rc = f(kind, blocks_per_sm, iters[name], 5, ctypes.c_void_p(sink.data_ptr()),
+               ctypes.c_void_p(tim.data_ptr()), ctypes.byref(ops), ctypes.byref(mhz),
+               ctypes.byref(per_clk), ctypes.byref(n))
+        if rc != 0:
+            raise RuntimeError("alu_peak_run(%s) failed: CUDA error %d" % (name, rc))
+        out[name] = {"ops_per_s": ops.value, "sm_mhz": round(mhz.value, 1),
+                     "ops_per_clk_per_sm": round(per_clk.value, 2)}
+    out["sms"] = sms
+    return out
+
+
+def alu_roofline(peaks, sm_mhz, units, launch_ms):
+    """Roofline of the summation kernel from the measured pipe rates at the sampled clock."""
+    sms = peaks["sms"]
+    fp32_clk = max(peaks["ffma"]["ops_per_clk_per_sm"], peaks["ffma2"]["ops_per_clk_per_sm"])
+    # the MUFU pipe time of one unit (one ex2, one sine, one cosine) at the measured rates
+    mufu_cyc = (1.0 / peaks["mufu_ex2"]["ops_per_clk_per_sm"]
+                + 1.0 / peaks["mufu_sin"]["ops_per_clk_per_sm"]
+                + 1.0 / peaks["mufu_cos"]["ops_per_clk_per_sm"])
+    clk = sm_mhz * 1e6
+    fp32_peak = fp32_clk * sms * clk
+    mufu_peak = MUFU_PER_UPDATE / mufu_cyc * sms * clk
+    t = launch_ms / 1e3
+    fp32 = units * OPS_PER_UPDATE / t
+    mufu = units * MUFU_PER_UPDATE / t
+    return {
+        "achieved": round(fp32 / 1e12, 3), "peak": round(fp32_peak / 1e12, 3), "unit": "Top/s",
+        "frac": round(fp32 / fp32_peak, 4),
+        "peak_basis": ("measured: %.1f FP32 lane-ops per SM and clock (max of the FFMA and "
+                       "FFMA2 microbenchmarks) x %d SMs x %.0f MHz (median SM clock sampled "
+                       "during the timed region)" % (fp32_clk, sms, sm_mhz)),
+        "mufu": {"ops_per_unit": MUFU_PER_UPDATE, "achieved": round(mufu / 1e12, 4),
+                 "peak": round(mufu_peak / 1e12, 4), "unit": "Top/s",
+                 "frac": round(mufu / mufu_peak, 4),
+                 "peak_basis": "measured MUFU rates per SM and clock (ex2 %.1f, sin %.1f, cos "
+                               "%.1f): one unit's ex2 + sine + cosine occupy the pipe %.4f "
+                               "clocks" % (peaks["mufu_ex2"]["ops_per_clk_per_sm"],
+                                           peaks["mufu_sin"]["ops_per_clk_per_sm"],
+                                           peaks["mufu_cos"]["ops_per_clk_per_sm"], mufu_cyc)}}
 
 
 # --------------------------------------------------------------------------- oracle leg
@@ -207,6 +272,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev_name)
     stream = torch.cuda.current_stream()
 
+    peaks = measure_alu_peaks(torch, dev_name)
+
     def step():
         T.zero_()
         rsim.doppler_accumulate(rd, pf, dev, 0, S, fp.n_fast, fp.n_doppler, args.precision,
@@ -216,9 +283,11 @@ def main():
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()                      # sampler warms up during the untimed warm-up
+    torch.cuda.nvtx.range_push("warm-up")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if clocks:
         time.sleep(0.3)
 
@@ -227,6 +296,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed steps")
     t0 = time.perf_counter()
     t0_epoch = time.time()
     for e0, e1, e2 in ev:
@@ -240,6 +310,7 @@ def main():
         e2.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
     t1_epoch = time.time()
@@ -257,15 +328,18 @@ def main():
     acc_mean_ms = statistics.mean(acc_ms)
 
     units = N * S                           # scatterer-updates per launch
-    achieved = units * OPS_PER_UPDATE / (acc_mean_ms / 1e3) / 1e12
-    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "accumulate_split_kernel<DOPPLER=true>",
-                "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "ops_per_unit": OPS_PER_UPDATE, "units_per_launch": units,
-                "launch_ms": round(acc_mean_ms, 4),
-                "hbm_bytes_per_launch_algorithmic": N * 28,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock), 1 op/lane/clk"}
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks["ffma2"]["sm_mhz"]
+    roofline = {"bound": "alu", "kernel": "accumulate_split_kernel<DOPPLER=true>"}
+    roofline.update(alu_roofline(peaks, sm_mhz, units, acc_mean_ms))
+    roofline.update({"traffic": None, "ops_per_unit": OPS_PER_UPDATE,
+                     "ops_basis": "FP32 operations of one scatterer-update counted from the "
+                                  "split-path formulation (position 3, range 9, gate 4, "
+                                  "amplitude 12, phase 8, C 3, pulse-pair bin 11, rasterise 2)",
+                     "units_per_launch": units, "launch_ms": round(acc_mean_ms, 4),
+                     "launch_ms_basis": "CUDA events around the summation call (workspace "
+                                        "clear + kernel + conversion) on its stream",
+                     "hbm_bytes_per_launch_algorithmic": N * 28,
+                     "alu_peaks_measured": peaks})
     prof_traffic = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof_traffic):
         try:
@@ -287,7 +361,10 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_name)
+        torch.cuda.nvtx.range_push("extras")
+        extras = run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_name,
+                            peaks, sm_mhz)
+        torch.cuda.nvtx.range_pop()
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -333,7 +410,8 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_name):
+def run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_name, peaks,
+               sm_mhz):
     out = {}
     N = dev.n
     # -- end to end through the public API with host buffers (pinned), copies timed.
@@ -435,10 +513,15 @@ def run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_na
     e1.record(stream)
     torch.cuda.synchronize()
     t_fast = e0.elapsed_time(e1) / 1e3
+    sms = peaks["sms"]
+    fp32_clk = max(peaks["ffma"]["ops_per_clk_per_sm"], peaks["ffma2"]["ops_per_clk_per_sm"])
+    reg_peak = fp32_clk * sms * sm_mhz * 1e6
     out["regular_mode"] = {"scatterer_pulse_contribs_per_s": round(reg_rate, 1),
                            "pulses": Pr, "ms": round(t_reg * 1e3, 3),
-                           "roofline_frac_alu": round(reg_rate * OPS_PER_PULSE_REGULAR /
-                                                      (SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6), 4)}
+                           "ops_per_unit": OPS_PER_PULSE_REGULAR,
+                           "roofline_frac_alu": round(reg_rate * OPS_PER_PULSE_REGULAR / reg_peak, 4),
+                           "peak_basis": "measured FP32 peak at %.0f MHz, as the bench "
+                                         "roofline" % sm_mhz}
     out["fast_vs_regular"] = {
         "fast_equivalent_contribs_per_s": round(N * P / t_fast, 1),
         "regular_contribs_per_s": round(reg_rate, 1),
@@ -448,9 +531,15 @@ def run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_na
                             "note": "end-to-end on the full workload, bin/gate flips included"}
     # -- the FP64 oracle on the host cores, bounded sample of the same workload.
     try:
+        import oracle
         v, cores, desc, secs = oracle_fast_sample(rd, pf, scene, P, fp)
+        v1, c1, desc1, secs1 = oracle_fast_sample(rd, pf, scene, P, fp, target_s=8.0, threads=1)
+        oracle.Oracle(cores)                 # restore the thread count for later users
         out["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": cores,
-                               "kind": "oracle", "sample": desc, "seconds": round(secs, 2)}
+                               "kind": "oracle", "sample": desc, "seconds": round(secs, 2),
+                               "compiler": " ".join([oracle.CC] + oracle.CFLAGS),
+                               "one_core": {"value": round(v1, 3), "unit": UNIT, "cores": c1,
+                                            "sample": desc1, "seconds": round(secs1, 2)}}
     except Exception as e:  # the oracle needs gcc on the host
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                "sample": "failed: %s" % e}

@@ -35,14 +35,31 @@ import numpy as np
 
 import scenegen as sg
 
-SMS = 152
-LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-ALU_PEAK_OPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6      # 1 FP32-pipe op / lane / clock
-FP64_PEAK_FLOPS = SMS * 2 * 2 * SM_MAX_MHZ * 1e6          # 2 DFMA / clock / SM, 2 flop each
-OPS_PER_UPDATE = 78
-OPS_PER_PULSE_REGULAR = 50
+from bench import OPS_PER_PULSE_REGULAR, OPS_PER_UPDATE  # noqa: E402  (counted there)
+
 L2_FLUSH_BYTES = 512 << 20
+_PEAKS = {}
+
+
+def _alu_peaks(torch):
+    """Measured pipe rates of this GPU (bench.measure_alu_peaks), once per process."""
+    if not _PEAKS:
+        import bench
+        _PEAKS.update(bench.measure_alu_peaks(torch, "cuda:%d" % torch.cuda.current_device()))
+    return _PEAKS
+
+
+def _fp32_peak_ops(torch):
+    """FP32 lane-operations per second: measured per SM and clock, at the clock the
+    microbenchmark ran at."""
+    p = _alu_peaks(torch)
+    per_clk = max(p["ffma"]["ops_per_clk_per_sm"], p["ffma2"]["ops_per_clk_per_sm"])
+    return per_clk * p["sms"] * p["ffma2"]["sm_mhz"] * 1e6
+
+
+def _fp64_peak_flops(torch):
+    p = _alu_peaks(torch)
+    return 2.0 * p["dfma"]["ops_per_clk_per_sm"] * p["sms"] * p["dfma"]["sm_mhz"] * 1e6
 
 
 def _timed(torch, fn, reps, flush=None):
@@ -135,11 +152,12 @@ def run_cfg0(torch, rsim, args):
     line["ms_per_call"] = res["fp64"]["ms_per_call"]
     line["roofline"] = {"bound": "fp64", "note": "FP64 path: geometry, phase and pattern in FP64",
                         "achieved_contribs_per_s": res["fp64"]["contribs_per_s"],
-                        "fp64_peak_tflops": round(FP64_PEAK_FLOPS / 1e12, 3)}
+                        "fp64_peak_tflops": round(_fp64_peak_flops(torch) / 1e12, 3),
+                        "peak_basis": "measured DFMA microbenchmark"}
     line["split"] = {"ms_per_call": res["split"]["ms_per_call"],
                      "contribs_per_s": res["split"]["contribs_per_s"],
                      "roofline_frac_alu": round(N * P * OPS_PER_PULSE_REGULAR /
-                                                (res["split"]["ms_per_call"] / 1e3) / ALU_PEAK_OPS, 4)}
+                                                (res["split"]["ms_per_call"] / 1e3) / _fp32_peak_ops(torch), 4)}
     line["rel_l2_vs_oracle"] = {"fp64": _rl2(res["fp64"]["Y"], Yo),
                                 "split": _rl2(res["split"]["Y"], Yo)}
     line["cpu_baseline"] = {"value": round(N * P / secs, 1), "unit": "contribs/s", "cores": cores,
@@ -252,7 +270,7 @@ def run_cfg2(torch, rsim, args):
         line[prec]["rel_l2_vs_oracle"] = {"spectra": _rl2(o["T"], To), "iq": _rl2(o["Y"], Yo),
                                           "spectra_same_cells": same_cells[prec]}
     line["split"]["roofline_frac_alu"] = round(
-        N * S * OPS_PER_UPDATE / (out["split"]["accumulate_ms"] / 1e3) / ALU_PEAK_OPS, 4)
+        N * S * OPS_PER_UPDATE / (out["split"]["accumulate_ms"] / 1e3) / _fp32_peak_ops(torch), 4)
     line["split_vs_fp64_gpu"] = {"rel_l2_spectra": _rl2(out["split"]["T"], out["fp64"]["T"]),
                                  "rel_l2_iq": _rl2(out["split"]["Y"], out["fp64"]["Y"])}
     line["residual_error_split_vs_fp64_per_scatterer"] = dict(hist, sample="first %d scatterers" % n_s)

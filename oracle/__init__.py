@@ -36,6 +36,11 @@ _lock = threading.Lock()
 WINDOWS = {"sqrt_linear": 0, "sqrt_raised_cosine": 1, "linear": 2}
 
 
+# compiler and flags of the C oracle (reported beside its timings)
+CC = "gcc"
+CFLAGS = ["-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off"]
+
+
 def build(force: bool = False) -> str:
     """Compile the C oracle with gcc (OpenMP, IEEE double, no FMA contraction)."""
     with _lock:
@@ -43,8 +48,7 @@ def build(force: bool = False) -> str:
                 and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
             return _LIB
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+        cmd = [CC] + CFLAGS + ["-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB

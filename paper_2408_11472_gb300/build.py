@@ -1,8 +1,10 @@
 """Build librsim.so (the C ABI over the sm_103a kernels) in-tree with nvcc.
 
 Each translation unit is compiled in parallel for ``sm_103a`` only, then linked
-into ``paper_2408_11472_gb300/librsim.so`` (static CUDA runtime).  Rebuilds
-only when a source or header is newer than the library.
+into ``paper_2408_11472_gb300/librsim.so`` (static CUDA runtime).  The pipe
+microbenchmarks the benchmark's roofline divides by are built beside it as
+``libalupeaks.so``.  Rebuilds only when a source or header is newer than the
+library.
 
     python paper_2408_11472_gb300/build.py [--force] [--verbose-ptxas]
 """
@@ -21,6 +23,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build", "rsim")
 LIB = os.path.join(PKG, "librsim.so")
+# measurement-only microbenchmarks of the arithmetic pipes (the roofline's denominators)
+PEAKS_SRC = os.path.join(CSRC, "peaks", "alu_peaks.cu")
+PEAKS_LIB = os.path.join(PKG, "libalupeaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,10 +46,11 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    return (all(os.path.getmtime(d) <= t for d in _deps())
+            and os.path.getmtime(PEAKS_SRC) <= os.path.getmtime(PEAKS_LIB))
 
 
 def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = False) -> str:
@@ -57,6 +63,10 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = False)
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]
     procs, objs = [], []
+    peaks_tmp = PEAKS_LIB + ".tmp%d" % os.getpid()
+    procs.append((PEAKS_SRC, subprocess.Popen(
+        [nvcc] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC,
+                         "-o", peaks_tmp], stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for src in sources():
         obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
         objs.append(obj)
@@ -73,6 +83,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = False)
     if failed:
         msg = "\n".join("== %s ==\n%s" % (s, t) for s, t in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
+    os.replace(peaks_tmp, PEAKS_LIB)
     tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
     os.replace(tmp, LIB)

@@ -383,7 +383,6 @@ struct SampleF {
     int gint;
 };
 
-__device__ __forceinline__ int sample_active(const SplitConst& s) { return __float_as_int(s.e.y); }
 __device__ __forceinline__ int sample_index(const SplitConst& s) { return __float_as_int(s.e.y); }
 
 // After the activity test: the entry carries its sample index and output slice instead.
