@@ -116,6 +116,33 @@ def test_c_oracle_matches_numpy_bruteforce_with_table(orc):
     assert np.abs(Yg - Yc).max() > 1e-3 * np.abs(Yc).max()
 
 
+def test_pulse_pair_bin_carries_the_pattern_phase_change(orc):
+    """Algorithm 1 takes D_i from arg(conj(C_{i+1}) C_i), and C carries the pattern, so the
+    pattern's own phase change between the facet's directions at the two pulses is part of
+    the Doppler.  A table whose phase ramps in u (G = e^{j 2 pi kappa u}, ~0.2 bins of phase
+    change per PRI along the track): the oracle's bin coordinate against the numpy
+    restatement's literal angle of C_{i+1} conj(C_i), to 2e-5 bins (that difference of two
+    ~7e7-cycle phases carries ~1e-6); the pattern's share is ~0.2 bins, so a dropped or
+    reversed pattern term fails."""
+    kappa, nd = 1.29e4, 32
+    tab = _table(lambda u, v: np.exp(2j * np.pi * kappa * u) + 0.0 * v, -2e-4, -2e-4, 4e-6, 4e-6,
+                 101, 101)
+    rd = sg.RadarParams(antenna=tab)
+    pf = sg.nadir_track(96)
+    sc = sg.sea_surface(40, 22)
+    for p in (0, 47, 95):
+        _, _, _, bc = orc.cells(rd, pf, sc, p, nd)
+        C1, _, _ = bf.echo(rd, pf, sc, p / rd.prf_hz)
+        C2, _, _ = bf.echo(rd, pf, sc, (p + 1) / rd.prf_hz)
+        lit = np.angle(C2 * np.conj(C1)) / (2 * np.pi) * nd + 0.5
+        d = np.mod(bc - lit, nd)
+        assert np.minimum(d, nd - d).max() < 2e-5
+        _, _, _, bc_g = orc.cells(dataclasses.replace(rd, antenna=None), pf, sc, p, nd)
+        d = np.mod(bc - bc_g, nd)
+        share = np.minimum(d, nd - d)
+        assert 0.1 < share.min() and share.max() < 0.3
+
+
 def test_gradient_with_table_vs_central_differences(orc):
     rd = sg.RadarParams(antenna=sg.antenna_table(11, n=65, half_width=0.01))
     P, nf, nd = 128, 64, 64
