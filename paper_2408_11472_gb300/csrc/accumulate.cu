@@ -73,9 +73,19 @@ __device__ __forceinline__ void chunk_ref(const Scat& sc, int64_t chunk0, float&
     cy = __ldg(sc.y + mid);
 }
 
+// dt Q, Q = P(t0) - c: the platform at the set's epoch t0 relative to the CTA reference point
+// (cx, cy, 0), times the PRI (the constant part of dt D(t) in the pulse-pair range change).
+__device__ __forceinline__ float3 chunk_dq(const Model& m, const double* p0, double t0, float cx,
+                                           float cy) {
+    const double dt = m.inv_prf;
+    return make_float3((float)(dt * (platform_coord(m, p0, 0, t0) - (double)cx)),
+                       (float)(dt * (platform_coord(m, p0, 1, t0) - (double)cy)),
+                       (float)(dt * platform_coord(m, p0, 2, t0)));
+}
+
 __device__ __forceinline__ ItemF item_split(const Model& m, float x, float y, float z, float vx,
                                             float vy, float vz, float nrcs, float cx, float cy,
-                                            float area) {
+                                            float area, float3 dq) {
     ItemF it;
     it.lx0 = x - cx;
     it.ly0 = y - cy;
@@ -89,18 +99,20 @@ __device__ __forceinline__ ItemF item_split(const Model& m, float x, float y, fl
     const float c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
     const float ex = fmaf(-vx, m.dt_f, m.ep[0]), ey = fmaf(-vy, m.dt_f, m.ep[1]);
     const float ez = fmaf(-vz, m.dt_f, m.ep[2]);
-    it.gam = fmaf(it.lx0, ex, fmaf(it.ly0, ey, fmaf(z, ez, c1)));
-    it.beta = fmaf(vx, ex, fmaf(vy, ey, vz * ez));
+    // gam = l0.e + c1 + dt (Q.v), beta = v.e + e_p.v  (see ItemF)
+    it.gam = fmaf(it.lx0, ex, fmaf(it.ly0, ey, fmaf(z, ez, c1))) +
+             fmaf(dq.x, vx, fmaf(dq.y, vy, dq.z * vz));
+    it.beta = fmaf(vx, ex, fmaf(vy, ey, vz * ez)) + epv;
     return it;
 }
 
 template <int IT>
 __device__ __forceinline__ void items_split(const Model& m, const RawT<IT>& r, float cx, float cy,
-                                            float area, ItemF (&it)[IT]) {
+                                            float area, float3 dq, ItemF (&it)[IT]) {
 #pragma unroll
     for (int q = 0; q < IT; ++q)
         it[q] = item_split(m, r.x[q], r.y[q], r.z[q], r.vx[q], r.vy[q], r.vz[q], r.s[q], cx, cy,
-                           area);
+                           area, dq);
 }
 
 __device__ __forceinline__ void items_fp64(const Raw& r, double area, ItemD (&it)[kItems]) {
@@ -194,10 +206,13 @@ struct ChunkCtx {
 // merged and single additions does not change the result's determinism.
 __host__ __device__ constexpr int queue_len(int items) { return 64 * items; }  // entries per warp; flushed before it can overflow
 
+// The FP64 constants of the exact re-decision are made here, per queued item, from the
+// entry's sample index: the queue is rare, so they are not tabulated for every sample.
 template <bool DOPPLER, bool ANT>
-__device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t chunk0, float cx,
-                                         float cy, float area, const SplitConst* tab,
-                                         const Fp64Const* tab64, const int* queue, int n) {
+__device__ __noinline__ void flush_queue(const Model& m, const Schedule& sch, const Scat& sc,
+                                         const double* p0, int64_t chunk0, float cx, float cy,
+                                         float area, float3 dq, const SplitConst* tab,
+                                         const int* queue, int n) {
     for (int e = threadIdx.x & 31; e < n; e += 32) {
         const int code = queue[e];
         const int i = code & 0xffff, j = code >> 16;
@@ -206,11 +221,12 @@ __device__ __noinline__ void flush_queue(const Model& m, const Scat& sc, int64_t
         const float x = __ldg(sc.x + idx), y = __ldg(sc.y + idx);
         const ItemF it = item_split(m, x, y, __ldg(sc.z + idx), __ldg(sc.vx + idx),
                                     __ldg(sc.vy + idx), __ldg(sc.vz + idx), __ldg(sc.nrcs + idx),
-                                    cx, cy, area);
+                                    cx, cy, area, dq);
         const SampleF k = load_sample(tab[j]);
+        const Fp64Const k64 = make_fp64_const(m, p0, sc.t0, sample_pulse(sch, sample_index(tab[j])));
         float re, im;
         int f;
-        const int key = eval_split<DOPPLER, true, false, ANT>(m, k, it, re, im, f, &tab64[j], x, y);
+        const int key = eval_split<DOPPLER, true, false, ANT>(m, k, it, re, im, f, &k64, x, y);
         if (key >= 0) emit_cell(sample_out(tab[j]), key, re, im);
     }
     __syncwarp();
@@ -224,7 +240,6 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
     constexpr int kQueue = queue_len(IT);
     static_assert(TH >= kTab && TH % 32 == 0, "CTA shape");
     __shared__ SplitConst tab[kTab];
-    __shared__ Fp64Const tab64[kTab];
     __shared__ float s_red[2];
     __shared__ int s_cnt[TH / 32];
     __shared__ int s_queue[TH / 32][kQueue];
@@ -234,6 +249,7 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
     int* const queue = s_queue[threadIdx.x >> 5];
     float cx, cy;
     chunk_ref(sc, cx_.chunk0, cx, cy);
+    const float3 dq = chunk_dq(m, cx_.p0, sc.t0, cx, cy);
     static_assert(IT % 2 == 0, "items are evaluated in pairs");
     ItemF2 it2[IT / 2];  // the thread's scatterers, paired for the .f32x2 evaluation
     {
@@ -241,7 +257,7 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
         RawT<IT> r;
         load_raw(sc, base, r);
         ItemF it[IT];
-        items_split(m, r, cx, cy, cx_.area, it);
+        items_split(m, r, cx, cy, cx_.area, dq, it);
 #pragma unroll
         for (int p = 0; p < IT / 2; ++p) it2[p] = pack_items(it[2 * p], it[2 * p + 1]);
         chunk_bounds(r, cx, cy, base, sc.n, s_red);
@@ -261,7 +277,6 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             SplitConst kc = make_split_const(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
             set_sample_slot(kc, s, cx_.ws + (int64_t)s * cells * 2);
             tab[slot] = kc;
-            tab64[slot] = make_fp64_const(m, cx_.p0, sc.t0, pulse);
         }
         __syncthreads();
         int nq = 0;  // entries in this warp's queue (warp-uniform)
@@ -293,13 +308,15 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             warp_reduce_emit<float, IT>(key, re, im, sample_out(tab[j]));
             if (nq > kQueue - 32 * IT) {  // room for one more sample's worth
                 __syncwarp();
-                flush_queue<DOPPLER, ANT>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
+                flush_queue<DOPPLER, ANT>(m, sch, sc, cx_.p0, cx_.chunk0, cx, cy, cx_.area, dq, tab,
+                                          queue, nq);
                 nq = 0;
             }
         }
         if (nq > 0) {  // before the table is rebuilt
             __syncwarp();
-            flush_queue<DOPPLER, ANT>(m, sc, cx_.chunk0, cx, cy, cx_.area, tab, tab64, queue, nq);
+            flush_queue<DOPPLER, ANT>(m, sch, sc, cx_.p0, cx_.chunk0, cx, cy, cx_.area, dq, tab,
+                                      queue, nq);
         }
     }
 }
@@ -483,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
         float cx, cy;
         chunk_ref(sc, chunk0, cx, cy);
         ItemF it[kItems];
-        items_split(m, r, cx, cy, (float)m.area, it);
+        items_split(m, r, cx, cy, (float)m.area, chunk_dq(m, m.p0, sc.t0, cx, cy), it);
         const SampleF k = load_sample(make_split_const(m, m.p0, sc.t0, pulse, cx, cy, 0.f, 0.f));
         const Fp64Const k64 = make_fp64_const(m, m.p0, sc.t0, pulse);
 #pragma unroll
@@ -543,7 +560,7 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
     {
         Raw r;
         load_raw(sc, base, r);
-        items_split(m, r, cx, cy, (float)m.area, it);
+        items_split(m, r, cx, cy, (float)m.area, chunk_dq(m, m.p0, sc.t0, cx, cy), it);
         chunk_bounds(r, cx, cy, base, sc.n, s_red);
 #pragma unroll
         for (int q = 0; q < kItems; ++q) { sig[q] = r.s[q]; xo[q] = r.x[q]; yo[q] = r.y[q]; }

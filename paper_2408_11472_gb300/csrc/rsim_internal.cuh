@@ -373,13 +373,14 @@ struct __align__(16) SplitConst {
     float4 d;   // beam_k / D_z^2, K0 = M . e_p as hi + lo (M = D + e_p/2), -n_doppler 2 / (lambda R_c)
     float4 e;   // floor of the gate coordinate of c (int bits); active flag, then the sample
                 // index (int bits); the sample's workspace slice (pointer bits, lo + hi)
-    float4 f;   // D dt (x, y, z) with dt = 1 / PRF; band of the FP32 gate decision
+    float4 f;   // beam series offsets qA0 = (D_x^2 + D_y^2) beam_k / D_z^2 and
+                // qA1 = 2 R_c beam_k / D_z^2; unused; band of the FP32 gate decision
 };
 
 // Register copy of one table entry.
 struct SampleF {
     float t, Dx, Dy, Dz, ux, uy, uz, h, invRc, gfrac_h, psic, l2kappa, kq, K0hi, K0lo, kbin;
-    float dtDx, dtDy, dtDz, gthr;
+    float qA0, qA1, gthr;
     int gint;
 };
 
@@ -409,7 +410,7 @@ __device__ __forceinline__ SampleF load_sample(const SplitConst& s) {
     k.ux = b.x; k.uy = b.y; k.uz = b.z; k.h = b.w;
     k.invRc = c.x; k.gfrac_h = c.y; k.psic = c.z; k.l2kappa = c.w;
     k.kq = d.x; k.K0hi = d.y; k.K0lo = d.z; k.kbin = d.w;
-    k.dtDx = f.x; k.dtDy = f.y; k.dtDz = f.z; k.gthr = f.w;
+    k.qA0 = f.x; k.qA1 = f.y; k.gthr = f.w;
     k.gint = __float_as_int(s.e.x);
     return k;
 }
@@ -440,11 +441,12 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, const dou
     // FP64 difference; beam_k / D_z^2 in FP32 (a float constant either way)
     const float xref = (float)((rref - Rc) * inv);
     const float invDz = 1.0f / (float)Dz;
+    const float kq = m.beam_k_f * invDz * invDz;
     SplitConst k;
     k.a = make_float4((float)ts, (float)Dx, (float)Dy, (float)Dz);
     k.b = make_float4((float)(Dx * inv), (float)(Dy * inv), (float)(Dz * inv), (float)(0.5 * inv));
     k.c = make_float4((float)inv, (float)(G - Gi - 0.5), (float)psi, 2.0f * kInvLn2F * log1pf(xref));
-    k.d = make_float4(m.beam_k_f * invDz * invDz, K0hi, (float)(K0 - (double)K0hi),
+    k.d = make_float4(kq, K0hi, (float)(K0 - (double)K0hi),
                       (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
     const double gi = fmax(fmin(Gi, 1.0e9), -1.0e9);
     k.e = make_float4(__int_as_float((int)gi),
@@ -452,17 +454,18 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, const dou
     // an item inside the window has |gate coordinate - gi| <= max(|gi|, |n_gates - gi|): the
     // FP32 error of its coordinate grows with that bound (out-of-window items need no band)
     const double gspan = fmax(fabs(gi), fabs((double)m.n_gates - gi)) + 2.0;
-    k.f = make_float4((float)(Dx * dt), (float)(Dy * dt), (float)(Dz * dt),
-                      (float)(0.5 - (double)kGateEps - (double)kEpsSlope * gspan));
+    k.f = make_float4((float)((Dx * Dx + Dy * Dy) * (double)kq), (float)(2.0 * Rc * (double)kq),
+                      0.f, (float)(0.5 - (double)kGateEps - (double)kEpsSlope * gspan));
     return k;
 }
 
 // Scatterer registers of the split path (positions relative to the CTA reference point).
-// c1 = dt (e_p . v) - dt^2 |v|^2 / 2 is the part of the pulse-pair range change that depends
-// on the scatterer alone.
-// e = e_p - v dt is the scatterer's displacement relative to the platform over one PRI;
-// gam = l0.e + c1 and beta = v.e carry the item's part of the pulse-pair range change
-// (c1 = dt e_p.v - dt^2 |v|^2 / 2, l0 = (lx0, ly0, z) the position at the set's epoch).
+// The pulse-pair range change needs (d + e/2).e with d = D - l, e = e_p - v dt the
+// scatterer's displacement relative to the platform over one PRI and D = P(t) - c linear in
+// t: (d + e/2).e = K0 - [dt (D.v) + l.e_p + c1], and with l = l0 + v t, D = Q + V t
+// (Q = P(t0) - c, t counted from the set's epoch) the bracket is gam + t beta, where
+// gam = l0.e + c1 + dt (Q.v) and beta = v.e + e_p.v carry the item's part
+// (c1 = dt e_p.v - dt^2 |v|^2 / 2, l0 = (lx0, ly0, z) the position at the epoch).
 struct ItemF {
     float lx0, ly0, z, vx, vy, vz, amp0, gam, beta;  // padding past the end of a set: amp0 = 0
 };
@@ -519,11 +522,14 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float lx = fmaf(it.vx, k.t, it.lx0);
     const float ly = fmaf(it.vy, k.t, it.ly0);
     const float lz = fmaf(it.vz, k.t, it.z);
-    // R - R_c = (|l|^2 - 2 D.l) / (R + R_c)
-    const float ul = fmaf(k.ux, lx, fmaf(k.uy, ly, k.uz * lz));
-    const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
-    const float dR0 = fmaf(ll, k.h, -ul);
-    const float dR = dR0 * fmaf(-dR0, k.h, 1.0f);
+    // R - R_c = (|l|^2 - 2 D.l) / (R + R_c); -u.l and |l|^2 built from their horizontal
+    // parts, which the beam angle below reuses
+    const float nuxy = fmaf(-k.ux, lx, __fmul_rn(-k.uy, ly));
+    const float nul = fmaf(-k.uz, lz, nuxy);
+    const float lxy2 = fmaf(lx, lx, __fmul_rn(ly, ly));
+    const float ll = fmaf(lz, lz, lxy2);
+    const float dR0 = fmaf(ll, k.h, nul);
+    const float dR = __fmul_rn(dR0, fmaf(-dR0, k.h, 1.0f));
     // gate: the coordinate less 1/2 (gch), rounded to the nearest integer, is the offset from
     // the reference gate, read from the low mantissa bits of gch + 1.5 2^23 (|gch| < 2^22; a
     // larger |gch| lands outside the window, or the sample's band flags every item); cell
@@ -532,20 +538,20 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float gch = fmaf(dR, m.inv_gw_f, k.gfrac_h);
     const float gr = gch + kRoundMagic;
     int g = k.gint + (__float_as_int(gr) - __float_as_int(kRoundMagic));
-    const bool gflag = fabsf(gch - (gr - kRoundMagic)) > k.gthr;
+    const bool gflag = fabsf(fmaf(gr - kRoundMagic, -1.0f, gch)) > k.gthr;
     bool wide = false, bflag = false;
     // |C| = sqrt(sigma A) 2^E, E = beam_k atan(q)^2 + log2 (r_ref/R_c)^2 - 2 log2(1 + dR/R_c),
-    // q = rho / d_z (series in qb = beam_k q^2 below 0.01 q^2; the exact angle beyond)
+    // q = rho / d_z (series in qb = beam_k q^2 below 0.01 q^2; the exact angle beyond), with
+    // qb = beam_k rho^2 / D_z^2 and rho^2 = |D_xy - l_xy|^2 = |D_xy|^2 - 2 R_c u_xy.l + |l_xy|^2
     const float dx = k.Dx - lx, dy = k.Dy - ly;
-    const float rho2 = fmaf(dx, dx, dy * dy);
-    const float qb = rho2 * k.kq;
+    const float qb = fmaf(k.qA1, nuxy, fmaf(lxy2, k.kq, k.qA0));
     float T = k.l2kappa;  // tabulated pattern: applied to C below
     if (!ANT) {
         T = fmaf(qb, fmaf(qb, fmaf(qb, m.s2, m.s1), 1.0f), k.l2kappa);
         wide = qb < m.qb_wide;
         if (wide) {
             if (GENERAL) {
-                const float th = atan2f(sqrtf(rho2), k.Dz - lz);
+                const float th = atan2f(sqrtf(fmaf(dx, dx, dy * dy)), k.Dz - lz);
                 T = fmaf(th * th, m.beam_k_f, k.l2kappa);
             }
         }
@@ -555,13 +561,15 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float xr = __fmul_rn(dR, k.invRc);
     const float E = fmaf(xr, fmaf(xr, kInvLn2F, -2.0f * kInvLn2F), T);
     const float a = it.amp0 * ex2_approx(E);
-    // phase in cycles: psi_c + dR 2/lambda (2/lambda as hi + lo, the product error-free)
-    const float p = __fmul_rn(dR, m.chi_hi);
-    const float perr = fmaf(dR, m.chi_hi, -p);
-    // |f| <= 1 cycle: the hardware sine and cosine take their arguments modulo one turn
-    const float f = (p - rintf(p)) + (k.psic + fmaf(dR, m.chi_lo, perr));
+    // phase in cycles, psi_c + dR 2/lambda reduced to [-1/2, 1/2] (2/lambda as hi + lo: the
+    // integer part leaves dR chi_hi exactly in one FMA); the argument is -2 pi f, so that
+    // C = a (cos, sin) of it (|f| <= 1 cycle: the hardware sine and cosine take their
+    // arguments modulo one turn)
+    const float nk = rintf(__fmul_rn(dR, -m.chi_hi));
+    const float fr = fmaf(dR, m.chi_hi, nk);
+    const float f = fmaf(dR, m.chi_lo, fr + k.psic);
     float sn, cs;
-    __sincosf(kTwoPiF * f, &sn, &cs);
+    __sincosf(__fmul_rn(f, -kTwoPiF), &sn, &cs);
     float2 gu, gv, G;
     PatCellF cell;
     float pu = 0.f, pv = 0.f, pat_bins = 0.f;
@@ -582,29 +590,28 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
             const float pr = fmaf(G2.x, G.x, G2.y * G.y), pi = fmaf(G2.y, G.x, -G2.x * G.y);
             pat_bins = __fmul_rn(small_arg_f(pi, pr), m.nd_over_2pi_f);
         }
-        re = a * fmaf(G.x, cs, G.y * sn);
-        im = a * fmaf(G.y, cs, -G.x * sn);
+        // e^{-j 2 pi f} = cs + j sn
+        re = a * fmaf(G.x, cs, -G.y * sn);
+        im = a * fmaf(G.y, cs, G.x * sn);
     } else {
         re = a * cs;
-        im = -a * sn;
+        im = a * sn;
     }
     int kb = 0;
     float b = 0.0f;
     if (DOPPLER) {
-        // pulse-pair range change D = 2 (d + e/2).e / (R + R'), d = D - l, e = e_p - v dt:
-        // (d + e/2).e = K0 - dt (d.v) - l.e_p - c1, and with l = l0 + v t,
-        // dt (d.v) + l.e_p = dt (D.v) + l0.e + t (v.e);  b = nu n_doppler = -n_doppler 2 D /
-        // lambda (unwrapped: the bin is taken mod n_doppler); bin = nearest integer to b
-        const float item = fmaf(k.dtDx, it.vx, fmaf(k.dtDy, it.vy,
-                                fmaf(k.dtDz, it.vz, fmaf(k.t, it.beta, it.gam))));
+        // pulse-pair range change D = 2 (d + e/2).e / (R + R'), (d + e/2).e = K0 - (gam + t beta);
+        // b = nu n_doppler = -n_doppler 2 D / lambda (unwrapped: the bin is taken mod
+        // n_doppler); bin = nearest integer to b
+        const float item = fmaf(k.t, it.beta, it.gam);
         b = ((k.K0hi - item) + k.K0lo) * k.kbin;
-        b = fmaf(-b, xr, b);                       // 1 / (R_c + dR) = (1 / R_c)(1 - dR / R_c)
+        b = fmaf(b, -xr, b);                       // 1 / (R_c + dR) = (1 / R_c)(1 - dR / R_c)
         if (ANT) b += pat_bins;
         // nearest integer mod n_doppler (a power of two <= 2^22) from the low mantissa bits;
         // beyond |b| ~ 1e6 the band below flags every item
         const float bm = b + kRoundMagic;
         kb = __float_as_int(bm) & (m.n_doppler - 1);
-        bflag = fabsf(b - (bm - kRoundMagic)) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps);
+        bflag = fabsf(fmaf(bm - kRoundMagic, -1.0f, b)) > fmaf(-fabsf(b), kEpsSlope, 0.5f - kBinEps);
     }
     if (DERIV) {
         // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
@@ -618,8 +625,9 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
             dv->dlna = 2.0f * dz * invR2;
             const float su = pu * dz * invR2, svv = pv * dz * invR2;
             const float dgx = fmaf(gu.x, su, gv.x * svv), dgy = fmaf(gu.y, su, gv.y * svv);
-            dv->pat = make_float2(a * fmaf(dgx, cs, dgy * sn), a * fmaf(dgy, cs, -dgx * sn));
+            dv->pat = make_float2(a * fmaf(dgx, cs, -dgy * sn), a * fmaf(dgy, cs, dgx * sn));
         } else {
+            const float rho2 = fmaf(dx, dx, dy * dy);
             const float q2 = qb * m.inv_beam_k;
             float rho_theta;
             if (q2 < 1e-2f) {
@@ -687,9 +695,11 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
     const float2 lx = __ffma2_rn(it.vx, t2, it.lx0);
     const float2 ly = __ffma2_rn(it.vy, t2, it.ly0);
     const float2 lz = __ffma2_rn(it.vz, t2, it.z);
-    // -u.l, with the signs carried by the constants (exact)
-    const float2 nul = __ffma2_rn(f2(-k.ux), lx, __ffma2_rn(f2(-k.uy), ly, __fmul2_rn(f2(-k.uz), lz)));
-    const float2 ll = __ffma2_rn(lx, lx, __ffma2_rn(ly, ly, __fmul2_rn(lz, lz)));
+    // -u.l and |l|^2 from their horizontal parts (as eval_split; the signs ride on constants)
+    const float2 nuxy = __ffma2_rn(f2(-k.ux), lx, __fmul2_rn(f2(-k.uy), ly));
+    const float2 nul = __ffma2_rn(f2(-k.uz), lz, nuxy);
+    const float2 lxy2 = __ffma2_rn(lx, lx, __fmul2_rn(ly, ly));
+    const float2 ll = __ffma2_rn(lz, lz, lxy2);
     const float2 dR0 = __ffma2_rn(ll, f2(k.h), nul);
     const float2 dR = __fmul2_rn(dR0, __ffma2_rn(dR0, f2(-k.h), one));
     // gate (as eval_split)
@@ -701,10 +711,7 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
     // amplitude (the tabulated pattern multiplies C below)
     float2 T = f2(k.l2kappa), qb = f2(0.0f), ndx, ndy;
     if (!ANT) {
-        const float2 dx = __ffma2_rn(lx, neg1, f2(k.Dx));
-        const float2 dy = __ffma2_rn(ly, neg1, f2(k.Dy));
-        const float2 rho2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-        qb = __fmul2_rn(rho2, f2(k.kq));
+        qb = __ffma2_rn(f2(k.qA1), nuxy, __ffma2_rn(lxy2, f2(k.kq), f2(k.qA0)));
         T = __ffma2_rn(qb, __ffma2_rn(qb, __ffma2_rn(qb, f2(m.s2), f2(m.s1)), one), T);
     } else {
         ndx = __ffma2_rn(f2(k.Dx), neg1, lx);   // -d_x = l_x - D_x (exact negation)
@@ -714,19 +721,18 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
     const float2 nxr = __fmul2_rn(dR, f2(-k.invRc));
     const float2 E = __ffma2_rn(nxr, __ffma2_rn(nxr, f2(kInvLn2F), f2(2.0f * kInvLn2F)), T);
     const float2 a = __fmul2_rn(it.amp0, make_float2(ex2_approx(E.x), ex2_approx(E.y)));
-    // phase in cycles with p = dR chi_hi carried as -p (exact)
+    // phase (as eval_split): -k = rint(-dR chi_hi), f = dR chi_lo + (dR chi_hi - k + psi_c)
     const float2 np = __fmul2_rn(dR, f2(-m.chi_hi));
-    const float2 perr = __ffma2_rn(dR, f2(m.chi_hi), np);
-    const float2 fr = __ffma2_rn(make_float2(rintf(np.x), rintf(np.y)), neg1, np);  // -(p - rint p)
-    const float2 s = __fadd2_rn(f2(k.psic), __ffma2_rn(dR, f2(m.chi_lo), perr));
-    const float2 arg = __fmul2_rn(f2(kTwoPiF), __ffma2_rn(fr, neg1, s));
+    const float2 fr = __ffma2_rn(dR, f2(m.chi_hi), make_float2(rintf(np.x), rintf(np.y)));
+    const float2 f = __ffma2_rn(dR, f2(m.chi_lo), __fadd2_rn(fr, f2(k.psic)));
+    const float2 arg = __fmul2_rn(f, f2(-kTwoPiF));
     float2 sn, cs;
     __sincosf(arg.x, &sn.x, &cs.x);
     __sincosf(arg.y, &sn.y, &cs.y);
     float2 pat_bins = f2(0.0f);
     if (!ANT) {
         re = __fmul2_rn(a, cs);
-        im = __fmul2_rn(__fmul2_rn(a, sn), neg1);
+        im = __fmul2_rn(a, sn);
     } else {
         // (u, v) = -(d_x, d_y) / R with 1 / R = (1 / R_c)(1 - x_r), as eval_split
         const float2 invR = __fmul2_rn(f2(k.invRc), __fadd2_rn(one, nxr));
@@ -747,14 +753,13 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
             pat_bins.y = __fmul_rn(small_arg_f(fmaf(H1.y, G1.x, -H1.x * G1.y),
                                                fmaf(H1.x, G1.x, H1.y * G1.y)), m.nd_over_2pi_f);
         }
-        re = make_float2(a.x * fmaf(G0.x, cs.x, G0.y * sn.x), a.y * fmaf(G1.x, cs.y, G1.y * sn.y));
-        im = make_float2(a.x * fmaf(G0.y, cs.x, -G0.x * sn.x), a.y * fmaf(G1.y, cs.y, -G1.x * sn.y));
+        re = make_float2(a.x * fmaf(G0.x, cs.x, -G0.y * sn.x), a.y * fmaf(G1.x, cs.y, -G1.y * sn.y));
+        im = make_float2(a.x * fmaf(G0.y, cs.x, G0.x * sn.x), a.y * fmaf(G1.y, cs.y, G1.x * sn.y));
     }
     bool refine0 = fabsf(gd.x) > k.gthr, refine1 = fabsf(gd.y) > k.gthr;
     int kb0 = 0, kb1 = 0;
     if (DOPPLER) {
-        const float2 item = __ffma2_rn(f2(k.dtDx), it.vx, __ffma2_rn(f2(k.dtDy), it.vy,
-                              __ffma2_rn(f2(k.dtDz), it.vz, __ffma2_rn(t2, it.beta, it.gam))));
+        const float2 item = __ffma2_rn(t2, it.beta, it.gam);
         float2 b = __fmul2_rn(__fadd2_rn(__ffma2_rn(item, neg1, f2(k.K0hi)), f2(k.K0lo)), f2(k.kbin));
         b = __ffma2_rn(b, nxr, b);
         if (ANT) b = __fadd2_rn(b, pat_bins);
