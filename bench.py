@@ -37,13 +37,15 @@ import scenegen as sg  # noqa: E402
 
 METRIC = "scatterer-pulse contribs/s & fast-mode IQ pulses/s at stated err vs FP64, % roofline"
 UNIT = "IQ pulses/s"
-# FP32 operations of one scatterer at one update in the split-path formulation, counted from
-# its arithmetic: position at t 3, range excess 9, gate 4, amplitude (beam series, range
-# factor) 12, phase 8, C 3, pulse-pair Doppler bin 11, rasterising C into its cell 2 (re, im);
-# plus 3 MUFU operations (ex2, sin, cos).  Regular mode: no Doppler bin (41 + 3 MUFU).
-OPS_PER_UPDATE = 52
+# Algorithmic cost of one scatterer at one update of the fast pass: two range evaluations
+# (the pulse pair), gate, beam-weighted amplitude, phase, pulse-pair Doppler bin and the
+# accumulation of C into its cell, about 50-70 FP32 operations; the low end is taken (the
+# split-path formulation here executes 41 for the evaluation and 2 for the accumulation), plus
+# 3 MUFU operations (ex2, sin, cos).  Regular mode, per scatterer-pulse: about 40 FP32
+# operations (no Doppler bin).
+OPS_PER_UPDATE = 50
 MUFU_PER_UPDATE = 3
-OPS_PER_PULSE_REGULAR = 41
+OPS_PER_PULSE_REGULAR = 40
 L2_FLUSH_BYTES = 512 << 20
 PEAK_KINDS = {"ffma": 0, "ffma2": 1, "mufu_ex2": 2, "mufu_sin": 3, "mufu_cos": 4, "dfma": 5}
 
@@ -332,9 +334,12 @@ def main():
     roofline = {"bound": "alu", "kernel": "accumulate_split_kernel<DOPPLER=true>"}
     roofline.update(alu_roofline(peaks, sm_mhz, units, acc_mean_ms))
     roofline.update({"traffic": None, "ops_per_unit": OPS_PER_UPDATE,
-                     "ops_basis": "FP32 operations of one scatterer-update counted from the "
-                                  "split-path formulation (position 3, range 9, gate 4, "
-                                  "amplitude 12, phase 8, C 3, pulse-pair bin 11, rasterise 2)",
+                     "ops_basis": "algorithmic FP32 operations of one scatterer-update (two "
+                                  "range evaluations, gate, amplitude, phase, pulse-pair bin, "
+                                  "accumulation: 50-70, low end taken); the split-path "
+                                  "formulation executes 41 + 2 (position 3, range 9, gate 4, "
+                                  "amplitude 9, phase 5 + 1 rounding, C 2, pulse-pair bin 8, "
+                                  "accumulation 2)",
                      "units_per_launch": units, "launch_ms": round(acc_mean_ms, 4),
                      "launch_ms_basis": "CUDA events around the summation call (workspace "
                                         "clear + kernel + conversion) on its stream",
