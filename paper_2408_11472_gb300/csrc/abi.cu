@@ -125,6 +125,7 @@ rsim::Model make_model(const rsim_radar* r, const rsim_platform* p, const rsim_s
     m.beam_k_f = (float)m.beam_k;
     m.chi_hi = (float)m.two_over_lambda;
     m.chi_lo = (float)(m.two_over_lambda - (double)m.chi_hi);
+    m.chi_lo_rad = (float)(-6.283185307179586476925 * (m.two_over_lambda - (double)m.chi_hi));
     m.dt_f = (float)m.inv_prf;
     m.hdt_f = (float)(0.5 * m.inv_prf);
     for (int i = 0; i < 3; ++i) m.ep[i] = (float)(p->v[i] * m.inv_prf);

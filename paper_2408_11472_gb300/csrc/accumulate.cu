@@ -288,12 +288,12 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
 #pragma unroll
             for (int q = 0; q < IT; q += 2) {
                 float2 r2, i2;
-                eval_split_pair<DOPPLER, ANT>(m, k, it2[q / 2], key[q], key[q + 1], r2, i2);
+                bool d;
+                eval_split_pair<DOPPLER, ANT>(m, k, it2[q / 2], key[q], key[q + 1], r2, i2, d);
                 re[q] = r2.x; re[q + 1] = r2.y;
                 im[q] = i2.x; im[q + 1] = i2.y;
+                deferred |= d;
             }
-#pragma unroll
-            for (int q = 0; q < IT; ++q) deferred |= key[q] == kKeyDeferred;
             if (__any_sync(kFull, deferred)) {  // rare: queue the flagged items
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {
@@ -305,7 +305,7 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
                     nq += __popc(b);
                 }
             }
-            warp_reduce_emit<float, IT>(key, re, im, sample_out(tab[j]));
+            warp_reduce_emit<float, IT>(key, re, im, sample_out(tab[j]), (unsigned)cells);
             if (nq > kQueue - 32 * IT) {  // room for one more sample's worth
                 __syncwarp();
                 flush_queue<DOPPLER, ANT>(m, sch, sc, cx_.p0, cx_.chunk0, cx, cy, cx_.area, dq, tab,
@@ -362,7 +362,8 @@ __device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Sche
 #pragma unroll
             for (int q = 0; q < kItems; ++q)
                 key[q] = eval_fp64<DOPPLER, false, ANT>(m, k, it[q], base + q, sc.n, re[q], im[q], nullptr);
-            warp_reduce_emit<double, kItems>(key, re, im, cx_.ws + (int64_t)s * cells * 2);
+            warp_reduce_emit<double, kItems>(key, re, im, cx_.ws + (int64_t)s * cells * 2,
+                                             (unsigned)cells);
         }
     }
 }

@@ -72,6 +72,7 @@ struct Model {
     int n_doppler;          // 1 in regular mode
     // FP32 copies for the split path
     float inv_gw_f, beam_k_f, chi_hi, chi_lo, dt_f, hdt_f, ep[3], inv_nd;
+    float chi_lo_rad;       // -2 pi chi_lo: radians of phase per metre carried by chi_lo
     // off-nadir series in qb = beam_k rho^2 / D_z^2: beam_k atan(q)^2 = qb (1 + qb (s1 + qb s2))
     float s1, s2, qb_wide, inv_beam_k;
     // tabulated two-way pattern on a u-v grid (nullptr: the analytic Gaussian pattern)
@@ -368,8 +369,8 @@ __device__ __forceinline__ int cta_reaches_window(const Model& m, const double* 
 struct __align__(16) SplitConst {
     float4 a;   // t - t0 (scatterer time since the set's epoch), D_x, D_y, D_z
     float4 b;   // D / R_c (x, y, z), 1 / (2 R_c)
-    float4 c;   // 1 / R_c, frac of the gate coordinate of c less 1/2, 2 R_c / lambda - rint(.),
-                // log2 (r_ref/R_c)^2
+    float4 c;   // 1 / R_c, frac of the gate coordinate of c less 1/2,
+                // -2 pi (2 R_c / lambda - rint(.)) [rad], log2 (r_ref/R_c)^2
     float4 d;   // beam_k / D_z^2, K0 = M . e_p as hi + lo (M = D + e_p/2), -n_doppler 2 / (lambda R_c)
     float4 e;   // floor of the gate coordinate of c (int bits); active flag, then the sample
                 // index (int bits); the sample's workspace slice (pointer bits, lo + hi)
@@ -445,7 +446,8 @@ __device__ __forceinline__ SplitConst make_split_const(const Model& m, const dou
     SplitConst k;
     k.a = make_float4((float)ts, (float)Dx, (float)Dy, (float)Dz);
     k.b = make_float4((float)(Dx * inv), (float)(Dy * inv), (float)(Dz * inv), (float)(0.5 * inv));
-    k.c = make_float4((float)inv, (float)(G - Gi - 0.5), (float)psi, 2.0f * kInvLn2F * log1pf(xref));
+    k.c = make_float4((float)inv, (float)(G - Gi - 0.5), (float)(-6.283185307179586476925 * psi),
+                      2.0f * kInvLn2F * log1pf(xref));
     k.d = make_float4(kq, K0hi, (float)(K0 - (double)K0hi),
                       (float)(-(double)m.n_doppler * m.two_over_lambda * inv));
     const double gi = fmax(fmin(Gi, 1.0e9), -1.0e9);
@@ -561,15 +563,15 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     const float xr = __fmul_rn(dR, k.invRc);
     const float E = fmaf(xr, fmaf(xr, kInvLn2F, -2.0f * kInvLn2F), T);
     const float a = it.amp0 * ex2_approx(E);
-    // phase in cycles, psi_c + dR 2/lambda reduced to [-1/2, 1/2] (2/lambda as hi + lo: the
-    // integer part leaves dR chi_hi exactly in one FMA); the argument is -2 pi f, so that
-    // C = a (cos, sin) of it (|f| <= 1 cycle: the hardware sine and cosine take their
-    // arguments modulo one turn)
+    // phase psi_c + dR 2/lambda in cycles, reduced to [-1/2, 1/2] (2/lambda as hi + lo: the
+    // integer part leaves dR chi_hi exactly in one FMA), taken as the argument -2 pi f in
+    // radians so that C = a (cos, sin) of it; psi_c and the chi_lo term are carried in
+    // radians (|arg| <= 2 pi: the hardware sine and cosine take their arguments modulo one turn)
     const float nk = rintf(__fmul_rn(dR, -m.chi_hi));
     const float fr = fmaf(dR, m.chi_hi, nk);
-    const float f = fmaf(dR, m.chi_lo, fr + k.psic);
+    const float arg = fmaf(dR, m.chi_lo_rad, fmaf(fr, -kTwoPiF, k.psic));
     float sn, cs;
-    __sincosf(__fmul_rn(f, -kTwoPiF), &sn, &cs);
+    __sincosf(arg, &sn, &cs);
     float2 gu, gv, G;
     PatCellF cell;
     float pu = 0.f, pv = 0.f, pat_bins = 0.f;
@@ -687,9 +689,14 @@ __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 // negations the pair forms cannot take as operand modifiers are exact rewrites
 // (fma(x, -1, y) = y - x, products with negated constants), so each lane's key, re and im
 // are bit-identical to the scalar evaluation's.
+// Keys: g n_doppler + bin inside the range window; every item outside it gets the one key
+// n_gates n_doppler (an unsigned minimum: negative gates wrap to large unsigned values), which
+// the emission drops; items the exact evaluation must take get kKeyDeferred, and `defer`
+// reports whether either of the two did.
 template <bool DOPPLER, bool ANT>
 __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k, const ItemF2& it,
-                                                int& key0, int& key1, float2& re, float2& im) {
+                                                int& key0, int& key1, float2& re, float2& im,
+                                                bool& defer) {
     const float2 one = f2(1.0f), neg1 = f2(-1.0f);
     const float2 t2 = f2(k.t);
     const float2 lx = __ffma2_rn(it.vx, t2, it.lx0);
@@ -721,11 +728,11 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
     const float2 nxr = __fmul2_rn(dR, f2(-k.invRc));
     const float2 E = __ffma2_rn(nxr, __ffma2_rn(nxr, f2(kInvLn2F), f2(2.0f * kInvLn2F)), T);
     const float2 a = __fmul2_rn(it.amp0, make_float2(ex2_approx(E.x), ex2_approx(E.y)));
-    // phase (as eval_split): -k = rint(-dR chi_hi), f = dR chi_lo + (dR chi_hi - k + psi_c)
+    // phase (as eval_split): -k = rint(-dR chi_hi), fr = dR chi_hi - k,
+    // arg = dR (-2 pi chi_lo) + (fr (-2 pi) + psi_c [rad])
     const float2 np = __fmul2_rn(dR, f2(-m.chi_hi));
     const float2 fr = __ffma2_rn(dR, f2(m.chi_hi), make_float2(rintf(np.x), rintf(np.y)));
-    const float2 f = __ffma2_rn(dR, f2(m.chi_lo), __fadd2_rn(fr, f2(k.psic)));
-    const float2 arg = __fmul2_rn(f, f2(-kTwoPiF));
+    const float2 arg = __ffma2_rn(dR, f2(m.chi_lo_rad), __ffma2_rn(fr, f2(-kTwoPiF), f2(k.psic)));
     float2 sn, cs;
     __sincosf(arg.x, &sn.x, &cs.x);
     __sincosf(arg.y, &sn.y, &cs.y);
@@ -770,10 +777,14 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
         refine0 |= fabsf(bd.x) > fmaf(-fabsf(b.x), kEpsSlope, 0.5f - kBinEps);
         refine1 |= fabsf(bd.y) > fmaf(-fabsf(b.y), kEpsSlope, 0.5f - kBinEps);
     }
-    const int c0 = ((unsigned)g0 < (unsigned)m.n_gates) ? g0 * m.n_doppler + kb0 : -1;
-    const int c1 = ((unsigned)g1 < (unsigned)m.n_gates) ? g1 * m.n_doppler + kb1 : -1;
-    key0 = (refine0 || (!ANT && qb.x < m.qb_wide)) ? kKeyDeferred : c0;
-    key1 = (refine1 || (!ANT && qb.y < m.qb_wide)) ? kKeyDeferred : c1;
+    const unsigned cells = (unsigned)(m.n_gates * m.n_doppler);
+    const int c0 = (int)min((unsigned)(g0 * m.n_doppler + kb0), cells);
+    const int c1 = (int)min((unsigned)(g1 * m.n_doppler + kb1), cells);
+    const bool d0 = refine0 || (!ANT && qb.x < m.qb_wide);
+    const bool d1 = refine1 || (!ANT && qb.y < m.qb_wide);
+    key0 = d0 ? kKeyDeferred : c0;
+    key1 = d1 ? kKeyDeferred : c1;
+    defer = d0 || d1;
 }
 
 // Squared off-nadir angle atan(rho / d_z)^2 in FP64 (series for small angles).
@@ -922,10 +933,28 @@ __device__ __forceinline__ void emit_cell(unsigned long long* __restrict__ base,
     red_add_u64(base + 2 * (int64_t)key + 1, (unsigned long long)qi);
 }
 
+// In-lane inclusive run sum: prev + v where the run continues, v where it starts, as one
+// (paired) FMA with a 0 / 1 factor -- the same values either way.
+__device__ __forceinline__ void run_sum(bool same, float& sr, float& si, float pr, float pi,
+                                        float vr, float vi) {
+    const float s = same ? 1.0f : 0.0f;
+    const float2 r = __ffma2_rn(make_float2(s, s), make_float2(pr, pi), make_float2(vr, vi));
+    sr = r.x;
+    si = r.y;
+}
+__device__ __forceinline__ void run_sum(bool same, double& sr, double& si, double pr, double pi,
+                                        double vr, double vi) {
+    sr = same ? pr + vr : vr;
+    si = same ? pi + vi : vi;
+}
+
+// Keys at or above `cells` (out of the window, deferred, or -1) are merged like any other and
+// dropped at emission.
 template <typename T, int J>
 __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&re)[J],
                                                const T (&im)[J],
-                                               unsigned long long* __restrict__ base) {
+                                               unsigned long long* __restrict__ base,
+                                               unsigned cells) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     // in-lane inclusive run sums; bit q of tails: a run ends at item q
@@ -936,8 +965,7 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
 #pragma unroll
     for (int q = 1; q < J; ++q) {
         const bool same = key[q] == key[q - 1];
-        sr[q] = same ? sr[q - 1] + re[q] : re[q];
-        si[q] = same ? si[q - 1] + im[q] : im[q];
+        run_sum(same, sr[q], si[q], sr[q - 1], si[q - 1], re[q], im[q]);
         if (!same) tails |= 1u << (q - 1);
     }
     const bool uniform = tails == 0u;
@@ -992,7 +1020,7 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
                 vr += in_r;
                 vi += in_i;
             }
-            if (k >= 0) emit_cell(base, k, vr, vi);  // runs out of the window are dropped
+            if ((unsigned)k < cells) emit_cell(base, k, vr, vi);  // out-of-window runs dropped
         }
     }
 }
