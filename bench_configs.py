@@ -669,6 +669,19 @@ def run_surface_update(torch, rsim, args):
     t_graph = _timed(torch, em.replay, 5, flush)
     graph_same = bool(torch.equal(em.spectra, T_e) and torch.equal(em.iq, Y_e))
     t_lin = _timed(torch, linear, 5, flush)
+    # the per-update summation alone: one launch over a block of 16 updates, each with its
+    # own synthesised state
+    K = min(16, S)
+    sets = surf.field_sets(K)
+    states = []
+    for i in range(K):
+        t = i * fp.n_fast / rd.prf_hz
+        surf.at(t, fields=sets[i])
+        states.append(sets[i] + (t,))
+    grid = surf.grid()
+    t_states = _timed(torch, lambda: rsim.doppler_accumulate_states(
+        rd, pf, grid, 0, states, fp.n_fast, fp.n_doppler, "split", workspace=ws), 10, flush)
+    del sets, states
     # algorithmic bytes of one synthesis: read A (8 L^2) + omega (8 L^2), write/read the packed
     # transforms (2 x 2 x 8 L^2), write 4 fields (16 L^2)
     nbytes = 8 * L * L + 8 * L * L + 32 * L * L + 16 * L * L
@@ -684,6 +697,10 @@ def run_surface_update(torch, rsim, args):
                                           "achieved_gbs": round(nbytes / (t_surf / 1e3) / 1e9, 1),
                                           "peak_gbs": peak, "peak_basis": basis,
                                           "frac": round(nbytes / (t_surf / 1e3) / 1e9 / peak, 4)}
+    line["states_summation"] = {"updates_per_launch": K, "ms_per_launch": round(t_states, 4),
+                                "ms_per_update": round(t_states / K, 4),
+                                "hbm_bytes_per_update": 16 * L * L,
+                                "achieved_gbs_state_reads": round(16 * L * L * K / (t_states / 1e3) / 1e9, 1)}
     line["step_ms"] = {"evolving_surface_graph": round(t_graph, 3),
                        "evolving_surface_eager": round(t_evo, 3),
                        "linear_kinematics": round(t_lin, 3)}

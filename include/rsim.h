@@ -217,7 +217,36 @@ rsim_status rsim_workspace_finalize(int32_t n_updates, int32_t n_gates, int32_t 
                                     rsim_precision precision, const void *workspace,
                                     size_t workspace_bytes, void *spectra, cudaStream_t stream);
 
-/* Launch plan of the batched scatterer pass.  Every choice gives bit-identical results;
+/* One surface update's state (Algorithm 1's update_simulation regenerates the surface at
+ * every update): heights and velocities of the scatterer set at epoch t0, DEVICE float32
+ * arrays [n], 16-byte aligned (e.g. the fields rsim_surface_at writes for t0). */
+typedef struct {
+    const float *z, *vx, *vy, *vz;
+    double t0;
+} rsim_surface_state;
+
+#define RSIM_MAX_STATES 64
+
+/* rsim_doppler_accumulate_partial for updates whose scatterers move between updates
+ * (Algorithm 1 with the surface regenerated at every update): update update0 + s takes the
+ * positions x, y and NRCS of `scat` (its origin and facet area; its z, vx, vy, vz and t0 are
+ * not read and may be NULL / 0) with the heights, velocities and epoch of states[s], and
+ * adds its spectrum to slot s of the exact fixed-point workspace (cleared before by
+ * rsim_workspace_clear, converted after by rsim_workspace_finalize).  One launch covers
+ * the n_updates updates: the horizontal positions are read once, each update's heights and
+ * velocities (16 bytes per scatterer) once per update.  Every (block, update) pair is
+ * evaluated (no range-window culling: pass only updates whose window can see the set).
+ * states : HOST array [n_updates], 0 <= n_updates <= RSIM_MAX_STATES;
+ * workspace >= rsim_workspace_size(n_updates, n_gates, n_doppler) bytes, 16-byte aligned.
+ * Other arguments as rsim_doppler_accumulate. */
+rsim_status rsim_doppler_accumulate_states(const rsim_radar *radar, const rsim_platform *platform,
+                                           const rsim_scatterers *scat, int64_t update0,
+                                           int32_t n_updates, const rsim_surface_state *states,
+                                           int32_t n_fast, int32_t n_doppler,
+                                           rsim_precision precision, void *workspace,
+                                           size_t workspace_bytes, cudaStream_t stream);
+
+/* Launch plan of the batched scatterer pass./* Launch plan of the batched scatterer pass.  Every choice gives bit-identical results;
  * only the speed differs (see rsim_autotune_batched). */
 typedef struct {
     int32_t sets_per_launch;   /* scatterer sets per launch, 1..96; 0 = 96 */

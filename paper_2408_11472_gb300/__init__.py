@@ -26,6 +26,7 @@ from ._lib import PRECISIONS, WINDOWS, RsimError
 __all__ = [
     "Antenna", "Radar", "Platform", "Scatterers", "RsimError", "workspace_size", "direct_sum",
     "doppler_accumulate", "doppler_accumulate_noalloc", "doppler_accumulate_batched",
+    "doppler_accumulate_states",
     "autotune_batched", "Tuning",
     "batched_workspace_size", "BatchedFastMode", "synth_pulses", "scatterer_cells", "scatterer_echo",
     "delay_doppler", "EvolvingSurface", "simulate_fast_evolving", "HostStreamer",
@@ -195,6 +196,30 @@ def doppler_accumulate(radar, platform, scat: Scatterers, update0: int, n_update
         int(n_fast), int(n_doppler), _prec(precision), _ptr(out), _ptr(ws),
         ws.numel() * ws.element_size(), _stream(stream)))
     return out
+
+
+def doppler_accumulate_states(radar, platform, scat: Scatterers, update0: int, states,
+                              n_fast: int, n_doppler: int, precision: str = "split",
+                              workspace: Optional[torch.Tensor] = None, stream=None):
+    """Spectra of updates update0 + s whose heights and velocities are states[s] = (z, vx, vy,
+    vz, t0) (float32 [n] tensors and the epoch), the x, y and NRCS being ``scat``'s: added to
+    the exact workspace slots s (rsim_doppler_accumulate_states; clear and convert with
+    rsim_workspace_clear / rsim_workspace_finalize).  At most 64 states per call."""
+    n = len(states)
+    if n > _lib.MAX_STATES:
+        raise ValueError("at most %d states per call" % _lib.MAX_STATES)
+    arr = (_lib.SurfaceState * max(n, 1))()
+    for i, (z, vx, vy, vz, t0) in enumerate(states):
+        for f in (z, vx, vy, vz):
+            _need(f, torch.float32, (scat.n,), scat.device, "state field")
+        arr[i] = _lib.SurfaceState(z.data_ptr(), vx.data_ptr(), vy.data_ptr(), vz.data_ptr(),
+                                   float(t0))
+    ws = workspace
+    rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
+    _lib.check(_lib.lib.rsim_doppler_accumulate_states(
+        ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(update0), n, arr, int(n_fast),
+        int(n_doppler), _prec(precision), _ptr(ws), ws.numel() * ws.element_size(),
+        _stream(stream)))
 
 
 def doppler_accumulate_noalloc(radar, platform, scat: Scatterers, update0: int, n_updates: int,
@@ -647,52 +672,71 @@ class EvolvingSurface:
         """A second (z, vx, vy, vz) set of buffers for ``at(..., fields=...)``."""
         return tuple(torch.empty_like(self.z) for _ in range(4))
 
+    def field_sets(self, k: int):
+        """k (z, vx, vy, vz) sets of buffers, one per update of a block."""
+        return [self.new_fields() for _ in range(k)]
+
+    def grid(self) -> Scatterers:
+        """The facet grid and NRCS as a scatterer set (heights and velocities: the surface's
+        own buffers; the per-update summation takes them from its states instead)."""
+        return Scatterers(self.x, self.y, self.z, self.vx, self.vy, self.vz, self.nrcs,
+                          origin=self.origin, area=self.area)
+
+
+# updates per summation launch of the evolving surface (each needs its own field set)
+EVOLVING_BLOCK = 16
+
 
 def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int, n_fast: int,
                       n_doppler: int, precision: str, T: torch.Tensor, ws: torch.Tensor,
-                      stream=None, fields2=None, side=None):
-    """Spectra T[s] (+=) of updates u0 + s, the surface regenerated at each update: one
-    workspace clear, per update a synthesis and a summation into that update's slot of the
-    exact fixed-point workspace, one conversion of all slots at the end.
+                      stream=None, groups=None, side=None):
+    """Spectra T[s] (+=) of updates u0 + s, the surface regenerated at each update, in blocks of
+    K updates: the K surfaces are synthesised into K field sets, then one summation launch
+    (rsim_doppler_accumulate_states) adds the block's spectra to their slots of the exact
+    fixed-point workspace; one clear before, one conversion of all slots at the end.
 
-    With a second field set ``fields2`` and a ``side`` stream, the syntheses run on the side
-    stream into alternating field sets, so update s + 1 is synthesised while update s is
-    summed (same kernels and inputs: the same bits)."""
+    ``groups``: one or two lists of K field sets (default: one of min(S, EVOLVING_BLOCK)).
+    With two and a ``side`` stream the syntheses of block b + 1 run on the side stream into
+    the other group while block b is summed (same kernels and inputs: the same bits)."""
     G = radar.n_gates
     nbytes = ws.numel() * ws.element_size()
     cur = stream if stream is not None else torch.cuda.current_stream()
-    st, prec = _stream(cur), _prec(precision)
-    rd, pf = _lib.make_radar(radar), _lib.make_platform(platform)
+    st = _stream(cur)
     _lib.check(_lib.lib.rsim_workspace_clear(S, G, n_doppler, _ptr(ws), nbytes, st))
     slot = workspace_size(1, G, n_doppler)
-    overlap = fields2 is not None and side is not None
+    if groups is None:
+        groups = [surface.field_sets(max(1, min(S, EVOLVING_BLOCK)))]
+    K = len(groups[0])
+    overlap = len(groups) > 1 and side is not None
+    grid = surface.grid()
+    read = [None] * len(groups)     # event after the summation that last read a group
     if overlap:
-        sets = ((surface.z, surface.vx, surface.vy, surface.vz), tuple(fields2))
-        read = [None, None]                 # event after the summation that last read a set
         fork = torch.cuda.Event()
         fork.record(cur)
         side.wait_event(fork)
-    for s in range(S):
-        t = (u0 + s) * n_fast / radar.prf_hz
+    for b, s0 in enumerate(range(0, S, K)):
+        s1 = min(S, s0 + K)
+        gi = b % len(groups)
+        sets = groups[gi]
+        syn = side if overlap else cur
+        if overlap and read[gi] is not None:
+            side.wait_event(read[gi])   # the summation two blocks back has read this group
+        states = []
+        for i, s in enumerate(range(s0, s1)):
+            t = (u0 + s) * n_fast / radar.prf_hz
+            surface.at(t, stream=syn, fields=sets[i])
+            states.append(sets[i] + (t,))
         if overlap:
-            k = s & 1
-            if read[k] is not None:
-                side.wait_event(read[k])    # the summation two updates back has read it
-            scat = surface.at(t, stream=side, fields=sets[k])
             made = torch.cuda.Event()
             made.record(side)
             cur.wait_event(made)
-        else:
-            scat = surface.at(t, stream=cur)
-        sc = scat.c_struct()
-        _lib.check(_lib.lib.rsim_doppler_accumulate_partial(
-            ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(u0 + s), 1, int(n_fast),
-            int(n_doppler), prec, ctypes.c_void_p(_ptr(ws) + s * slot), nbytes - s * slot, st))
+        doppler_accumulate_states(radar, platform, grid, u0 + s0, states, n_fast, n_doppler,
+                                  precision, workspace=ws[s0 * slot:], stream=cur)
         if overlap:
-            read[k] = torch.cuda.Event()
-            read[k].record(cur)
-    _lib.check(_lib.lib.rsim_workspace_finalize(S, G, n_doppler, prec, _ptr(ws), nbytes, _ptr(T),
-                                                st))
+            read[gi] = torch.cuda.Event()
+            read[gi].record(cur)
+    _lib.check(_lib.lib.rsim_workspace_finalize(S, G, n_doppler, _prec(precision), _ptr(ws), nbytes,
+                                                _ptr(T), st))
 
 
 def simulate_fast_evolving(radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
@@ -715,11 +759,12 @@ def simulate_fast_evolving(radar, platform, surface: EvolvingSurface, n_pulses: 
 
 class EvolvingFastMode:
     """simulate_fast_evolving with every buffer allocated once, so the whole update loop
-    (per update a surface synthesis and a summation, then the post-processing) can be
-    captured into a CUDA graph (``capture()``) and replayed (``replay()``).  The syntheses
-    run on a side stream into two alternating field sets, overlapped with the summations;
-    the results are those of simulate_fast_evolving bit for bit.  ``spectra`` and ``iq``
-    hold the results; ``run()`` enqueues the same work eagerly."""
+    (per block of updates the surface syntheses and one summation launch, then the
+    post-processing) can be captured into a CUDA graph (``capture()``) and replayed
+    (``replay()``).  The syntheses run on a side stream into two alternating groups of field
+    sets, overlapped with the summations; the results are those of simulate_fast_evolving
+    bit for bit.  ``spectra`` and ``iq`` hold the results; ``run()`` enqueues the same work
+    eagerly."""
 
     def __init__(self, radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
                  n_doppler: int, window: str = "sqrt_raised_cosine", precision: str = "split",
@@ -734,9 +779,10 @@ class EvolvingFastMode:
         self.iq = torch.empty((n_pulses, G), dtype=cdt, device=dev)
         self.workspace = torch.empty(max(16, workspace_size(self.S, G, n_doppler)),
                                      dtype=torch.uint8, device=dev)
-        # a second field set and a side stream: update s + 1 is synthesised while update s
+        # two groups of field sets and a side stream: block b + 1 is synthesised while block b
         # is summed
-        self.fields2 = surface.new_fields()
+        K = max(1, min(self.S, EVOLVING_BLOCK))
+        self.groups = [surface.field_sets(K), surface.field_sets(K)]
         self.side = torch.cuda.Stream(device=dev)
         self.graph = None
 
@@ -744,7 +790,7 @@ class EvolvingFastMode:
         self.spectra.zero_()
         _evolving_spectra(self.radar, self.platform, self.surface, self.u0, self.S, self.n_fast,
                           self.n_doppler, self.precision, self.spectra, self.workspace,
-                          fields2=self.fields2, side=self.side)
+                          groups=self.groups, side=self.side)
         synth_pulses(self.radar, self.spectra, self.u0, self.n_fast, self.pulse0, self.n_pulses,
                      self.window, out=self.iq)
 

@@ -60,6 +60,13 @@ class Tuning(ctypes.Structure):
                                                                      self.samples_per_group)
 
 
+class SurfaceState(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("z", "vx", "vy", "vz")] + [("t0", ctypes.c_double)]
+
+
+MAX_STATES = 64
+
+
 class WaveSpectrum(ctypes.Structure):
     _fields_ = [("coef", ctypes.c_void_p), ("L", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("spacing", ctypes.c_double), ("scale", ctypes.c_double), ("g", ctypes.c_double)]
@@ -111,6 +118,9 @@ PROTOTYPES = {
                               ctypes.c_int),
     "rsim_doppler_accumulate_noalloc": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int,
                                          _P, _P], ctypes.c_int),
+    "rsim_doppler_accumulate_states": ([_RP, _PP, _SP, _I64, _I32, ctypes.POINTER(SurfaceState),
+                                        _I32, _I32, ctypes.c_int, _P, ctypes.c_size_t, _P],
+                                       ctypes.c_int),
 }
 
 

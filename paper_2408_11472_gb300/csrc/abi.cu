@@ -389,6 +389,76 @@ rsim_status rsim_scatterer_cells(const rsim_radar* radar, const rsim_platform* p
     return RSIM_OK;
 }
 
+static_assert(RSIM_MAX_STATES == rsim::kMaxStates, "states per launch");
+
+rsim_status rsim_doppler_accumulate_states(const rsim_radar* radar, const rsim_platform* platform,
+                                           const rsim_scatterers* scat, int64_t update0,
+                                           int32_t n_updates, const rsim_surface_state* states,
+                                           int32_t n_fast, int32_t n_doppler,
+                                           rsim_precision precision, void* workspace,
+                                           size_t workspace_bytes, cudaStream_t stream) {
+    rsim_status st;
+    if ((st = check_radar(radar)) != RSIM_OK) return st;
+    if ((st = check_platform(platform)) != RSIM_OK) return st;
+    if ((st = check_precision(precision)) != RSIM_OK) return st;
+    if (n_fast < 1) return fail(RSIM_ERR_INVALID_ARG, "n_fast=%d < 1", n_fast);
+    if (!is_pow2(n_doppler) || n_doppler > 4096)
+        return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [1, 4096]", n_doppler);
+    if ((int64_t)radar->n_gates * n_doppler > ((int64_t)1 << 24))
+        return fail(RSIM_ERR_INVALID_ARG, "n_gates * n_doppler > 2^24");
+    if (update0 < 0 || update0 > (((int64_t)1 << 52) / n_fast) - RSIM_MAX_STATES)
+        return fail(RSIM_ERR_INVALID_ARG, "update index out of range");
+    if (n_updates < 0 || n_updates > RSIM_MAX_STATES)
+        return fail(RSIM_ERR_INVALID_ARG, "n_updates=%d outside [0, %d]", n_updates, RSIM_MAX_STATES);
+    if (!scat) return fail(RSIM_ERR_INVALID_ARG, "scatterers is NULL");
+    if (scat->n < 0 || scat->n > ((int64_t)1 << 40))
+        return fail(RSIM_ERR_INVALID_ARG, "scatterer count out of range");
+    if (scat->n > 0 && (!scat->x || !scat->y || !scat->nrcs || !aligned(scat->x, 4) ||
+                        !aligned(scat->y, 4) || !aligned(scat->nrcs, 4)))
+        return fail(RSIM_ERR_INVALID_ARG, "scatterer x, y or nrcs NULL or misaligned");
+    if (!finite_pos(scat->facet_area_m2)) return fail(RSIM_ERR_INVALID_ARG, "facet_area_m2 must be > 0");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(scat->origin[i])) return fail(RSIM_ERR_INVALID_ARG, "origin must be finite");
+    if (n_updates > 0 && !states) return fail(RSIM_ERR_INVALID_ARG, "states is NULL");
+    rsim::StatesParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.n = n_updates;
+    for (int i = 0; i < n_updates; ++i) {
+        const rsim_surface_state& q = states[i];
+        const float* f[4] = {q.z, q.vx, q.vy, q.vz};
+        for (int c = 0; c < 4; ++c)
+            if (scat->n > 0 && (!f[c] || !aligned(f[c], 16)))
+                return fail(RSIM_ERR_INVALID_ARG, "state %d array %d NULL or not 16-byte aligned", i, c);
+        if (!std::isfinite(q.t0)) return fail(RSIM_ERR_INVALID_ARG, "state %d epoch not finite", i);
+        sp.s[i].z = q.z;
+        sp.s[i].vx = q.vx;
+        sp.s[i].vy = q.vy;
+        sp.s[i].vz = q.vz;
+        sp.s[i].t0 = q.t0;
+    }
+    const size_t need = ws_bytes(n_updates, radar->n_gates, n_doppler);
+    if (!workspace) return fail(RSIM_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
+    if (!aligned(workspace, 16)) return fail(RSIM_ERR_WORKSPACE, "workspace not 16-byte aligned");
+    if (workspace_bytes < need)
+        return fail(RSIM_ERR_WORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, need);
+    if (n_updates == 0 || scat->n == 0) return RSIM_OK;
+    const rsim::Model m = make_model(radar, platform, scat, n_doppler);
+    const rsim::Scat sc = make_scat(scat);
+    const int64_t chunks = (scat->n + rsim::kChunk - 1) / rsim::kChunk;
+    if (chunks > 0x7fffffff) return fail(RSIM_ERR_INVALID_ARG, "too many scatterers");
+    rsim::Schedule sch;
+    sch.pulse_base = update0 * (int64_t)n_fast;
+    sch.pulse_stride = n_fast;
+    sch.n_samples = n_updates;
+    sch.samples_per_group = n_updates;
+    sch.pad = 0;
+    const cudaError_t e = rsim::launch_accumulate_states(
+        m, sch, sc, sp, precision == RSIM_FP64, true, static_cast<unsigned long long*>(workspace),
+        (unsigned)chunks, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "summation kernel launch");
+    return RSIM_OK;
+}
+
 rsim_status rsim_doppler_accumulate_partial(const rsim_radar* radar, const rsim_platform* platform,
                                             const rsim_scatterers* scat, int64_t update0,
                                             int32_t n_updates, int32_t n_fast, int32_t n_doppler,

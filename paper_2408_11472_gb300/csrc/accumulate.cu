@@ -83,6 +83,21 @@ __device__ __forceinline__ float3 chunk_dq(const Model& m, const double* p0, dou
                        (float)(dt * platform_coord(m, p0, 2, t0)));
 }
 
+// The item's part of the pulse-pair range change (gam, beta; see ItemF) from its position
+// and velocity (the same arithmetic as item_split).
+__device__ __forceinline__ void item_motion(const Model& m, ItemF& it, float3 dq) {
+    const float vx = it.vx, vy = it.vy, vz = it.vz, z = it.z;
+    const float epv = fmaf(m.ep[0], vx, fmaf(m.ep[1], vy, m.ep[2] * vz));
+    const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    const float c1 = m.dt_f * fmaf(-m.hdt_f, vv, epv);
+    const float ex = fmaf(-vx, m.dt_f, m.ep[0]), ey = fmaf(-vy, m.dt_f, m.ep[1]);
+    const float ez = fmaf(-vz, m.dt_f, m.ep[2]);
+    // gam = l0.e + c1 + dt (Q.v), beta = v.e + e_p.v  (see ItemF)
+    it.gam = fmaf(it.lx0, ex, fmaf(it.ly0, ey, fmaf(z, ez, c1))) +
+             fmaf(dq.x, vx, fmaf(dq.y, vy, dq.z * vz));
+    it.beta = fmaf(vx, ex, fmaf(vy, ey, vz * ez)) + epv;
+}
+
 __device__ __forceinline__ ItemF item_split(const Model& m, float x, float y, float z, float vx,
                                             float vy, float vz, float nrcs, float cx, float cy,
                                             float area, float3 dq) {
@@ -232,6 +247,48 @@ __device__ __noinline__ void flush_queue(const Model& m, const Schedule& sch, co
     __syncwarp();
 }
 
+// dt (P(t0) - c) = dt D(t) - e_p (t - t0): the per-sample dq of a sample whose state has its
+// own epoch t0, from the sample's entry.
+__device__ __forceinline__ float3 state_dq(const Model& m, const SampleF& k) {
+    return make_float3(fmaf(-m.ep[0], k.t, k.Dx * m.dt_f), fmaf(-m.ep[1], k.t, k.Dy * m.dt_f),
+                       fmaf(-m.ep[2], k.t, k.Dz * m.dt_f));
+}
+
+// flush_queue for samples with their own surface states: the item's height, velocity and
+// epoch are those of its sample's state.
+template <bool DOPPLER, bool ANT>
+__device__ __noinline__ void flush_states_queue(const Model& m, const Schedule& sch,
+                                                const Scat& sc, const StatesParams& sp,
+                                                const double* p0, int64_t chunk0, float cx,
+                                                float cy, float area, const SplitConst* tab,
+                                                const int* queue, int n) {
+    for (int e = threadIdx.x & 31; e < n; e += 32) {
+        const int code = queue[e];
+        const int i = code & 0xffff, j = code >> 16;
+        const int64_t idx = chunk0 + i;
+        if (idx >= sc.n) continue;  // padding items carry no amplitude
+        const SampleF k = load_sample(tab[j]);
+        const int s = sample_index(tab[j]);
+        const StateEntry& st = sp.s[s];
+        const float x = __ldg(sc.x + idx), y = __ldg(sc.y + idx);
+        ItemF it;
+        it.lx0 = x - cx;
+        it.ly0 = y - cy;
+        it.z = __ldg(st.z + idx);
+        it.vx = __ldg(st.vx + idx);
+        it.vy = __ldg(st.vy + idx);
+        it.vz = __ldg(st.vz + idx);
+        it.amp0 = sqrtf(__ldg(sc.nrcs + idx) * area);
+        item_motion(m, it, state_dq(m, k));
+        const Fp64Const k64 = make_fp64_const(m, p0, st.t0, sample_pulse(sch, s));
+        float re, im;
+        int f;
+        const int key = eval_split<DOPPLER, true, false, ANT>(m, k, it, re, im, f, &k64, x, y);
+        if (key >= 0) emit_cell(sample_out(tab[j]), key, re, im);
+    }
+    __syncwarp();
+}
+
 template <bool DOPPLER, bool ANT, int IT>
 __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Schedule& sch,
                                                        const ChunkCtx& cx_, int s_begin,
@@ -243,6 +300,9 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
     __shared__ float s_red[2];
     __shared__ int s_cnt[TH / 32];
     __shared__ int s_queue[TH / 32][kQueue];
+    // amplitude and pulse-pair constants of the thread's item pairs: read once per sample, so
+    // they wait in shared memory (thread-private slots) rather than in registers
+    __shared__ float2 s_ext[3][IT / 2][TH];
     constexpr unsigned kFull = 0xffffffffu;
     const Scat& sc = *cx_.sc;
     const int lane = threadIdx.x & 31;
@@ -259,7 +319,12 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
         ItemF it[IT];
         items_split(m, r, cx, cy, cx_.area, dq, it);
 #pragma unroll
-        for (int p = 0; p < IT / 2; ++p) it2[p] = pack_items(it[2 * p], it[2 * p + 1]);
+        for (int p = 0; p < IT / 2; ++p) {
+            it2[p] = pack_items(it[2 * p], it[2 * p + 1]);
+            s_ext[0][p][threadIdx.x] = it2[p].amp0;
+            s_ext[1][p][threadIdx.x] = it2[p].gam;
+            s_ext[2][p][threadIdx.x] = it2[p].beta;
+        }
         chunk_bounds(r, cx, cy, base, sc.n, s_red);
     }
     const int cells = m.n_gates * m.n_doppler;
@@ -289,7 +354,11 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
             for (int q = 0; q < IT; q += 2) {
                 float2 r2, i2;
                 bool d;
-                eval_split_pair<DOPPLER, ANT>(m, k, it2[q / 2], key[q], key[q + 1], r2, i2, d);
+                ItemF2 itq = it2[q / 2];
+                itq.amp0 = s_ext[0][q / 2][threadIdx.x];
+                itq.gam = s_ext[1][q / 2][threadIdx.x];
+                itq.beta = s_ext[2][q / 2][threadIdx.x];
+                eval_split_pair<DOPPLER, ANT>(m, k, itq, key[q], key[q + 1], r2, i2, d);
                 re[q] = r2.x; re[q + 1] = r2.y;
                 im[q] = i2.x; im[q + 1] = i2.y;
                 deferred |= d;
@@ -365,6 +434,204 @@ __device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Sche
             warp_reduce_emit<double, kItems>(key, re, im, cx_.ws + (int64_t)s * cells * 2,
                                              (unsigned)cells);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Updates with their own surface states (Algorithm 1 regenerates the surface at every
+// update): sample s of the launch takes the CTA's horizontal positions and NRCS with the
+// heights, velocities and epoch of state s.  The horizontal part of every item stays in
+// registers; each sample's heights and velocities are copied into shared memory with
+// cp.async one sample ahead (thread-private slots, two buffers), so the copies of sample
+// s + 1 are in flight while sample s is evaluated.  No culling: every (CTA, sample) pair is
+// evaluated (the states' heights are not known when the CTA starts).
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(d), "l"((unsigned long long)__cvta_generic_to_global(gmem_src)),
+                    "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
+
+// The thread's IT items of one state (z, vx, vy, vz) into dst[field][h][thread], h < IT / 4
+// float4 groups, zero past the end of the set (arrays 16-byte aligned, base a multiple of IT).
+template <int IT, int TH>
+__device__ __forceinline__ void fetch_state(const StateEntry& st, int64_t base, int64_t n,
+                                            float4 (*dst)[IT / 4][TH]) {
+    const float* const f[4] = {st.z, st.vx, st.vy, st.vz};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int h = 0; h < IT / 4; ++h) {
+            const int64_t i = base + 4 * h;
+            const int64_t left = n - i;
+            const int valid = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
+            cp_async16(&dst[c][h][threadIdx.x], valid > 0 ? f[c] + i : f[c], 4 * valid);
+        }
+    }
+}
+
+template <bool DOPPLER, bool ANT, int IT>
+__device__ __forceinline__ void accumulate_split_states_chunk(const Model& m, const Schedule& sch,
+                                                              const StatesParams& sp,
+                                                              const ChunkCtx& cx_, int s_begin,
+                                                              int s_end) {
+    constexpr int TH = kChunk / IT;
+    constexpr int kQueue = 32 * IT;        // flushed after any sample that deferred an item
+    static_assert(IT % 4 == 0, "items are fetched as float4 groups");
+    __shared__ SplitConst tab[kMaxStates];
+    __shared__ int s_queue[TH / 32][kQueue];
+    __shared__ float4 s_st[2][4][IT / 4][TH];
+    constexpr unsigned kFull = 0xffffffffu;
+    const Scat& sc = *cx_.sc;
+    const int lane = threadIdx.x & 31;
+    int* const queue = s_queue[threadIdx.x >> 5];
+    float cx, cy;
+    chunk_ref(sc, cx_.chunk0, cx, cy);
+    const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * IT;
+    float lx0[IT], ly0[IT], amp0[IT];
+    {
+        float xv[IT], yv[IT], sv[IT];
+        const bool vec = sc.vec4 != 0;
+        load_items(sc.x, base, sc.n, vec, xv);
+        load_items(sc.y, base, sc.n, vec, yv);
+        load_items(sc.nrcs, base, sc.n, vec, sv);
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            lx0[q] = xv[q] - cx;
+            ly0[q] = yv[q] - cy;
+            amp0[q] = sqrtf(sv[q] * cx_.area);
+        }
+    }
+    const int cells = m.n_gates * m.n_doppler;
+    const int nb = s_end - s_begin;        // <= kMaxStates
+    if (threadIdx.x < nb) {
+        const int s = s_begin + threadIdx.x;
+        SplitConst kc = make_split_const(m, cx_.p0, sp.s[s].t0, sample_pulse(sch, s), cx, cy,
+                                         0.f, 0.f);
+        set_sample_slot(kc, s, cx_.ws + (int64_t)s * cells * 2);
+        tab[threadIdx.x] = kc;
+    }
+    fetch_state<IT, TH>(sp.s[s_begin], base, sc.n, s_st[0]);
+    cp_async_commit();
+    __syncthreads();
+    int nq = 0;
+    for (int j = 0; j < nb; ++j) {
+        if (j + 1 < nb) fetch_state<IT, TH>(sp.s[s_begin + j + 1], base, sc.n, s_st[(j + 1) & 1]);
+        cp_async_commit();                 // (empty on the last sample: the count stays uniform)
+        cp_async_wait<1>();                // this sample's copies have landed
+        const SampleF k = load_sample(tab[j]);
+        const float3 dq = state_dq(m, k);
+        ItemF2 it2[IT / 2];
+        {
+            ItemF it[IT];
+#pragma unroll
+            for (int h = 0; h < IT / 4; ++h) {
+                const float4 z4 = s_st[j & 1][0][h][threadIdx.x];
+                const float4 vx4 = s_st[j & 1][1][h][threadIdx.x];
+                const float4 vy4 = s_st[j & 1][2][h][threadIdx.x];
+                const float4 vz4 = s_st[j & 1][3][h][threadIdx.x];
+                const float zz[4] = {z4.x, z4.y, z4.z, z4.w}, ax[4] = {vx4.x, vx4.y, vx4.z, vx4.w};
+                const float ay[4] = {vy4.x, vy4.y, vy4.z, vy4.w}, az[4] = {vz4.x, vz4.y, vz4.z, vz4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = 4 * h + u;
+                    it[q].lx0 = lx0[q];
+                    it[q].ly0 = ly0[q];
+                    it[q].z = zz[u];
+                    it[q].vx = ax[u];
+                    it[q].vy = ay[u];
+                    it[q].vz = az[u];
+                    it[q].amp0 = amp0[q];
+                    item_motion(m, it[q], dq);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < IT / 2; ++p) it2[p] = pack_items(it[2 * p], it[2 * p + 1]);
+        }
+        int key[IT];
+        float re[IT], im[IT];
+        bool deferred = false;
+#pragma unroll
+        for (int q = 0; q < IT; q += 2) {
+            float2 r2, i2;
+            bool d;
+            eval_split_pair<DOPPLER, ANT>(m, k, it2[q / 2], key[q], key[q + 1], r2, i2, d);
+            re[q] = r2.x; re[q + 1] = r2.y;
+            im[q] = i2.x; im[q + 1] = i2.y;
+            deferred |= d;
+        }
+        if (__any_sync(kFull, deferred)) {  // rare: queue the flagged items
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                const bool mine = key[q] == kKeyDeferred;
+                const unsigned b = __ballot_sync(kFull, mine);
+                if (mine)
+                    queue[nq + __popc(b & ((1u << lane) - 1u))] = (threadIdx.x * IT + q) | (j << 16);
+                nq += __popc(b);
+            }
+        }
+        warp_reduce_emit<float, IT>(key, re, im, sample_out(tab[j]), (unsigned)cells);
+        if (nq > 0) {
+            __syncwarp();
+            flush_states_queue<DOPPLER, ANT>(m, sch, sc, sp, cx_.p0, cx_.chunk0, cx, cy,
+                                             cx_.area, tab, queue, nq);
+            nq = 0;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <bool DOPPLER, bool ANT>
+__device__ __forceinline__ void accumulate_fp64_states_chunk(const Model& m, const Schedule& sch,
+                                                             const StatesParams& sp,
+                                                             const ChunkCtx& cx_, int s_begin,
+                                                             int s_end) {
+    __shared__ Fp64Const tab[kMaxStates];
+    const Scat& sc = *cx_.sc;
+    const int64_t base = cx_.chunk0 + (int64_t)threadIdx.x * kItems;
+    ItemD it[kItems];
+    {
+        Raw r;
+        load_raw(sc, base, r);       // z, vx, vy, vz replaced per sample below
+        items_fp64(r, (double)cx_.area, it);
+    }
+    const int cells = m.n_gates * m.n_doppler;
+    const int nb = s_end - s_begin;
+    if (threadIdx.x < nb) {
+        const int s = s_begin + threadIdx.x;
+        Fp64Const kd = make_fp64_const(m, cx_.p0, sp.s[s].t0, sample_pulse(sch, s));
+        kd.index = s;
+        tab[threadIdx.x] = kd;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        const Fp64Const& k = tab[j];
+        const StateEntry& st = sp.s[k.index];
+#pragma unroll
+        for (int q = 0; q < kItems; ++q) {
+            const int64_t i = base + q;
+            const bool in = i < sc.n;
+            it[q].z = in ? __ldg(st.z + i) : 0.f;
+            it[q].vx = in ? __ldg(st.vx + i) : 0.f;
+            it[q].vy = in ? __ldg(st.vy + i) : 0.f;
+            it[q].vz = in ? __ldg(st.vz + i) : 0.f;
+        }
+        int key[kItems];
+        double re[kItems], im[kItems];
+#pragma unroll
+        for (int q = 0; q < kItems; ++q)
+            key[q] = eval_fp64<DOPPLER, false, ANT>(m, k, it[q], base + q, sc.n, re[q], im[q], nullptr);
+        warp_reduce_emit<double, kItems>(key, re, im, cx_.ws + (int64_t)k.index * cells * 2,
+                                         (unsigned)cells);
     }
 }
 
@@ -446,6 +713,32 @@ __global__ void __launch_bounds__(kThreads) accumulate_fp64_batched_kernel(
     int s0, s1;
     sample_range(sch, s0, s1);
     accumulate_fp64_chunk<DOPPLER, ANT>(m, sch, c, s0, s1);
+}
+
+template <bool DOPPLER, bool ANT>
+__global__ void __launch_bounds__(kChunk / split_items(ANT), ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_states_kernel(
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
+    const __grid_constant__ StatesParams sp, unsigned long long* __restrict__ ws) {
+    ChunkCtx c;
+    c.sc = &sc;
+    c.p0 = m.p0;
+    c.area = (float)m.area;
+    c.chunk0 = (int64_t)blockIdx.x * kChunk;
+    c.ws = ws;
+    accumulate_split_states_chunk<DOPPLER, ANT, split_items(ANT)>(m, sch, sp, c, 0, sch.n_samples);
+}
+
+template <bool DOPPLER, bool ANT>
+__global__ void __launch_bounds__(kThreads) accumulate_fp64_states_kernel(
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
+    const __grid_constant__ StatesParams sp, unsigned long long* __restrict__ ws) {
+    ChunkCtx c;
+    c.sc = &sc;
+    c.p0 = m.p0;
+    c.area = (float)m.area;
+    c.chunk0 = (int64_t)blockIdx.x * kChunk;
+    c.ws = ws;
+    accumulate_fp64_states_chunk<DOPPLER, ANT>(m, sch, sp, c, 0, sch.n_samples);
 }
 
 // Fixed point (q 2^-32) to float without the FP64 pipe: |q| = hi 2^32 + lo, both unsigned
@@ -726,6 +1019,31 @@ cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const
         } else {
             if (doppler) accumulate_split_batched_kernel<true, false><<<grid, kChunk / split_items(false), 0, stream>>>(m, sch, bp);
             else accumulate_split_batched_kernel<false, false><<<grid, kChunk / split_items(false), 0, stream>>>(m, sch, bp);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_states(const Model& m, const Schedule& sch, const Scat& sc,
+                                     const StatesParams& sp, bool fp64, bool doppler,
+                                     unsigned long long* ws, unsigned n_chunks,
+                                     cudaStream_t stream) {
+    const bool ant = m.ant != nullptr;
+    if (fp64) {
+        if (ant) {
+            if (doppler) accumulate_fp64_states_kernel<true, true><<<n_chunks, kThreads, 0, stream>>>(m, sch, sc, sp, ws);
+            else accumulate_fp64_states_kernel<false, true><<<n_chunks, kThreads, 0, stream>>>(m, sch, sc, sp, ws);
+        } else {
+            if (doppler) accumulate_fp64_states_kernel<true, false><<<n_chunks, kThreads, 0, stream>>>(m, sch, sc, sp, ws);
+            else accumulate_fp64_states_kernel<false, false><<<n_chunks, kThreads, 0, stream>>>(m, sch, sc, sp, ws);
+        }
+    } else {
+        if (ant) {
+            if (doppler) accumulate_split_states_kernel<true, true><<<n_chunks, kChunk / split_items(true), 0, stream>>>(m, sch, sc, sp, ws);
+            else accumulate_split_states_kernel<false, true><<<n_chunks, kChunk / split_items(true), 0, stream>>>(m, sch, sc, sp, ws);
+        } else {
+            if (doppler) accumulate_split_states_kernel<true, false><<<n_chunks, kChunk / split_items(false), 0, stream>>>(m, sch, sc, sp, ws);
+            else accumulate_split_states_kernel<false, false><<<n_chunks, kChunk / split_items(false), 0, stream>>>(m, sch, sc, sp, ws);
         }
     }
     return cudaGetLastError();

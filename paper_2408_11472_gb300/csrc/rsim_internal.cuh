@@ -245,6 +245,22 @@ struct BatchParams {
     BatchEntry e[kMaxBatch];
 };
 
+// Surface states of a block of updates (Algorithm 1 regenerates the surface at every
+// update): per update the heights and velocities of the set and their epoch; the horizontal
+// positions and NRCS are the scatterer set's own.
+constexpr int kMaxStates = 64;
+
+struct StateEntry {
+    const float *z, *vx, *vy, *vz;
+    double t0;
+};
+
+struct StatesParams {
+    int n;
+    int pad;
+    StateEntry s[kMaxStates];
+};
+
 struct FinalizeBatch {
     const void* ws[kMaxBatch];
     void* out[kMaxBatch];

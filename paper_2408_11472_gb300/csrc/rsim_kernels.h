@@ -12,12 +12,17 @@ struct Schedule;
 struct Scat;
 struct BatchParams;
 struct FinalizeBatch;
+struct StatesParams;
 
 cudaError_t launch_accumulate(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
                               bool doppler, unsigned long long* ws, dim3 grid,
                               cudaStream_t stream);
 cudaError_t launch_finalize(const void* ws, void* out, int64_t n_vals, bool fp64, int n_sms,
                             cudaStream_t stream);
+cudaError_t launch_accumulate_states(const Model& m, const Schedule& sch, const Scat& sc,
+                                     const StatesParams& sp, bool fp64, bool doppler,
+                                     unsigned long long* ws, unsigned n_chunks,
+                                     cudaStream_t stream);
 cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const BatchParams& bp,
                                       bool fp64, bool doppler, dim3 grid, cudaStream_t stream);
 cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t n_vals, bool fp64,

@@ -108,6 +108,25 @@ def test_noalloc_size_limit_is_checked_on_the_host(L):
                                                None) == 1
 
 
+def test_states_summation_validates_on_the_host(L):
+    """rsim_doppler_accumulate_states checks its states before any CUDA call: at most 64 per
+    call, a states array when there are updates, 16-byte aligned fields."""
+    B = ctypes.byref
+    rd, pf, sc = _structs(L)
+    lib = L.lib
+    st = (L.SurfaceState * 1)(L.SurfaceState(0x1000, 0x1000, 0x1000, 0x1000, 0.0))
+    assert lib.rsim_doppler_accumulate_states(B(rd), B(pf), B(sc), 0, 65, st, 64, 64, 1,
+                                              0x1000, 1 << 30, None) == 1
+    assert lib.rsim_doppler_accumulate_states(B(rd), B(pf), B(sc), 0, 1, None, 64, 64, 1,
+                                              0x1000, 1 << 30, None) == 1
+    bad = (L.SurfaceState * 1)(L.SurfaceState(0x1004, 0x1000, 0x1000, 0x1000, 0.0))
+    assert lib.rsim_doppler_accumulate_states(B(rd), B(pf), B(sc), 0, 1, bad, 64, 64, 1,
+                                              0x1000, 1 << 30, None) == 1
+    assert b"16-byte" in lib.rsim_last_error()
+    assert lib.rsim_doppler_accumulate_states(B(rd), B(pf), B(sc), 0, 1, st, 64, 64, 1,
+                                              0x1000, 16, None) == 5
+
+
 def test_empty_work_is_a_noop(L):
     B = ctypes.byref
     rd, pf, sc = _structs(L, n=0)

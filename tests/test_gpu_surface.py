@@ -119,3 +119,56 @@ def test_bad_spectra_are_rejected(rsim):
         L.check(L.lib.rsim_surface_at(ctypes.byref(surf.spec), 0.0, surf.z.data_ptr(),
                                       surf.vx.data_ptr(), surf.vy.data_ptr(), surf.vz.data_ptr(),
                                       small.data_ptr(), 16, None))
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_states_summation_equals_single_state_pass(rsim, precision):
+    """rsim_doppler_accumulate_states with every update given the same state (epoch 0) is the
+    one-state summation of that scene: the FP64 path bit for bit, the split path to its
+    rounding (its pulse-pair constant is formed per update in FP32).  8,100 scatterers: the
+    last thread's float4 group is partial."""
+    c = sg.config(1)
+    rd, pf, fp = c["radar"], c["platform"], c["fast"]
+    sc = sg.sea_surface(90, 27)
+    dev = rsim.Scatterers.from_arrays(sc)
+    u0, S = 29, 7
+    ref = rsim.doppler_accumulate(rd, pf, dev, u0, S, fp.n_fast, fp.n_doppler, precision)
+    G = rd.n_gates
+    ws = torch.empty(rsim.workspace_size(S, G, fp.n_doppler), dtype=torch.uint8, device="cuda")
+    out = torch.zeros_like(ref)
+    from paper_2408_11472_gb300 import _lib
+    st = torch.cuda.current_stream().cuda_stream
+    nbytes = ws.numel()
+    _lib.check(_lib.lib.rsim_workspace_clear(S, G, fp.n_doppler, ws.data_ptr(), nbytes, st))
+    states = [(dev.z, dev.vx, dev.vy, dev.vz, 0.0)] * S
+    rsim.doppler_accumulate_states(rd, pf, dev, u0, states[:4], fp.n_fast, fp.n_doppler,
+                                   precision, workspace=ws)
+    slot = rsim.workspace_size(1, G, fp.n_doppler)
+    rsim.doppler_accumulate_states(rd, pf, dev, u0 + 4, states[4:], fp.n_fast, fp.n_doppler,
+                                   precision, workspace=ws[4 * slot:])
+    prec = 0 if precision == "fp64" else 1
+    _lib.check(_lib.lib.rsim_workspace_finalize(S, G, fp.n_doppler, prec, ws.data_ptr(), nbytes,
+                                                out.data_ptr(), st))
+    torch.cuda.synchronize()
+    assert np.abs(np_(ref)).max() > 0
+    if precision == "fp64":
+        assert torch.equal(out, ref)
+    else:
+        assert rel_l2(np_(out), np_(ref)) <= 1e-5
+
+
+def test_states_summation_rejects_bad_arguments(rsim):
+    rd = sg.RadarParams()
+    pf = sg.nadir_track(256)
+    dev = rsim.Scatterers.from_arrays(sg.sea_surface(64, 3))
+    ws = torch.empty(rsim.workspace_size(65, rd.n_gates, 64), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        rsim.doppler_accumulate_states(rd, pf, dev, 0, [(dev.z, dev.vx, dev.vy, dev.vz, 0.0)] * 65,
+                                       64, 64, workspace=ws)
+    shifted = torch.empty(dev.n + 1, dtype=torch.float32, device="cuda")[1:]
+    with pytest.raises(rsim.RsimError):
+        rsim.doppler_accumulate_states(rd, pf, dev, 0, [(shifted, dev.vx, dev.vy, dev.vz, 0.0)],
+                                       64, 64, workspace=ws)
+    with pytest.raises(rsim.RsimError):
+        rsim.doppler_accumulate_states(rd, pf, dev, 0, [(dev.z, dev.vx, dev.vy, dev.vz, 0.0)],
+                                       64, 64, workspace=ws[:16])
