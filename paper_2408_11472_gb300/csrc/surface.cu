@@ -10,7 +10,8 @@
 // transform: IFFT2[H_a + j H_b] = a + j b.  Two packed transforms (eta + j v_z,
 // v_x + j v_y) per update:
 //   rows pass    : one CTA per row iy builds both packed rows from A(k), A(-k) and the
-//                  phase e^{-j omega t}, and transforms them along x (shared memory);
+//                  phase e^{-j omega t} (read straight from global memory) and transforms
+//                  them along x (shared memory);
 //   columns pass : one CTA per block of columns (32 bytes of every row) transforms along y
 //                  and writes the fields.
 // Both passes use the register mixed-radix transform (radix-16 passes, one shared-memory
@@ -54,39 +55,36 @@ __global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega) {
     }
 }
 
-constexpr int kRowsThreads = 512;   // two rows of at most 4096 points: 16 per thread
+constexpr int kRowsThreads = 256;   // two rows of at most 2048 points: 16 per thread
+constexpr int kRowsThreadsBig = 512; // two rows of 4096 points
 constexpr int kColsThreads = 512;   // at most 8192 points: 16 per thread
 
-__global__ void __launch_bounds__(kRowsThreads) surf_rows_kernel(SurfArgs a, const float2* __restrict__ coef,
-                                                        const float2* __restrict__ omega,
-                                                        float2* __restrict__ tmp) {
+// Rows pass: one CTA per row iy.  The coefficients of rows iy and -iy and the omega row are
+// read straight from global memory (coalesced; the row of -k in reverse order) into the
+// two packed rows in shared memory, which then hold the only shared-memory copy.
+template <int TH>
+__global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2* __restrict__ coef,
+                                                       const float2* __restrict__ omega,
+                                                       float2* __restrict__ tmp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = a.L, NP = padded_len(L);
     float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L)
     float2* buf0 = tw + (L >> 1);
-    float2* sA = buf0 + 2 * NP;    // A(k) on row iy, A on row -iy, omega / 2 pi on row iy
-    float2* sB = sA + L;
-    float2* sW = sB + L;
     const int iy = blockIdx.x;
     const int iyn = (L - iy) & (L - 1);                     // row of -k
-    // the three input rows are copied asynchronously, all in flight at once
-    for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
-        cp_async8(sA + ix, coef + (int64_t)iy * L + ix);
-        cp_async8(sB + ix, coef + (int64_t)iyn * L + ix);
-        cp_async8(sW + ix, omega + (int64_t)iy * L + ix);
-    }
-    cp_async_commit();
-    for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
+    for (int r = threadIdx.x; r < (L >> 1); r += TH) twiddle(r, L, 1.0f, tw[r]);
     const float ky = (float)wave_number(iy, L, a.dk);
-    cp_async_wait<0>();
-    __syncthreads();
-    for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
+    const float2* rowA = coef + (int64_t)iy * L;
+    const float2* rowB = coef + (int64_t)iyn * L;
+    const float2* rowW = omega + (int64_t)iy * L;
+#pragma unroll 4
+    for (int ix = threadIdx.x; ix < L; ix += TH) {
         const int ixn = (L - ix) & (L - 1);
         const float kx = (float)wave_number(ix, L, a.dk);
-        const float2 A1 = sA[ix];
-        const float2 A2 = sB[ixn];
+        const float2 A1 = __ldg(rowA + ix);
+        const float2 A2 = __ldg(rowB + ixn);
         // e^{-j omega t}: omega t / 2 pi = w t with w = hi + lo, t = t_hi + t_lo
-        const float2 w = sW[ix];
+        const float2 w = __ldg(rowW + ix);
         const float p = w.x * a.t_hi;
         const float pe = fmaf(w.x, a.t_hi, -p);
         float f = (p - rintf(p)) + (pe + fmaf(w.x, a.t_lo, w.y * a.t_hi));
@@ -115,9 +113,9 @@ __global__ void __launch_bounds__(kRowsThreads) surf_rows_kernel(SurfArgs a, con
         buf0[NP + pad16(ix)] = make_float2(hx.x - hy.y, hx.y + hy.x);  // H_vx + j H_vy
     }
     __syncthreads();
-    fft_rows_reg<16>(buf0, 2, L, a.log2L, tw, 1.0f);   // 2 L <= 16 x 512
+    fft_rows_reg<16>(buf0, 2, L, a.log2L, tw, 1.0f);   // 2 L <= 16 x TH
 #pragma unroll 4
-    for (int ix = threadIdx.x; ix < L; ix += blockDim.x) {
+    for (int ix = threadIdx.x; ix < L; ix += TH) {
         tmp[(int64_t)iy * L + ix] = buf0[pad16(ix)];
         tmp[(int64_t)L * L + (int64_t)iy * L + ix] = buf0[NP + pad16(ix)];
     }
@@ -160,7 +158,7 @@ __global__ void __launch_bounds__(kColsThreads) surf_cols_kernel(SurfArgs a, con
 }  // namespace
 
 size_t surf_rows_smem(int L) {
-    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)padded_len(L) + 3 * (size_t)L);
+    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)padded_len(L));
 }
 size_t surf_cols_smem(int L, int cols) {
     return sizeof(float2) * ((size_t)(L / 2) + (size_t)cols * padded_len(L));
@@ -178,15 +176,24 @@ cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const float2* om
                            float* z, float* vx, float* vy, float* vz, cudaStream_t stream) {
     const size_t s1 = surf_rows_smem(a.L), s2 = surf_cols_smem(a.L, a.cols);
     cudaError_t e;
+    const bool big = a.L > 2048;
     if (s1 > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(surf_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)s1)) != cudaSuccess)
+        (e = big ? cudaFuncSetAttribute(surf_rows_kernel<kRowsThreadsBig>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)
+                 : cudaFuncSetAttribute(surf_rows_kernel<kRowsThreads>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) !=
+            cudaSuccess)
         return e;
     if (s2 > 48 * 1024 &&
         (e = cudaFuncSetAttribute(surf_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)s2)) != cudaSuccess)
         return e;
-    surf_rows_kernel<<<(unsigned)a.L, kRowsThreads, s1, stream>>>(a, static_cast<const float2*>(coef), omega, tmp);
+    if (big)
+        surf_rows_kernel<kRowsThreadsBig><<<(unsigned)a.L, kRowsThreadsBig, s1, stream>>>(
+            a, static_cast<const float2*>(coef), omega, tmp);
+    else
+        surf_rows_kernel<kRowsThreads><<<(unsigned)a.L, kRowsThreads, s1, stream>>>(
+            a, static_cast<const float2*>(coef), omega, tmp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), kColsThreads, s2, stream>>>(a, tmp, z, vx, vy, vz);
     return cudaGetLastError();
