@@ -191,7 +191,8 @@ rsim_status rsim_doppler_accumulate(const rsim_radar *radar, const rsim_platform
                                     size_t workspace_bytes, cudaStream_t stream);
 
 /* Workspace bytes of rsim_doppler_accumulate_batched: n_real regions of
- * rsim_workspace_size(n_samples, n_gates, n_doppler) rounded up to 256 bytes. */
+ * rsim_workspace_size(n_samples, n_gates, n_doppler) rounded up to 256 bytes, then one
+ * 4-byte work counter per launch (rounded up to 256 bytes). */
 size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_gates,
                                    int32_t n_doppler);
 
@@ -250,9 +251,14 @@ rsim_status rsim_doppler_accumulate_states(const rsim_radar *radar, const rsim_p
  * only the speed differs (see rsim_autotune_batched). */
 typedef struct {
     int32_t sets_per_launch;   /* scatterer sets per launch, 1..96; 0 = 96 */
-    int32_t samples_per_group; /* updates handled by one CTA (the rest of the updates go to
-                                  further CTAs over the same scatterers); 0 = library's choice */
-    int32_t reserved[6];       /* must be 0 */
+    int32_t samples_per_group; /* updates handled by one work item (the rest of the updates go
+                                  to further items over the same scatterers); 0 = library's
+                                  choice */
+    int32_t persistent;        /* 0: one CTA per (block of scatterers, group of updates);
+                                  1..8: RSIM_SPLIT only -- one launch of this many CTAs per SM
+                                  that stay resident and take (set, block, update group) work
+                                  items in order from an atomic counter until none are left */
+    int32_t reserved[5];       /* must be 0 */
 } rsim_tuning;
 
 /* rsim_doppler_accumulate for n_real independent scatterer sets -- realizations of the same
@@ -278,8 +284,9 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar *radar,
 
 /* Autotuner of the batched scatterer pass: runs rsim_doppler_accumulate_batched with the
  * same arguments under candidate launch plans (sets per launch in {96, 32, 8}, samples per
- * group in {library's choice, n_updates, n_updates/2, /4, /8}, limited to what the call can
- * use), times each with CUDA events on `stream` (one untimed run, then the median of
+ * group in {library's choice, n_updates, n_updates/2, /4, /8}, each as one CTA per work
+ * item and, for RSIM_SPLIT, as a persistent launch of 4 CTAs per SM; limited to what the
+ * call can use), times each with CUDA events on `stream` (one untimed run, then the median of
  * `reps` >= 1 runs) and writes the fastest plan to *best and its time in ms to *best_ms
  * (may be NULL).  Tune on a representative part of the job (e.g. a few dozen updates):
  * the plan then applies to any update range of the same sets.
@@ -429,8 +436,8 @@ rsim_status rsim_direct_sum_backward(const rsim_radar *radar, const rsim_platfor
  * RSIM_ERR_WORKSPACE.  Nothing is allocated: no cudaMalloc/cudaFree or allocating library
  * call.  The first call in each CUDA context looks the array's device address up
  * (cudaGetSymbolAddress, with that context current) and keeps it under the context's ID,
- * so a non-primary context, or a context made after cudaDeviceReset, gets its own address:
- * make each context's first call before any stream capture.  All calls in a context share
+ * so a non-primary context, or a context made after cudaDeviceReset, gets its own address.
+ * All calls in a context share
  * the array and each clears it on entry, so calls that may overlap on the GPU race; order
  * them (one stream, or events). */
 rsim_status rsim_doppler_accumulate_noalloc(const rsim_radar *radar,

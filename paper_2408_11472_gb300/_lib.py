@@ -53,11 +53,11 @@ class Scatterers(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("sets_per_launch", ctypes.c_int32), ("samples_per_group", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("persistent", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
     def __repr__(self):
-        return "Tuning(sets_per_launch=%d, samples_per_group=%d)" % (self.sets_per_launch,
-                                                                     self.samples_per_group)
+        return "Tuning(sets_per_launch=%d, samples_per_group=%d, persistent=%d)" % (
+            self.sets_per_launch, self.samples_per_group, self.persistent)
 
 
 class SurfaceState(ctypes.Structure):

@@ -695,10 +695,15 @@ rsim_status rsim_doppler_accumulate_backward(const rsim_radar* radar,
                         n_doppler, true, precision, grad_spectra, grad_z, grad_nrcs, stream);
 }
 
+// Work counters of the persistent batched launches, one per launch, after the sets' regions.
+size_t batch_counters_bytes(int32_t n_real) {
+    return ((size_t)4 * (size_t)(n_real > 0 ? n_real : 0) + 255u) & ~(size_t)255u;
+}
+
 size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_gates,
                                    int32_t n_doppler) {
     if (n_real < 0 || rsim_workspace_size(n_samples, n_gates, n_doppler) == 0) return 0;
-    return (size_t)n_real * batch_stride(n_samples, n_gates, n_doppler);
+    return (size_t)n_real * batch_stride(n_samples, n_gates, n_doppler) + batch_counters_bytes(n_real);
 }
 
 rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_platform* platform,
@@ -711,9 +716,13 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
     rsim_status st;
     int sets_per_launch = rsim::kMaxBatch;
     int32_t spg_req = 0;
+    int persistent = 0;
     if (tuning) {
-        for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 5; ++i)
             if (tuning->reserved[i] != 0) return fail(RSIM_ERR_INVALID_ARG, "tuning.reserved must be 0");
+        if (tuning->persistent < 0 || tuning->persistent > 8)
+            return fail(RSIM_ERR_INVALID_ARG, "tuning.persistent=%d not in [0, 8]", tuning->persistent);
+        persistent = tuning->persistent;
         if (tuning->sets_per_launch < 0 || tuning->sets_per_launch > rsim::kMaxBatch)
             return fail(RSIM_ERR_INVALID_ARG, "tuning.sets_per_launch=%d not in [0, %d]",
                         tuning->sets_per_launch, rsim::kMaxBatch);
@@ -744,7 +753,8 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
             return fail(RSIM_ERR_INVALID_ARG, "realization %d: spectra NULL or misaligned", r);
     }
     const size_t stride_b = batch_stride(n_updates, radar->n_gates, n_doppler);
-    const size_t need = (size_t)n_real * stride_b;
+    const size_t need = (size_t)n_real * stride_b + batch_counters_bytes(n_real);
+    if (fp64) persistent = 0;                       // the persistent form is the split path's
     if (!workspace) return fail(RSIM_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
     if (!aligned(workspace, 256)) return fail(RSIM_ERR_WORKSPACE, "workspace not 256-byte aligned");
     if (workspace_bytes < need)
@@ -756,6 +766,9 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
     const int64_t n_vals = (int64_t)(ws_bytes(n_updates, radar->n_gates, n_doppler) / 8);
     static thread_local rsim::BatchParams bp;       // 11.5 KB: kept off the host stack
     static thread_local rsim::FinalizeBatch fb;
+    unsigned* counters = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) +
+                                                     (size_t)n_real * stride_b);
+    int n_launch = 0;
     int r = 0;
     while (r < n_real) {
         int k = 0;
@@ -781,8 +794,18 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
         rsim::Schedule sch;
         const int64_t groups = plan_samples(chunks, update0 * (int64_t)n_fast, n_fast, n_updates, &sch,
                                             spg_req);
-        e = rsim::launch_accumulate_batched(m, sch, bp, fp64, true, dim3((unsigned)chunks, (unsigned)groups),
-                                            stream);
+        if (persistent > 0) {
+            const int64_t items = chunks * groups;
+            if (items > 0x7fffffff) return fail(RSIM_ERR_INVALID_ARG, "too many work items in one batch");
+            int64_t ctas = (int64_t)device_sms() * persistent;
+            if (ctas > items) ctas = items;
+            e = rsim::launch_accumulate_batched_persistent(m, sch, bp, true, counters + n_launch,
+                                                          chunks, (int)groups, (unsigned)ctas, stream);
+        } else {
+            e = rsim::launch_accumulate_batched(m, sch, bp, fp64, true,
+                                                dim3((unsigned)chunks, (unsigned)groups), stream);
+        }
+        ++n_launch;
         if (e != cudaSuccess) return cuda_fail(e, "batched summation kernel launch");
         e = rsim::launch_finalize_batched(fb, k, n_vals, fp64, device_sms(), stream);
         if (e != cudaSuccess) return cuda_fail(e, "batched finalize kernel launch");
@@ -809,19 +832,24 @@ rsim_status rsim_autotune_batched(const rsim_radar* radar, const rsim_platform* 
     std::vector<rsim_tuning> cand;
     int nonempty = 0;
     for (int r = 0; r < n_real; ++r) nonempty += (scats && scats[r].n > 0) ? 1 : 0;
-    for (int a = 0; a < 3; ++a) {
-        if (a > 0 && sets_c[a] >= nonempty) continue;  // same grouping as a larger value
-        for (int b = 0; b < 5; ++b) {
-            if (b > 0 && spg_c[b] < 1) continue;
-            rsim_tuning t;
-            memset(&t, 0, sizeof(t));
-            t.sets_per_launch = sets_c[a];
-            t.samples_per_group = spg_c[b];
-            bool dup = false;
-            for (const rsim_tuning& c : cand)
-                dup = dup || (c.sets_per_launch == t.sets_per_launch &&
-                              c.samples_per_group == t.samples_per_group);
-            if (!dup) cand.push_back(t);
+    const int n_modes = precision == RSIM_SPLIT ? 2 : 1;   // persistent form: split path only
+    for (int mode = 0; mode < n_modes; ++mode) {
+        for (int a = 0; a < 3; ++a) {
+            if (a > 0 && sets_c[a] >= nonempty) continue;  // same grouping as a larger value
+            for (int b = 0; b < 5; ++b) {
+                if (b > 0 && spg_c[b] < 1) continue;
+                rsim_tuning t;
+                memset(&t, 0, sizeof(t));
+                t.sets_per_launch = sets_c[a];
+                t.samples_per_group = spg_c[b];
+                t.persistent = mode == 0 ? 0 : rsim::kMinBlocks;
+                bool dup = false;
+                for (const rsim_tuning& c : cand)
+                    dup = dup || (c.sets_per_launch == t.sets_per_launch &&
+                                  c.samples_per_group == t.samples_per_group &&
+                                  c.persistent == t.persistent);
+                if (!dup) cand.push_back(t);
+            }
         }
     }
     cudaEvent_t e0, e1;

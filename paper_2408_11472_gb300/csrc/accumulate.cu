@@ -690,6 +690,33 @@ __global__ void __launch_bounds__(kChunk / split_items(ANT), ANT ? kMinBlocksAnt
     accumulate_split_chunk<DOPPLER, ANT, split_items(ANT)>(m, sch, c, s0, s1);
 }
 
+// Persistent form of the batched pass: one wave of CTAs; each takes work items
+// (block of scatterers, group of updates) in order from `counter` (zeroed before the launch)
+// until the n_chunks x groups items are gone.  Item i is chunk i / groups, update group
+// i % groups, so consecutive items share a block's scatterers.  A plain atomic increment per
+// item: no CTA waits on another.
+template <bool DOPPLER, bool ANT>
+__global__ void __launch_bounds__(kChunk / split_items(ANT), ANT ? kMinBlocksAnt : kMinBlocks) accumulate_split_batched_persistent_kernel(
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ BatchParams bp,
+    unsigned* __restrict__ counter, int64_t n_chunks, int groups) {
+    __shared__ unsigned s_item;
+    const int64_t total = n_chunks * groups;
+    for (;;) {
+        __syncthreads();                   // the last item's shared tables are no longer read
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const int64_t i = s_item;
+        if (i >= total) break;
+        const int64_t chunk = i / groups;
+        const int g = (int)(i - chunk * groups);
+        const int r = batch_find(bp, chunk);
+        const ChunkCtx c = batch_ctx(bp, r, chunk);
+        const int s0 = g * sch.samples_per_group;
+        const int s1 = min(sch.n_samples, s0 + sch.samples_per_group);
+        accumulate_split_chunk<DOPPLER, ANT, split_items(ANT)>(m, sch, c, s0, s1);
+    }
+}
+
 template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads) accumulate_fp64_kernel(
     const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
@@ -1045,6 +1072,20 @@ cudaError_t launch_accumulate_states(const Model& m, const Schedule& sch, const 
             if (doppler) accumulate_split_states_kernel<true, false><<<n_chunks, kChunk / split_items(false), 0, stream>>>(m, sch, sc, sp, ws);
             else accumulate_split_states_kernel<false, false><<<n_chunks, kChunk / split_items(false), 0, stream>>>(m, sch, sc, sp, ws);
         }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_batched_persistent(const Model& m, const Schedule& sch,
+                                                 const BatchParams& bp, bool doppler,
+                                                 unsigned* counter, int64_t n_chunks, int groups,
+                                                 unsigned n_ctas, cudaStream_t stream) {
+    if (m.ant) {
+        if (doppler) accumulate_split_batched_persistent_kernel<true, true><<<n_ctas, kChunk / split_items(true), 0, stream>>>(m, sch, bp, counter, n_chunks, groups);
+        else accumulate_split_batched_persistent_kernel<false, true><<<n_ctas, kChunk / split_items(true), 0, stream>>>(m, sch, bp, counter, n_chunks, groups);
+    } else {
+        if (doppler) accumulate_split_batched_persistent_kernel<true, false><<<n_ctas, kChunk / split_items(false), 0, stream>>>(m, sch, bp, counter, n_chunks, groups);
+        else accumulate_split_batched_persistent_kernel<false, false><<<n_ctas, kChunk / split_items(false), 0, stream>>>(m, sch, bp, counter, n_chunks, groups);
     }
     return cudaGetLastError();
 }

@@ -15,7 +15,7 @@
 // (per context on a device): the pass clears it at the start of each call, but calls that
 // may overlap on the GPU (different streams, or host threads without ordering) race on it.
 // The first call in each CUDA context looks the array's address up (cudaGetSymbolAddress)
-// and should come before any stream capture in that context.
+// and keeps it for that context.
 #include <mutex>
 #include <string>
 

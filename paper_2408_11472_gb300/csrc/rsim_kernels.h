@@ -25,6 +25,10 @@ cudaError_t launch_accumulate_states(const Model& m, const Schedule& sch, const 
                                      cudaStream_t stream);
 cudaError_t launch_accumulate_batched(const Model& m, const Schedule& sch, const BatchParams& bp,
                                       bool fp64, bool doppler, dim3 grid, cudaStream_t stream);
+cudaError_t launch_accumulate_batched_persistent(const Model& m, const Schedule& sch,
+                                                 const BatchParams& bp, bool doppler,
+                                                 unsigned* counter, int64_t n_chunks, int groups,
+                                                 unsigned n_ctas, cudaStream_t stream);
 cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t n_vals, bool fp64,
                                     int n_sms, cudaStream_t stream);
 cudaError_t launch_cells(const Model& m, int64_t pulse, bool fp64, bool doppler, const Scat& sc,

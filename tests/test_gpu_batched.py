@@ -51,12 +51,43 @@ def test_every_launch_plan_gives_the_same_bits(rsim):
     scats = _sets(rsim, [40, 0, 72, 33, 90, 16, 64, 25, 51, 12], seed0=700, shift=11.0)
     u0, S = 30, 9
     ref = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler)
-    for sets, spg in ((1, 0), (3, 1), (8, 4), (96, 9), (0, 2), (5, 100)):
-        t = rsim.Tuning(sets, spg)
+    for sets, spg, pers in ((1, 0, 0), (3, 1, 0), (8, 4, 0), (96, 9, 0), (0, 2, 0), (5, 100, 0),
+                            (0, 0, 4), (3, 1, 4), (96, 9, 1), (8, 2, 8)):
+        t = rsim.Tuning(sets, spg, pers)
         outs = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler,
                                                tuning=t)
         for a, b in zip(outs, ref):
-            assert torch.equal(a, b), (sets, spg)
+            assert torch.equal(a, b), (sets, spg, pers)
+    # the FP64 path ignores the persistent form
+    ref64 = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler, "fp64")
+    outs = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler, "fp64",
+                                           tuning=rsim.Tuning(0, 0, 4))
+    for a, b in zip(outs, ref64):
+        assert torch.equal(a, b)
+
+
+def test_persistent_form_on_a_culled_long_track(rsim):
+    """The persistent form on the 100 km track, where most (block, update) items are culled:
+    the same bits as one call per set."""
+    rd = sg.RadarParams()
+    P = 257_143
+    pf = sg.nadir_track(P)
+    scats = []
+    for i, L in enumerate((96, 40, 130)):
+        d = sg.sea_surface(L, 950 + i)
+        d["t0"] = P / (2 * rd.prf_hz)
+        d["origin"] = (300.0 * i, 0.0, 0.0)
+        scats.append(rsim.Scatterers.from_arrays(d))
+    mid = P // 2 // 64
+    u0, S = mid - 300, 64          # the sets enter the range window 250-285 updates before nadir
+    outs = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, 64, 64,
+                                           tuning=rsim.Tuning(0, 8, 4))
+    nonzero = 0
+    for s, T in zip(scats, outs):
+        T1 = rsim.doppler_accumulate(rd, pf, s, u0, S, 64, 64)
+        assert torch.equal(T, T1)
+        nonzero += int(torch.count_nonzero(T1))
+    assert nonzero > 0
 
 
 def test_autotune_returns_a_valid_plan(rsim):
@@ -68,7 +99,7 @@ def test_autotune_returns_a_valid_plan(rsim):
     t, ms = rsim.autotune_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler, reps=2)
     assert ms > 0.0
     assert 1 <= t.sets_per_launch <= 96 and t.samples_per_group >= 0
-    assert list(t.reserved) == [0] * 6
+    assert 0 <= t.persistent <= 8 and list(t.reserved) == [0] * 5
     outs = rsim.doppler_accumulate_batched(rd, pf, scats, u0, S, fp.n_fast, fp.n_doppler, tuning=t)
     for a, b in zip(outs, ref):
         assert torch.equal(a, b)
@@ -85,7 +116,8 @@ def test_bad_tuning_is_rejected(rsim):
     c = sg.config(1)
     rd, pf, fp = c["radar"], c["platform"], c["fast"]
     scats = _sets(rsim, [16], seed0=720)
-    for t in (rsim.Tuning(97, 0), rsim.Tuning(-1, 0), rsim.Tuning(4, -2)):
+    for t in (rsim.Tuning(97, 0), rsim.Tuning(-1, 0), rsim.Tuning(4, -2), rsim.Tuning(4, 0, 9),
+              rsim.Tuning(4, 0, -1)):
         with pytest.raises(rsim.RsimError):
             rsim.doppler_accumulate_batched(rd, pf, scats, 0, 1, fp.n_fast, fp.n_doppler, tuning=t)
     t = rsim.Tuning(4, 0)
