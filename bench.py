@@ -83,8 +83,9 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
-    def stop(self, t_begin=None, t_end=None):
-        """Stop sampling; keep the samples stamped within [t_begin, t_end] (epoch s)."""
+    def stop(self, t_begin=None, t_end=None, windows=None):
+        """Stop sampling; keep the samples stamped within [t_begin, t_end] (epoch s), or within
+        any of the (begin, end) pairs of ``windows``."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -104,6 +105,9 @@ class ClockSampler:
             except ValueError:
                 ts = None
             if ts is not None and t_begin is not None and not (t_begin - 0.05 <= ts <= t_end + 0.05):
+                continue
+            if ts is not None and windows is not None and \
+                    not any(a - 0.05 <= ts <= b + 0.05 for a, b in windows):
                 continue
             f = f[1:]
             try:

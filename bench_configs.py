@@ -62,11 +62,16 @@ def _fp64_peak_flops(torch):
     return 2.0 * p["dfma"]["ops_per_clk_per_sm"] * p["sms"] * p["dfma"]["sm_mhz"] * 1e6
 
 
+# (begin, end) epoch seconds of every timed region of the run, for the clock record
+_TIMED_WINDOWS = []
+
+
 def _timed(torch, fn, reps, flush=None):
     """Median CUDA-event time (ms) of fn over reps runs after one untimed run."""
     fn()
     torch.cuda.synchronize()
     out = []
+    t_begin = time.time()
     for _ in range(reps):
         if flush is not None:
             flush.fill_(1.0)
@@ -76,6 +81,7 @@ def _timed(torch, fn, reps, flush=None):
         e1.record()
         torch.cuda.synchronize()
         out.append(e0.elapsed_time(e1))
+    _TIMED_WINDOWS.append((t_begin, time.time()))
     return statistics.median(out)
 
 
@@ -135,11 +141,13 @@ def run_cfg0(torch, rsim, args):
             g.replay()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_begin = time.time()
         e0.record()
         for _ in range(reps):
             g.replay()
         e1.record()
         torch.cuda.synchronize()
+        _TIMED_WINDOWS.append((t_begin, time.time()))
         ms = e0.elapsed_time(e1) / reps
         res[prec] = {"ms_per_call": round(ms, 5), "contribs_per_s": round(N * P / (ms / 1e3), 1),
                      "Y": _np(Y)}
@@ -326,20 +334,32 @@ def run_cfg3(torch, rsim, args):
                                fp.window, "split", update_block=64)
     u_mid = P_track // 2 // fp.n_fast
     tuning, tune_ms = bfm.autotune(reps=2, at_update=u_mid - bfm.block // 2)
-    bfm.capture()
-    for _ in range(1):
-        bfm.replay()
-    torch.cuda.synchronize()
-    times = []
     steps = max(1, min(args.steps, 3))
-    for _ in range(steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+
+    def replay_ms():
+        bfm.capture()
         bfm.replay()
-        e1.record()
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    ms = statistics.median(times)
+        times = []
+        t_begin = time.time()
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bfm.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        _TIMED_WINDOWS.append((t_begin, time.time()))
+        return statistics.median(times)
+
+    # the other form of the autotuned plan (persistent <-> one CTA per work item), then the
+    # autotuned plan itself (whose results the rest of the run reads)
+    other = rsim.Tuning(tuning.sets_per_launch, tuning.samples_per_group,
+                        0 if tuning.persistent else 4)
+    bfm.tuning = other
+    ms_other = replay_ms()
+    bfm.tuning = tuning
+    ms = replay_ms()
     N_tot = int(sum(s.n for s in scats))
     S = bfm.S
     mean_power = torch.zeros((n_pulses, rd.n_gates), dtype=torch.float64, device="cuda")
@@ -365,10 +385,14 @@ def run_cfg3(torch, rsim, args):
         "scatterers_total": N_tot, "track_pulses": P_track, "active_updates": [bfm.u0, bfm.u0 + S],
         "pulses_per_realization": n_pulses, "spectra_per_realization": S,
         "update_block": bfm.block, "tuning": {"sets_per_launch": tuning.sets_per_launch,
-                                              "samples_per_group": tuning.samples_per_group},
+                                              "samples_per_group": tuning.samples_per_group,
+                                              "persistent": tuning.persistent},
         "graph": "whole update loop (zeroing, batched spectrum launches, post-processing) "
                  "captured once, replayed"})
     line["ms_per_step"] = round(ms, 3)
+    line["launch_forms"] = {
+        ("persistent" if tuning.persistent else "cta_per_item") + "_autotuned_ms": round(ms, 3),
+        ("cta_per_item" if tuning.persistent else "persistent") + "_same_plan_ms": round(ms_other, 3)}
     line["scatterer_updates_per_s_nominal"] = round(N_tot * S / (ms / 1e3), 1)
     line["note"] = ("nominal = every scatterer at every active update; blocks whose range window "
                     "cannot be reached are skipped, so the work done is less")
@@ -413,7 +437,11 @@ def run_cfg4(torch, rsim, args):
                                     prec)
             loss = ((Y.abs() ** 2 - tgt) ** 2).sum()
             gz, gs = torch.autograd.grad(loss, (z, s))
-            return loss, gz, gs
+            # detached: no autograd graph outlives the step.  A live graph would keep the
+            # leaves' AccumulateGrad nodes, which remember the stream they were created on;
+            # a later captured backward would then synchronise with that (legacy default)
+            # stream, which invalidates the capture
+            return loss.detach(), gz, gs
 
         def fwd():
             with torch.no_grad():
@@ -715,5 +743,13 @@ RUNS = {"0": run_cfg0, "2": run_cfg2, "3": run_cfg3, "4": run_cfg4, "nfast": run
 def run(k: str, args):
     import torch
     import paper_2408_11472_gb300 as rsim
+    from bench import ClockSampler
     torch.cuda.set_device(0)
-    return RUNS[str(k)](torch, rsim, args)
+    del _TIMED_WINDOWS[:]
+    clocks = ClockSampler(0)
+    clocks.start()
+    line = RUNS[str(k)](torch, rsim, args)
+    # SM clock and throttle reasons over the timed regions only (not the oracle's CPU legs)
+    line["clocks"] = clocks.stop(windows=list(_TIMED_WINDOWS))
+    line["clocks"]["timed_regions"] = len(_TIMED_WINDOWS)
+    return line
