@@ -71,7 +71,7 @@
 extern "C" {
 #endif
 
-#define RSIM_ABI_VERSION 1
+#define RSIM_ABI_VERSION 2
 
 typedef enum {
     RSIM_OK = 0,
@@ -79,7 +79,8 @@ typedef enum {
     RSIM_ERR_CUDA = 2,         /* a CUDA launch or stream operation failed                 */
     RSIM_ERR_UNSUPPORTED = 3,  /* valid request the library does not implement           */
     RSIM_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                       */
-    RSIM_ERR_WORKSPACE = 5     /* workspace missing, misaligned or smaller than required   */
+    RSIM_ERR_WORKSPACE = 5,    /* workspace missing, misaligned or smaller than required   */
+    RSIM_ERR_CHECK = 6         /* -DRSIM_CHECK builds only: a kernel's bounds check failed  */
 } rsim_status;
 
 /* Arithmetic of the per-scatterer path.
@@ -155,6 +156,16 @@ typedef struct {
 /* Library version (RSIM_ABI_VERSION). */
 int rsim_version(void);
 
+/* 1 if the library was compiled with -DRSIM_CHECK (librsim_check.so), else 0.  In that
+ * debug build the summation, cell, echo and adjoint kernels check every Doppler bin when a
+ * cell key is formed (0 <= bin < n_doppler), every contribution sum before its fixed-point
+ * conversion (|value| < 2^30), every sample slot against the call's samples, and every
+ * adjoint gather cell against n_gates x n_doppler.  A failed check skips the addition or
+ * read it guards and records itself; the entry point then returns RSIM_ERR_CHECK, with the
+ * check and the offending value in rsim_last_error().  Those entry points synchronise their
+ * stream to read the record, so the debug build is for testing, not for timing. */
+int rsim_check_build(void);
+
 /* Number of consecutive scatterers that share one FP64 reference point in RSIM_SPLIT
  * (the scatterer block of one CTA).  Splitting a scatterer set at multiples of it keeps every
  * scatterer's arithmetic, and so its index decisions, identical to an unsplit call. */
@@ -172,23 +183,35 @@ size_t rsim_workspace_size(int32_t n_samples, int32_t n_gates, int32_t n_doppler
  *   iq[p][g] += sum_n C_n(t_{pulse0+p}) [gate_n = g],  p in [0, n_pulses).
  * iq        : [n_pulses][n_gates] complex (see precision), accumulated (+=).
  * workspace : >= rsim_workspace_size(n_pulses, n_gates, 1) bytes, 16-byte aligned.
+ * out_of_window : NULL, or DEVICE [n_pulses] uint64, 8-byte aligned, accumulated (+=):
+ *             out_of_window[p] += the number of scatterers whose gate at pulse pulse0 + p lies
+ *             outside [0, n_gates), so that the call leaves them out.  The decisions are the
+ *             summation's own (same precision, same re-decisions near a gate edge); counting
+ *             costs one more kernel launch of about a third of the summation's time and
+ *             changes nothing in iq.
  * pulse0 >= 0, n_pulses >= 0 (0: no-op). */
 rsim_status rsim_direct_sum(const rsim_radar *radar, const rsim_platform *platform,
                             const rsim_scatterers *scat, int64_t pulse0, int32_t n_pulses,
                             rsim_precision precision, void *iq, void *workspace,
-                            size_t workspace_bytes, cudaStream_t stream);
+                            size_t workspace_bytes, unsigned long long *out_of_window,
+                            cudaStream_t stream);
 
 /* Fast-mode Doppler spectra (Algorithm 1 of Section III.B) for the updates
  * i in [update0, update0 + n_updates): pulse pair (p_i, p_i + 1), p_i = i n_fast,
  *   spectra[i - update0][g][k] += sum of C_n(t_{p_i}) over scatterers with gate g, bin k.
  * spectra   : [n_updates][n_gates][n_doppler] complex, accumulated (+=).
  * n_fast >= 1; n_doppler a power of two in [1, 4096]; update0 >= 0.
- * workspace : >= rsim_workspace_size(n_updates, n_gates, n_doppler) bytes, 16-byte aligned. */
+ * workspace : >= rsim_workspace_size(n_updates, n_gates, n_doppler) bytes, 16-byte aligned.
+ * out_of_window : NULL, or DEVICE [n_updates] uint64, 8-byte aligned, accumulated (+=):
+ *             out_of_window[i - update0] += the number of scatterers whose gate at pulse p_i
+ *             lies outside [0, n_gates) (left out of update i's spectrum), decided as the
+ *             summation decides; as rsim_direct_sum's. */
 rsim_status rsim_doppler_accumulate(const rsim_radar *radar, const rsim_platform *platform,
                                     const rsim_scatterers *scat, int64_t update0,
                                     int32_t n_updates, int32_t n_fast, int32_t n_doppler,
                                     rsim_precision precision, void *spectra, void *workspace,
-                                    size_t workspace_bytes, cudaStream_t stream);
+                                    size_t workspace_bytes, unsigned long long *out_of_window,
+                                    cudaStream_t stream);
 
 /* Workspace bytes of rsim_doppler_accumulate_batched: n_real regions of
  * rsim_workspace_size(n_samples, n_gates, n_doppler) rounded up to 256 bytes, then one
@@ -203,9 +226,10 @@ size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_
  *   rsim_workspace_finalize (adds the sums to the complex spectra, +=).
  * Blocks that start at multiples of rsim_block_scatterers() keep every scatterer's FP64
  * reference point, so the spectra are bit-identical to one rsim_doppler_accumulate call on
- * the whole set.  Arguments as rsim_doppler_accumulate; workspace 16-byte aligned, of at
- * least rsim_workspace_size(n_updates, n_gates, n_doppler) bytes, and must not be shared
- * by overlapping calls. */
+ * the whole set.  Arguments as rsim_doppler_accumulate (without the out-of-window
+ * counter); workspace 16-byte aligned, of at least
+ * rsim_workspace_size(n_updates, n_gates, n_doppler) bytes, and must not be shared by
+ * overlapping calls. */
 rsim_status rsim_workspace_clear(int32_t n_updates, int32_t n_gates, int32_t n_doppler,
                                  void *workspace, size_t workspace_bytes, cudaStream_t stream);
 rsim_status rsim_doppler_accumulate_partial(const rsim_radar *radar,
@@ -429,7 +453,8 @@ rsim_status rsim_direct_sum_backward(const rsim_radar *radar, const rsim_platfor
  * device memory where they run (allocation-free real-time loops, plug-ins inside a host
  * process whose allocator they do not own, tenants of a pre-partitioned GPU).  The paper
  * has no counterpart: this is a deployment variant of the same computation.
- * Same arguments and results as rsim_doppler_accumulate minus the workspace; the
+ * Same arguments and results as rsim_doppler_accumulate minus the workspace and the
+ * out-of-window counter; the
  * fixed-point scratch is a 16 MiB device array built into the library (held by every GPU
  * that loads the library until the process exits), so
  * rsim_workspace_size(n_updates, n_gates, n_doppler) must be <= 16 MiB, else

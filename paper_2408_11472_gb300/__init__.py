@@ -163,38 +163,52 @@ def _workspace(workspace, nbytes, device):
     return workspace
 
 
+def _counter(t: Optional[torch.Tensor], n: int, device) -> Optional[int]:
+    if t is None:
+        return None
+    _need(t, torch.int64, (n,), device, "out_of_window")
+    return t.data_ptr()
+
+
 def direct_sum(radar, platform, scat: Scatterers, pulse0: int, n_pulses: int,
                precision: str = "split", out: Optional[torch.Tensor] = None,
-               workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-    """Regular mode: IQ [n_pulses, n_gates] (+= into ``out`` if given, else a new zeroed tensor)."""
+               workspace: Optional[torch.Tensor] = None, stream=None,
+               out_of_window: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Regular mode: IQ [n_pulses, n_gates] (+= into ``out`` if given, else a new zeroed tensor).
+    ``out_of_window``: optional int64 [n_pulses] tensor; += the scatterers left out of each
+    pulse (gate outside the window), as the summation decides."""
     shape = (n_pulses, radar.n_gates)
     if out is None:
         out = torch.zeros(shape, dtype=_cdtype(precision), device=scat.device)
     _need(out, _cdtype(precision), shape, scat.device, "out")
+    oow = _counter(out_of_window, n_pulses, scat.device)
     ws = _workspace(workspace, workspace_size(n_pulses, radar.n_gates, 1), scat.device)
     rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
     _lib.check(_lib.lib.rsim_direct_sum(ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc),
                                         int(pulse0), int(n_pulses), _prec(precision),
                                         _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
-                                        _stream(stream)))
+                                        oow, _stream(stream)))
     return out
 
 
 def doppler_accumulate(radar, platform, scat: Scatterers, update0: int, n_updates: int,
                        n_fast: int, n_doppler: int, precision: str = "split",
                        out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
-                       stream=None) -> torch.Tensor:
-    """Fast-mode Doppler spectra [n_updates, n_gates, n_doppler] of updates update0.. (Algorithm 1)."""
+                       stream=None, out_of_window: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Fast-mode Doppler spectra [n_updates, n_gates, n_doppler] of updates update0.. (Algorithm 1).
+    ``out_of_window``: optional int64 [n_updates] tensor; += the scatterers left out of each
+    update's spectrum (gate outside the window at its first pulse), as the summation decides."""
     shape = (n_updates, radar.n_gates, n_doppler)
     if out is None:
         out = torch.zeros(shape, dtype=_cdtype(precision), device=scat.device)
     _need(out, _cdtype(precision), shape, scat.device, "out")
+    oow = _counter(out_of_window, n_updates, scat.device)
     ws = _workspace(workspace, workspace_size(n_updates, radar.n_gates, n_doppler), scat.device)
     rd, pf, sc = _lib.make_radar(radar), _lib.make_platform(platform), scat.c_struct()
     _lib.check(_lib.lib.rsim_doppler_accumulate(
         ctypes.byref(rd), ctypes.byref(pf), ctypes.byref(sc), int(update0), int(n_updates),
         int(n_fast), int(n_doppler), _prec(precision), _ptr(out), _ptr(ws),
-        ws.numel() * ws.element_size(), _stream(stream)))
+        ws.numel() * ws.element_size(), oow, _stream(stream)))
     return out
 
 

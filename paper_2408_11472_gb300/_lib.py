@@ -12,10 +12,13 @@ import weakref
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsim.so")
+# the same library compiled with -DRSIM_CHECK (kernel bounds checks; for tests)
+CHECK_LIB_PATH = os.path.join(_HERE, "librsim_check.so")
 
 RSIM_OK = 0
 STATUS_NAMES = {0: "RSIM_OK", 1: "RSIM_ERR_INVALID_ARG", 2: "RSIM_ERR_CUDA",
-                3: "RSIM_ERR_UNSUPPORTED", 4: "RSIM_ERR_TIMEOUT", 5: "RSIM_ERR_WORKSPACE"}
+                3: "RSIM_ERR_UNSUPPORTED", 4: "RSIM_ERR_TIMEOUT", 5: "RSIM_ERR_WORKSPACE",
+                6: "RSIM_ERR_CHECK"}
 PRECISIONS = {"fp64": 0, "split": 1}
 WINDOWS = {"sqrt_linear": 0, "sqrt_raised_cosine": 1, "linear": 2}
 
@@ -80,13 +83,14 @@ _I32, _I64 = ctypes.c_int32, ctypes.c_int64
 
 PROTOTYPES = {
     "rsim_version": ([], ctypes.c_int),
+    "rsim_check_build": ([], ctypes.c_int),
     "rsim_last_error": ([], ctypes.c_char_p),
     "rsim_block_scatterers": ([], ctypes.c_int),
     "rsim_workspace_size": ([_I32, _I32, _I32], ctypes.c_size_t),
-    "rsim_direct_sum": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, ctypes.c_size_t, _P],
-                        ctypes.c_int),
+    "rsim_direct_sum": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, ctypes.c_size_t, _P,
+                         _P], ctypes.c_int),
     "rsim_doppler_accumulate": ([_RP, _PP, _SP, _I64, _I32, _I32, _I32, ctypes.c_int, _P, _P,
-                                 ctypes.c_size_t, _P], ctypes.c_int),
+                                 ctypes.c_size_t, _P, _P], ctypes.c_int),
     "rsim_synth_pulses": ([_RP, _P, _I32, _I64, _I32, _I32, _I64, _I32, ctypes.c_int,
                            ctypes.c_int, _P, _P], ctypes.c_int),
     "rsim_scatterer_cells": ([_RP, _PP, _SP, _I64, _I32, ctypes.c_int, _P, _P, _P, _P, _P],

@@ -1,7 +1,8 @@
 """Build librsim.so (the C ABI over the sm_103a kernels) in-tree with nvcc.
 
 Each translation unit is compiled in parallel for ``sm_103a`` only, then linked
-into ``paper_2408_11472_gb300/librsim.so`` (static CUDA runtime).  The pipe
+into ``paper_2408_11472_gb300/librsim.so`` (static CUDA runtime), and once more with
+``-DRSIM_CHECK`` into ``librsim_check.so`` (kernel bounds checks; a debug build).  The pipe
 microbenchmarks the benchmark's roofline divides by are built beside it as
 ``libalupeaks.so``.  Rebuilds only when a source or header is newer than the
 library.
@@ -23,6 +24,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build", "rsim")
 LIB = os.path.join(PKG, "librsim.so")
+# the same sources compiled with -DRSIM_CHECK: kernel bounds checks that make the entry points
+# return RSIM_ERR_CHECK (a debug build for tests)
+CHECK_BUILD_DIR = os.path.join(ROOT, "_build", "rsim_check")
+CHECK_LIB = os.path.join(PKG, "librsim_check.so")
 # measurement-only microbenchmarks of the arithmetic pipes (the roofline's denominators)
 PEAKS_SRC = os.path.join(CSRC, "peaks", "alu_peaks.cu")
 PEAKS_LIB = os.path.join(PKG, "libalupeaks.so")
@@ -46,9 +51,9 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
+    if not all(os.path.exists(p) for p in (LIB, CHECK_LIB, PEAKS_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(CHECK_LIB))
     return (all(os.path.getmtime(d) <= t for d in _deps())
             and os.path.getmtime(PEAKS_SRC) <= os.path.getmtime(PEAKS_LIB))
 
@@ -62,7 +67,8 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = False)
                     "-I", CSRC, "--expt-relaxed-constexpr"]
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]
-    procs, objs = [], []
+    procs, objs, check_objs = [], [], []
+    os.makedirs(CHECK_BUILD_DIR, exist_ok=True)
     peaks_tmp = PEAKS_LIB + ".tmp%d" % os.getpid()
     procs.append((PEAKS_SRC, subprocess.Popen(
         [nvcc] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC,
@@ -72,6 +78,11 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = False)
         objs.append(obj)
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        cobj = os.path.join(CHECK_BUILD_DIR, os.path.basename(src) + ".o")
+        check_objs.append(cobj)
+        cmd = [nvcc] + flags + ["-DRSIM_CHECK", "-c", src, "-o", cobj]
+        procs.append((src + " (RSIM_CHECK)",
+                      subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -84,9 +95,10 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = False)
         msg = "\n".join("== %s ==\n%s" % (s, t) for s, t in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     os.replace(peaks_tmp, PEAKS_LIB)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
+    for lib, lib_objs in ((LIB, objs), (CHECK_LIB, check_objs)):
+        tmp = lib + ".tmp%d" % os.getpid()
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + lib_objs, check=True)
+        os.replace(tmp, lib)
     return LIB
 
 

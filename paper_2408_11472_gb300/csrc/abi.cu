@@ -33,6 +33,29 @@ rsim_status cuda_fail(cudaError_t e, const char* what) {
     return fail(RSIM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+// Return value of an entry point whose kernels were all launched: RSIM_OK, or, in a
+// -DRSIM_CHECK build, RSIM_ERR_CHECK if one of them failed a check (the build reads the
+// summation unit's check word here, which synchronises the stream).
+rsim_status checked_ok(cudaStream_t stream) {
+#ifdef RSIM_CHECK
+    static const char* const names[] = {"?", "Doppler bin range", "fixed-point range",
+                                        "sample slot", "adjoint gather cell"};
+    unsigned long long w = 0;
+    const cudaError_t e = rsim::check_take(stream, &w);
+    if (e != cudaSuccess) return cuda_fail(e, "check word read");
+    if (w != 0) {
+        const unsigned code = (unsigned)(w >> 56);
+        long long v = (long long)(w & ((1ull << 56) - 1ull));
+        if (v & (1ll << 55)) v -= (1ll << 56);  // sign of the recorded value
+        return fail(RSIM_ERR_CHECK, "bounds check failed: %s (value %lld)",
+                    names[code < 5 ? code : 0], v);
+    }
+#else
+    (void)stream;
+#endif
+    return RSIM_OK;
+}
+
 int device_sms() {
     static int cache[256] = {0};
     int dev = 0;
@@ -203,7 +226,8 @@ rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platfor
                            const rsim_scatterers* scat, int64_t pulse_base, int32_t stride,
                            int32_t n_samples, int32_t n_doppler, bool doppler,
                            rsim_precision precision, void* out, void* workspace,
-                           size_t workspace_bytes, cudaStream_t stream, bool partial = false) {
+                           size_t workspace_bytes, cudaStream_t stream, bool partial = false,
+                           unsigned long long* out_of_window = nullptr) {
     rsim_status st;
     if ((st = check_radar(radar)) != RSIM_OK) return st;
     if ((st = check_platform(platform)) != RSIM_OK) return st;
@@ -219,6 +243,8 @@ rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platfor
         if (!out) return fail(RSIM_ERR_INVALID_ARG, "output is NULL");
         if (!aligned(out, fp64 ? 16 : 8)) return fail(RSIM_ERR_INVALID_ARG, "output misaligned");
     }
+    if (out_of_window && !aligned(out_of_window, 8))
+        return fail(RSIM_ERR_INVALID_ARG, "out_of_window not 8-byte aligned");
     const size_t need = ws_bytes(n_samples, radar->n_gates, n_doppler);
     if (!workspace) return fail(RSIM_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
     if (!aligned(workspace, 16)) return fail(RSIM_ERR_WORKSPACE, "workspace not 16-byte aligned");
@@ -240,12 +266,15 @@ rsim_status run_accumulate(const rsim_radar* radar, const rsim_platform* platfor
                                 dim3((unsigned)chunks, (unsigned)groups), stream);
     if (partial) {
         if (e != cudaSuccess) return cuda_fail(e, "summation kernel launch");
-        return RSIM_OK;
+        return checked_ok(stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "summation kernel launch");
+    if (out_of_window &&
+        (e = rsim::launch_window_count(m, sch, sc, fp64, doppler, out_of_window, stream)) != cudaSuccess)
+        return cuda_fail(e, "window count kernel launch");
     e = rsim::launch_finalize(workspace, out, (int64_t)(need / 8), fp64, device_sms(), stream);
     if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
-    return RSIM_OK;
+    return checked_ok(stream);
 }
 
 rsim_status check_synth_args(const rsim_radar* radar, int32_t n_spectra, int64_t update0,
@@ -315,6 +344,14 @@ extern "C" {
 
 int rsim_version(void) { return RSIM_ABI_VERSION; }
 
+int rsim_check_build(void) {
+#ifdef RSIM_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char* rsim_last_error(void) { return g_last_error.c_str(); }
 
 int rsim_block_scatterers(void) { return rsim::kChunk; }
@@ -328,16 +365,18 @@ size_t rsim_workspace_size(int32_t n_samples, int32_t n_gates, int32_t n_doppler
 rsim_status rsim_direct_sum(const rsim_radar* radar, const rsim_platform* platform,
                             const rsim_scatterers* scat, int64_t pulse0, int32_t n_pulses,
                             rsim_precision precision, void* iq, void* workspace,
-                            size_t workspace_bytes, cudaStream_t stream) {
+                            size_t workspace_bytes, unsigned long long* out_of_window,
+                            cudaStream_t stream) {
     return run_accumulate(radar, platform, scat, pulse0, 1, n_pulses, 1, false, precision, iq,
-                          workspace, workspace_bytes, stream);
+                          workspace, workspace_bytes, stream, false, out_of_window);
 }
 
 rsim_status rsim_doppler_accumulate(const rsim_radar* radar, const rsim_platform* platform,
                                     const rsim_scatterers* scat, int64_t update0,
                                     int32_t n_updates, int32_t n_fast, int32_t n_doppler,
                                     rsim_precision precision, void* spectra, void* workspace,
-                                    size_t workspace_bytes, cudaStream_t stream) {
+                                    size_t workspace_bytes, unsigned long long* out_of_window,
+                                    cudaStream_t stream) {
     if (n_fast < 1) return fail(RSIM_ERR_INVALID_ARG, "n_fast=%d < 1 (regular mode is rsim_direct_sum)", n_fast);
     if (!is_pow2(n_doppler) || n_doppler > 4096)
         return fail(RSIM_ERR_INVALID_ARG, "n_doppler=%d must be a power of two in [1, 4096]", n_doppler);
@@ -346,7 +385,8 @@ rsim_status rsim_doppler_accumulate(const rsim_radar* radar, const rsim_platform
     if (update0 < 0) return fail(RSIM_ERR_INVALID_ARG, "update0 < 0");
     if (update0 > (((int64_t)1 << 52) / n_fast)) return fail(RSIM_ERR_INVALID_ARG, "update0 too large");
     return run_accumulate(radar, platform, scat, update0 * (int64_t)n_fast, n_fast, n_updates,
-                          n_doppler, true, precision, spectra, workspace, workspace_bytes, stream);
+                          n_doppler, true, precision, spectra, workspace, workspace_bytes, stream,
+                          false, out_of_window);
 }
 
 rsim_status rsim_synth_pulses(const rsim_radar* radar, const void* spectra, int32_t n_spectra,
@@ -386,7 +426,7 @@ rsim_status rsim_scatterer_cells(const rsim_radar* radar, const rsim_platform* p
     const cudaError_t e = rsim::launch_cells(m, pulse, precision == RSIM_FP64, n_doppler > 1, sc,
                                              gate, bin, gate_coord, bin_coord, nullptr, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cells kernel launch");
-    return RSIM_OK;
+    return checked_ok(stream);
 }
 
 static_assert(RSIM_MAX_STATES == rsim::kMaxStates, "states per launch");
@@ -456,7 +496,7 @@ rsim_status rsim_doppler_accumulate_states(const rsim_radar* radar, const rsim_p
         m, sch, sc, sp, precision == RSIM_FP64, true, static_cast<unsigned long long*>(workspace),
         (unsigned)chunks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "summation kernel launch");
-    return RSIM_OK;
+    return checked_ok(stream);
 }
 
 rsim_status rsim_doppler_accumulate_partial(const rsim_radar* radar, const rsim_platform* platform,
@@ -625,7 +665,7 @@ rsim_status rsim_scatterer_echo(const rsim_radar* radar, const rsim_platform* pl
     const cudaError_t e = rsim::launch_cells(m, pulse, fp64, false, sc, nullptr, nullptr, nullptr,
                                              nullptr, contrib, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cells kernel launch");
-    return RSIM_OK;
+    return checked_ok(stream);
 }
 
 rsim_status rsim_synth_pulses_backward(const rsim_radar* radar, const void* grad_iq,
@@ -676,7 +716,7 @@ static rsim_status run_backward(const rsim_radar* radar, const rsim_platform* pl
     sch.pad = 0;
     const cudaError_t e = rsim::launch_backward(m, sch, sc, fp64, doppler, G, grad_z, grad_nrcs, stream);
     if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
-    return RSIM_OK;
+    return checked_ok(stream);
 }
 
 rsim_status rsim_doppler_accumulate_backward(const rsim_radar* radar,
@@ -810,7 +850,7 @@ rsim_status rsim_doppler_accumulate_batched(const rsim_radar* radar, const rsim_
         e = rsim::launch_finalize_batched(fb, k, n_vals, fp64, device_sms(), stream);
         if (e != cudaSuccess) return cuda_fail(e, "batched finalize kernel launch");
     }
-    return RSIM_OK;
+    return checked_ok(stream);
 }
 
 rsim_status rsim_autotune_batched(const rsim_radar* radar, const rsim_platform* platform,

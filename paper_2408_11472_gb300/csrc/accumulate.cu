@@ -335,7 +335,8 @@ __device__ __forceinline__ void accumulate_split_chunk(const Model& m, const Sch
         const int s = sb + threadIdx.x;
         const int64_t pulse = sample_pulse(sch, s);
         const bool act = threadIdx.x < nb &&
-                         cta_reaches_window(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+                         cta_reaches_window(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]) &&
+                         RSIM_CHECK_OK(s < sch.n_samples, kChkSample, s);
         int slot;
         const int na = compact_samples<TH>(act, s_cnt, slot);
         if (act) {
@@ -414,7 +415,9 @@ __device__ __forceinline__ void accumulate_fp64_chunk(const Model& m, const Sche
         __syncthreads();
         const int64_t pulse = sample_pulse(sch, sb + threadIdx.x);
         const bool act = threadIdx.x < nb &&
-                         cta_reaches_window(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+                         cta_reaches_window(m, cx_.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]) &&
+                         RSIM_CHECK_OK(sb + (int)threadIdx.x < sch.n_samples, kChkSample,
+                                       sb + (int)threadIdx.x);
         int slot;
         const int na = compact_samples(act, s_cnt, slot);
         if (act) {
@@ -863,6 +866,81 @@ __global__ void __launch_bounds__(kThreads) cells_kernel(Model m, int64_t pulse,
     }
 }
 
+// ------------------------------------------------------------------------- window counts
+// Scatterers outside the range window (Section II.A: only facets whose range falls in one of
+// the n_gates gates contribute), per sample of a summation call.  The decisions are the
+// summation's own: the same culling test per (block, sample) -- a block that cannot reach the
+// window counts all its scatterers -- and, for the others, the split path's FP32 gate with the
+// FP64 re-decision near a cell edge (the scalar evaluation with the re-decision inline takes
+// the same decisions as the paired evaluation and its deferred queue), or the FP64 path's.
+// Grid: (block of scatterers, group of kCountSamples samples); one atomic add per warp and
+// sample into counts[s].
+constexpr int kCountSamples = 32;
+
+template <bool DOPPLER, bool ANT>
+__global__ void __launch_bounds__(kThreads) window_count_kernel(
+    const __grid_constant__ Model m, const Schedule sch, const __grid_constant__ Scat sc,
+    int fp64, unsigned long long* __restrict__ counts) {
+    __shared__ SplitConst tab[kCountSamples];
+    __shared__ Fp64Const tab64[kCountSamples];
+    __shared__ float s_red[2];
+    __shared__ int s_reach[kCountSamples];
+    const int64_t chunk0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t base = chunk0 + (int64_t)threadIdx.x * kItems;
+    const int s0 = (int)blockIdx.y * kCountSamples;
+    const int ns = min(kCountSamples, sch.n_samples - s0);
+    Raw r;
+    load_raw(sc, base, r);
+    float cx, cy;
+    chunk_ref(sc, chunk0, cx, cy);
+    chunk_bounds(r, cx, cy, base, sc.n, s_red);
+    __syncthreads();
+    if (threadIdx.x < ns) {
+        const int64_t pulse = sample_pulse(sch, s0 + threadIdx.x);
+        s_reach[threadIdx.x] = cta_reaches_window(m, m.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+        tab64[threadIdx.x] = make_fp64_const(m, m.p0, sc.t0, pulse);
+        if (!fp64)
+            tab[threadIdx.x] = make_split_const(m, m.p0, sc.t0, pulse, cx, cy, s_red[0], s_red[1]);
+    }
+    __syncthreads();
+    int valid = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) valid += (base + q < sc.n) ? 1 : 0;
+    ItemF itf[kItems];
+    ItemD itd[kItems];
+    if (!fp64) items_split(m, r, cx, cy, (float)m.area, chunk_dq(m, m.p0, sc.t0, cx, cy), itf);
+    else items_fp64(r, m.area, itd);
+    for (int j = 0; j < ns; ++j) {
+        int n_out = valid;  // culled: every scatterer of the block is outside
+        if (s_reach[j]) {
+            n_out = 0;
+            if (!fp64) {
+                const SampleF k = load_sample(tab[j]);
+#pragma unroll
+                for (int q = 0; q < kItems; ++q) {
+                    float re, im;
+                    int f, g;
+                    eval_split<DOPPLER, true, false, ANT>(m, k, itf[q], re, im, f, &tab64[j],
+                                                          r.x[q], r.y[q], nullptr, &g);
+                    n_out += (base + q < sc.n && (unsigned)g >= (unsigned)m.n_gates) ? 1 : 0;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kItems; ++q) {
+                    double re, im;
+                    int g;
+                    eval_fp64<DOPPLER, false, ANT>(m, tab64[j], itd[q], base + q, sc.n, re, im,
+                                                   nullptr, &g);
+                    n_out += (base + q < sc.n && (unsigned)g >= (unsigned)m.n_gates) ? 1 : 0;
+                }
+            }
+        }
+        const unsigned w = __reduce_add_sync(0xffffffffu, (unsigned)n_out);
+        if ((threadIdx.x & 31) == 0 && w != 0)
+            atomicAdd(counts + s0 + j, (unsigned long long)w);
+    }
+}
+
 // ------------------------------------------------------------------------------- backward
 template <bool DOPPLER, bool ANT>
 __global__ void __launch_bounds__(kThreads) backward_split_kernel(
@@ -916,7 +994,7 @@ __global__ void __launch_bounds__(kThreads) backward_split_kernel(
                 DerivF dv;
                 const int key = eval_split<DOPPLER, true, true, ANT>(m, k, it[q], re, im, f, &tab64[j],
                                                                  xo[q], yo[q], &dv);
-                if (key >= 0) {
+                if (key >= 0 && RSIM_CHECK_OK(key < cells, kChkGather, key)) {
                     const float2 g = __ldg(G + (int64_t)s * cells + key);
                     const float cr = fmaf(g.x, re, g.y * im);   // Re(conj(G) C)
                     const float ci = fmaf(g.x, im, -g.y * re);  // Im(conj(G) C)
@@ -983,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads) backward_fp64_kernel(
                 double re, im;
                 DerivD dv;
                 const int key = eval_fp64<DOPPLER, true, ANT>(m, k, it[q], base + q, sc.n, re, im, &dv);
-                if (key >= 0) {
+                if (key >= 0 && RSIM_CHECK_OK(key < cells, kChkGather, key)) {
                     const double2 g = G[(int64_t)s * cells + key];
                     const double cr = g.x * re + g.y * im;
                     const double ci = g.x * im - g.y * re;
@@ -1115,6 +1193,37 @@ cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t
     const dim3 grid((unsigned)blocks, (unsigned)n_real);
     if (fp64) finalize_batched_kernel<double><<<grid, threads, 0, stream>>>(fb, n_vals);
     else finalize_batched_kernel<float><<<grid, threads, 0, stream>>>(fb, n_vals);
+    return cudaGetLastError();
+}
+
+#ifdef RSIM_CHECK
+cudaError_t check_take(cudaStream_t stream, unsigned long long* word) {
+    *word = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(word, g_check_word, sizeof(*word), 0,
+                                              cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess && *word != 0) {
+        static const unsigned long long zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_check_word, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice,
+                                    stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    }
+    return e;
+}
+#endif
+
+cudaError_t launch_window_count(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
+                                bool doppler, unsigned long long* counts, cudaStream_t stream) {
+    const int64_t chunks = (sc.n + kChunk - 1) / kChunk;
+    const dim3 grid((unsigned)chunks, (unsigned)((sch.n_samples + kCountSamples - 1) / kCountSamples));
+    const int f = fp64 ? 1 : 0;
+    if (m.ant) {
+        if (doppler) window_count_kernel<true, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, f, counts);
+        else window_count_kernel<false, true><<<grid, kThreads, 0, stream>>>(m, sch, sc, f, counts);
+    } else {
+        if (doppler) window_count_kernel<true, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, f, counts);
+        else window_count_kernel<false, false><<<grid, kThreads, 0, stream>>>(m, sch, sc, f, counts);
+    }
     return cudaGetLastError();
 }
 

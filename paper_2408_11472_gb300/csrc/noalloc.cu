@@ -152,5 +152,6 @@ extern "C" rsim_status rsim_doppler_accumulate_noalloc(
     const rsim_status st = scratch_for_current_context(&scratch);
     if (st != RSIM_OK) return st;
     return rsim_doppler_accumulate(radar, platform, scat, update0, n_updates, n_fast, n_doppler,
-                                   precision, spectra, scratch, kNoAllocScratchBytes, stream);
+                                   precision, spectra, scratch, kNoAllocScratchBytes, nullptr,
+                                   stream);
 }

@@ -57,6 +57,30 @@ constexpr float kRoundMagic = 12582912.0f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kInvLn2F = 1.44269504088896340736f;
 
+// Debug-build checks (compiled with -DRSIM_CHECK).  A failed check records its code and the
+// offending value in the translation unit's check word (the first failure wins) and skips
+// the access or addition it guards; the entry point reads the word once the call's kernels
+// have run and returns RSIM_ERR_CHECK.  Without RSIM_CHECK every check is the constant true
+// and costs nothing.
+enum CheckCode : unsigned {
+    kChkBin = 1,     // Doppler bin outside [0, n_doppler) when the cell key is formed
+    kChkFixed = 2,   // a contribution sum at or beyond 2^30 (outside the fixed-point range)
+    kChkSample = 3,  // sample slot outside the call's samples
+    kChkGather = 4,  // adjoint gather cell outside [0, n_gates n_doppler)
+};
+#ifdef RSIM_CHECK
+static __device__ unsigned long long g_check_word;
+static __device__ __noinline__ void check_record(unsigned code, long long value) {
+    const unsigned long long w = ((unsigned long long)code << 56) |
+                                 ((unsigned long long)value & ((1ull << 56) - 1ull));
+    atomicCAS(&g_check_word, 0ull, w);
+}
+#define RSIM_CHECK_OK(cond, code, value) \
+    ((cond) || (::rsim::check_record((code), (long long)(value)), false))
+#else
+#define RSIM_CHECK_OK(cond, code, value) (true)
+#endif
+
 // Host-prepared constants of the model (kernel parameter).
 struct Model {
     double prf, inv_prf;
@@ -673,7 +697,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     if (gc_out) *gc_out = gcd;
     if (bc_out) *bc_out = bcd;
     // padding items (past the end of the set) carry zero amplitude: harmless in any cell
-    const int key = ((unsigned)g < (unsigned)m.n_gates) ? g * m.n_doppler + kb : -1;
+    int key = ((unsigned)g < (unsigned)m.n_gates) ? g * m.n_doppler + kb : -1;
+    if (!RSIM_CHECK_OK((unsigned)kb < (unsigned)m.n_doppler, kChkBin, kb)) key = -1;
     return (!GENERAL && (refine || wide)) ? kKeyDeferred : key;
 }
 
@@ -794,8 +819,10 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
         refine1 |= fabsf(bd.y) > fmaf(-fabsf(b.y), kEpsSlope, 0.5f - kBinEps);
     }
     const unsigned cells = (unsigned)(m.n_gates * m.n_doppler);
-    const int c0 = (int)min((unsigned)(g0 * m.n_doppler + kb0), cells);
-    const int c1 = (int)min((unsigned)(g1 * m.n_doppler + kb1), cells);
+    int c0 = (int)min((unsigned)(g0 * m.n_doppler + kb0), cells);
+    int c1 = (int)min((unsigned)(g1 * m.n_doppler + kb1), cells);
+    if (!RSIM_CHECK_OK((unsigned)kb0 < (unsigned)m.n_doppler, kChkBin, kb0)) c0 = (int)cells;
+    if (!RSIM_CHECK_OK((unsigned)kb1 < (unsigned)m.n_doppler, kChkBin, kb1)) c1 = (int)cells;
     const bool d0 = refine0 || (!ANT && qb.x < m.qb_wide);
     const bool d1 = refine1 || (!ANT && qb.y < m.qb_wide);
     key0 = d0 ? kKeyDeferred : c0;
@@ -883,6 +910,7 @@ __device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, con
     if (g_out) *g_out = g;
     if (gc_out) *gc_out = gc;
     if (bc_out) *bc_out = bc;
+    if (!RSIM_CHECK_OK((unsigned)kb < (unsigned)m.n_doppler, kChkBin, kb)) return -1;
     return (n < n_total && g >= 0 && g < m.n_gates) ? g * m.n_doppler + kb : -1;
 }
 
@@ -943,6 +971,9 @@ __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long
 template <typename T>
 __device__ __forceinline__ void emit_cell(unsigned long long* __restrict__ base, int key, T re,
                                           T im) {
+    if (!RSIM_CHECK_OK(fabs((double)re) < 1073741824.0 && fabs((double)im) < 1073741824.0,
+                       kChkFixed, key))
+        return;
     const long long qr = to_fixed(re), qi = to_fixed(im);
     // a zero addend (padding items) is a no-op: not worth a test per emission
     red_add_u64(base + 2 * (int64_t)key, (unsigned long long)qr);

@@ -31,6 +31,14 @@ cudaError_t launch_accumulate_batched_persistent(const Model& m, const Schedule&
                                                  unsigned n_ctas, cudaStream_t stream);
 cudaError_t launch_finalize_batched(const FinalizeBatch& fb, int n_real, int64_t n_vals, bool fp64,
                                     int n_sms, cudaStream_t stream);
+#ifdef RSIM_CHECK
+// -DRSIM_CHECK builds: reads (synchronising `stream`) and clears the check word of the
+// summation kernels' translation unit: 0, or the first failed check (code << 56 | value).
+cudaError_t check_take(cudaStream_t stream, unsigned long long* word);
+#endif
+// counts[s] += scatterers the summation over `sch` leaves out (gate outside the window)
+cudaError_t launch_window_count(const Model& m, const Schedule& sch, const Scat& sc, bool fp64,
+                                bool doppler, unsigned long long* counts, cudaStream_t stream);
 cudaError_t launch_cells(const Model& m, int64_t pulse, bool fp64, bool doppler, const Scat& sc,
                          int32_t* gate, int32_t* bin, double* gc, double* bc, void* contrib,
                          cudaStream_t stream);

@@ -39,8 +39,25 @@ def test_library_exports_every_declared_symbol(L):
         assert name in L.PROTOTYPES, "binding lacks a prototype for %s" % name
 
 
+def test_check_build_flag(L):
+    """librsim_check.so is the same library compiled with -DRSIM_CHECK: it says so, exports
+    the whole boundary and validates arguments on the host exactly as librsim.so does."""
+    assert L.lib.rsim_check_build() == 0
+    chk = L.load(L.CHECK_LIB_PATH)
+    assert chk.rsim_check_build() == 1
+    assert chk.rsim_version() == L.lib.rsim_version()
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+    B = ctypes.byref
+    rd, pf, sc = _structs(L)
+    assert chk.rsim_direct_sum(None, B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, 1 << 20, None,
+                               None) == 1
+    assert b"radar" in chk.rsim_last_error()
+    assert chk.rsim_workspace_size(65, 128, 64) == L.lib.rsim_workspace_size(65, 128, 64)
+
+
 def test_version_and_workspace_size(L):
-    assert L.lib.rsim_version() == 1
+    assert L.lib.rsim_version() == 2
     assert L.lib.rsim_workspace_size(65, 128, 64) == 65 * 128 * 64 * 16
     assert L.lib.rsim_workspace_size(4096, 128, 1) == 4096 * 128 * 16
     assert L.lib.rsim_workspace_size(4, 128, 3) == 0      # not a power of two
@@ -62,24 +79,24 @@ def test_invalid_arguments_are_rejected(L):
     rd, pf, sc = _structs(L)
     lib = L.lib
     # missing structs
-    assert lib.rsim_direct_sum(None, B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, 1 << 20, None) == 1
+    assert lib.rsim_direct_sum(None, B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, 1 << 20, None, None) == 1
     assert b"radar" in lib.rsim_last_error()
     # bad radar
     bad, _, _ = _structs(L, n_gates=0)
-    assert lib.rsim_direct_sum(B(bad), B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, 1 << 20, None) == 1
+    assert lib.rsim_direct_sum(B(bad), B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, 1 << 20, None, None) == 1
     # bad precision
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 7, 0x1000, 0x1000, 1 << 20, None) == 1
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 7, 0x1000, 0x1000, 1 << 20, None, None) == 1
     # negative pulse / count
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), -1, 4, 1, 0x1000, 0x1000, 1 << 20, None) == 1
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, -4, 1, 0x1000, 0x1000, 1 << 20, None) == 1
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), -1, 4, 1, 0x1000, 0x1000, 1 << 20, None, None) == 1
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, -4, 1, 0x1000, 0x1000, 1 << 20, None, None) == 1
     # fast mode: n_fast = 0 is regular mode, n_doppler must be a power of two
     assert lib.rsim_doppler_accumulate(B(rd), B(pf), B(sc), 0, 2, 0, 64, 1, 0x1000, 0x1000,
-                                       1 << 24, None) == 1
+                                       1 << 24, None, None) == 1
     assert lib.rsim_doppler_accumulate(B(rd), B(pf), B(sc), 0, 2, 64, 48, 1, 0x1000, 0x1000,
-                                       1 << 24, None) == 1
+                                       1 << 24, None, None) == 1
     # null scatterer arrays with n > 0
     sc_null = L.Scatterers(16, *([None] * 7), (ctypes.c_double * 3)(0, 0, 0), 1.0)
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc_null), 0, 4, 1, 0x1000, 0x1000, 1 << 20, None) == 1
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc_null), 0, 4, 1, 0x1000, 0x1000, 1 << 20, None, None) == 1
 
 
 def test_workspace_errors(L):
@@ -87,10 +104,26 @@ def test_workspace_errors(L):
     rd, pf, sc = _structs(L)
     lib = L.lib
     need = lib.rsim_workspace_size(4, 128, 1)
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, 0x1000, None, need, None) == 5
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, need - 1, None) == 5
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, 0x1000, 0x1008, need, None) == 5
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, 0x1000, None, need, None, None) == 5
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, need - 1, None, None) == 5
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, 0x1000, 0x1008, need, None, None) == 5
     assert b"workspace" in lib.rsim_last_error()
+
+
+def test_out_of_window_counter_must_be_aligned(L):
+    """The optional out-of-window counter of the two summation calls is checked on the host
+    (8-byte alignment) before any CUDA call."""
+    B = ctypes.byref
+    rd, pf, sc = _structs(L)
+    lib = L.lib
+    need = lib.rsim_workspace_size(4, 128, 1)
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, 0x1000, 0x1000, need, 0x2004,
+                               None) == 1
+    assert b"out_of_window" in lib.rsim_last_error()
+    need = lib.rsim_workspace_size(2, 128, 64)
+    assert lib.rsim_doppler_accumulate(B(rd), B(pf), B(sc), 0, 2, 64, 64, 1, 0x1000, 0x1000,
+                                       need, 0x2002, None) == 1
+    assert b"out_of_window" in lib.rsim_last_error()
 
 
 def test_noalloc_size_limit_is_checked_on_the_host(L):
@@ -131,9 +164,9 @@ def test_empty_work_is_a_noop(L):
     B = ctypes.byref
     rd, pf, sc = _structs(L, n=0)
     lib = L.lib
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, None, None, 0, None) == 0
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 4, 1, None, None, 0, None, None) == 0
     rd, pf, sc = _structs(L)
-    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 0, 1, None, None, 0, None) == 0
+    assert lib.rsim_direct_sum(B(rd), B(pf), B(sc), 0, 0, 1, None, None, 0, None, None) == 0
     assert lib.rsim_synth_pulses(B(rd), None, 0, 0, 64, 64, 0, 0, 1, 1, None, None) == 0
 
 
