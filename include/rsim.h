@@ -389,8 +389,9 @@ typedef struct {
     double g;            /* gravity (m/s^2), > 0 */
 } rsim_wave_spectrum;
 
-/* Workspace bytes of the surface update: a table of omega / (2 pi) (8 L^2 bytes) and two
- * packed L x L complex transforms (16 L^2 bytes). */
+/* Workspace bytes of the surface update: a table of omega / (2 pi) (8 L^2 bytes), two
+ * packed L x L complex transforms (16 L^2 bytes), the transform's twiddles and the wave
+ * numbers (12 L bytes), rounded up to 256 bytes. */
 size_t rsim_surface_workspace_size(int32_t L);
 
 /* Fills the workspace's omega table for `spectrum` (once per spectrum and workspace; the

@@ -608,7 +608,8 @@ static rsim_status surface_args(const rsim_wave_spectrum* sp, rsim::SurfArgs* a)
 
 size_t rsim_surface_workspace_size(int32_t L) {
     if (L < 1) return 0;
-    return (size_t)24 * (size_t)L * (size_t)L;
+    const size_t b = (size_t)24 * (size_t)L * (size_t)L + (size_t)12 * (size_t)L;
+    return (b + 255u) & ~(size_t)255u;
 }
 
 rsim_status rsim_surface_prepare(const rsim_wave_spectrum* spectrum, void* workspace,
@@ -619,8 +620,8 @@ rsim_status rsim_surface_prepare(const rsim_wave_spectrum* spectrum, void* works
     const size_t need = rsim_surface_workspace_size(a.L);
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < need)
         return fail(RSIM_ERR_WORKSPACE, "surface workspace: need %zu bytes, 256-byte aligned", need);
-    const cudaError_t e = rsim::launch_surf_prepare(a, static_cast<float2*>(workspace), device_sms(),
-                                                    stream);
+    const cudaError_t e = rsim::launch_surf_prepare(a, rsim::surf_tables(a.L, workspace),
+                                                    device_sms(), stream);
     if (e != cudaSuccess) return cuda_fail(e, "surface prepare kernel launch");
     return RSIM_OK;
 }
@@ -640,9 +641,8 @@ rsim_status rsim_surface_at(const rsim_wave_spectrum* spectrum, double t, float*
         if (!outs[i] || !aligned(outs[i], 4)) return fail(RSIM_ERR_INVALID_ARG, "output field NULL or misaligned");
     a.t_hi = (float)t;
     a.t_lo = (float)(t - (double)a.t_hi);
-    float2* omega = static_cast<float2*>(workspace);
-    float2* tmp = omega + (size_t)a.L * a.L;
-    const cudaError_t e = rsim::launch_surf_at(a, spectrum->coef, omega, tmp, z, vx, vy, vz, stream);
+    const cudaError_t e = rsim::launch_surf_at(a, spectrum->coef, rsim::surf_tables(a.L, workspace),
+                                               z, vx, vy, vz, stream);
     if (e != cudaSuccess) return cuda_fail(e, "surface kernels launch");
     return RSIM_OK;
 }

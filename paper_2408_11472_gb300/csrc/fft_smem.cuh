@@ -36,6 +36,13 @@ __device__ __forceinline__ void twiddle(int r, int N, double sign, double2& w) {
     sincospi(2.0 * (double)r / (double)N, &s, &c);
     w = make_double2(c, sign * s);
 }
+// Entry n < N of the full table: twiddle(n) for n < N / 2, and -twiddle(n - N / 2) above
+// (W^(n + N/2) = -W^n, exact), so a butterfly reads any power with one look-up.
+__device__ __forceinline__ void twiddle_full(int n, int N, float sign, float2& w) {
+    const int h = N >> 1;
+    twiddle(n < h ? n : n - h, N, sign, w);
+    if (n >= h) w = make_float2(-w.x, -w.y);
+}
 
 // Radix-4 Stockham autosort (a final radix-2 stage when log2 N is odd) over `rows`
 // independent N-point rows in shared memory: half the passes over the data that radix-2
@@ -194,18 +201,28 @@ template <> __device__ __forceinline__ void dft_reg<2>(float2 (&x)[2], float) {
     x[1] = csub(t, x[1]);
 }
 
-// One pass of radix R over `rows` padded rows; U = work units per thread (the caller
-// guarantees rows * N / R <= U * blockDim.x).
+// One pass of radix R over `rows` padded rows, row r at element r * NP; U = work units per
+// thread (the caller guarantees rows * N / R <= U * blockDim.x).  twf: the full table
+// twf[n] = exp(sign j 2 pi n / N), n < N (see twiddle_full).
 template <int R, int U>
 __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, int log2N, int log2s,
-                                                  const float2* __restrict__ tw, float sign) {
+                                                  const float2* __restrict__ twf, float sign,
+                                                  int NP) {
     constexpr int log2R = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
     const int log2nb = log2N - log2R;           // butterflies per row: N / R
     const int nb = 1 << log2nb;
     const int s = 1 << log2s;
     const int m = nb >> log2s;                  // N / (R s)
     const int total = rows << log2nb;
-    const int NP = padded_len(N);
+    // Padded offsets: pad16(i + 16 t) = pad16(i) + 17 t, so when a butterfly's elements are a
+    // multiple of 16 apart their padded offsets are one base plus a fixed stride (no per-element
+    // index arithmetic).  Loads are N / R apart; stores s apart, or consecutive within one
+    // aligned group of 16 when R s = 16.
+    const int ld = nb;                                  // s m = N / R
+    const bool ld_fast = (ld & 15) == 0;
+    const bool st_fast = (s & 15) == 0 || R * s == 16;
+    const int ld_step = ld + (ld >> 4);
+    const int st_step = (s & 15) == 0 ? s + (s >> 4) : s;
     float2 x[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -214,8 +231,14 @@ __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, in
             const int bi = idx & (nb - 1);
             const int p = bi >> log2s, q = bi & (s - 1);
             const float2* ar = a + (idx >> log2nb) * NP;
+            if (ld_fast) {
+                const float2* ab = ar + pad16(q + s * p);
 #pragma unroll
-            for (int k = 0; k < R; ++k) x[u][k] = ar[pad16(q + s * (p + k * m))];
+                for (int k = 0; k < R; ++k) x[u][k] = ab[k * ld_step];
+            } else {
+#pragma unroll
+                for (int k = 0; k < R; ++k) x[u][k] = ar[pad16(q + s * (p + k * m))];
+            }
         }
     }
     __syncthreads();
@@ -229,30 +252,38 @@ __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, in
             dft_reg<R>(x[u], sign);
             const int e = p * s;
             const int o = q + s * (R * p);
-            ar[pad16(o)] = x[u][0];
+            if (st_fast) {
+                float2* ab = ar + pad16(o);
+                ab[0] = x[u][0];
 #pragma unroll
-            for (int j = 1; j < R; ++j) ar[pad16(o + s * j)] = cmul(x[u][j], tw_full(tw, j * e, N));
+                for (int j = 1; j < R; ++j) ab[j * st_step] = cmul(x[u][j], twf[j * e]);
+            } else {
+                ar[pad16(o)] = x[u][0];
+#pragma unroll
+                for (int j = 1; j < R; ++j) ar[pad16(o + s * j)] = cmul(x[u][j], twf[j * e]);
+            }
         }
     }
     __syncthreads();
 }
 
-// The whole transform of `rows` padded rows of N = 2^log2N points (N >= 2).  MAXE bounds
-// the elements per thread: rows * N <= MAXE * blockDim.x (MAXE a multiple of 16).
-// tw[n] = exp(sign j 2 pi n / N) for n < N / 2.  Result in place, natural order.
+// The whole transform of `rows` padded rows of N = 2^log2N points (N >= 2), row r at element
+// r * NP (NP >= padded_len(N)).  MAXE bounds the elements per thread: rows * N <= MAXE *
+// blockDim.x (MAXE a multiple of 16).  twf: the full twiddle table (twiddle_full).  Result in
+// place, natural order.
 template <int MAXE>
-__device__ void fft_rows_reg(float2* a, int rows, int N, int log2N, const float2* __restrict__ tw,
-                             float sign) {
+__device__ void fft_rows_reg(float2* a, int rows, int N, int log2N, const float2* __restrict__ twf,
+                             float sign, int NP) {
     static_assert(MAXE % 16 == 0, "elements per thread");
     int log2s = 0;
     while (log2N - log2s >= 4) {
-        stockham_pass_reg<16, MAXE / 16>(a, rows, N, log2N, log2s, tw, sign);
+        stockham_pass_reg<16, MAXE / 16>(a, rows, N, log2N, log2s, twf, sign, NP);
         log2s += 4;
     }
     switch (log2N - log2s) {
-        case 3: stockham_pass_reg<8, MAXE / 8>(a, rows, N, log2N, log2s, tw, sign); break;
-        case 2: stockham_pass_reg<4, MAXE / 4>(a, rows, N, log2N, log2s, tw, sign); break;
-        case 1: stockham_pass_reg<2, MAXE / 2>(a, rows, N, log2N, log2s, tw, sign); break;
+        case 3: stockham_pass_reg<8, MAXE / 8>(a, rows, N, log2N, log2s, twf, sign, NP); break;
+        case 2: stockham_pass_reg<4, MAXE / 4>(a, rows, N, log2N, log2s, twf, sign, NP); break;
+        case 1: stockham_pass_reg<2, MAXE / 2>(a, rows, N, log2N, log2s, twf, sign, NP); break;
         default: break;
     }
 }

@@ -78,10 +78,20 @@ struct SurfArgs {
     float t_hi, t_lo;            // update time as hi + lo
     float scale_over_L2;         // amplitude scale / L^2
 };
+// The surface workspace: omega / (2 pi) hi + lo [L^2] float2, the two packed transforms
+// [2][L^2] float2, the full twiddle table [L] float2, the wave numbers [L] float.
+struct SurfTables {
+    float2* omega;
+    float2* tmp;
+    float2* twf;
+    float* kf;
+};
+SurfTables surf_tables(int L, void* workspace);
 size_t surf_rows_smem(int L);
 size_t surf_cols_smem(int L, int cols);
-cudaError_t launch_surf_prepare(const SurfArgs& a, float2* omega, int n_sms, cudaStream_t stream);
-cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const float2* omega, float2* tmp,
+cudaError_t launch_surf_prepare(const SurfArgs& a, const SurfTables& t, int n_sms,
+                                cudaStream_t stream);
+cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const SurfTables& t,
                            float* z, float* vx, float* vy, float* vz, cudaStream_t stream);
 
 }  // namespace rsim

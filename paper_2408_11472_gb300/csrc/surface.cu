@@ -42,8 +42,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
-// omega / (2 pi) as hi + lo floats for every grid point.
-__global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega) {
+// The spectrum's tables: omega / (2 pi) as hi + lo floats for every grid point, the wave
+// numbers 2 pi fftfreq(L, spacing) as floats, and the full inverse-transform twiddle table
+// (so that the per-update kernels run no FP64 and no sine per CTA).
+__global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega, float* __restrict__ kf,
+                                    float2* __restrict__ twf) {
     const int64_t n = (int64_t)a.L * a.L;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -52,6 +55,10 @@ __global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega) {
         const double w = sqrt(a.g * sqrt(kx * kx + ky * ky)) / 6.283185307179586476925;
         const float hi = (float)w;
         omega[idx] = make_float2(hi, (float)(w - (double)hi));
+        if (idx < a.L) {
+            kf[idx] = (float)wave_number((int)idx, a.L, a.dk);
+            twiddle_full((int)idx, a.L, 1.0f, twf[idx]);
+        }
     }
 }
 
@@ -65,22 +72,24 @@ constexpr int kColsThreads = 512;   // at most 8192 points: 16 per thread
 template <int TH>
 __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2* __restrict__ coef,
                                                        const float2* __restrict__ omega,
+                                                       const float* __restrict__ kf,
+                                                       const float2* __restrict__ twf_g,
                                                        float2* __restrict__ tmp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = a.L, NP = padded_len(L);
-    float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L)
-    float2* buf0 = tw + (L >> 1);
+    float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L), r < L
+    float2* buf0 = tw + L;
     const int iy = blockIdx.x;
     const int iyn = (L - iy) & (L - 1);                     // row of -k
-    for (int r = threadIdx.x; r < (L >> 1); r += TH) twiddle(r, L, 1.0f, tw[r]);
-    const float ky = (float)wave_number(iy, L, a.dk);
+    for (int r = threadIdx.x; r < L; r += TH) tw[r] = __ldg(twf_g + r);
+    const float ky = __ldg(kf + iy);
     const float2* rowA = coef + (int64_t)iy * L;
     const float2* rowB = coef + (int64_t)iyn * L;
     const float2* rowW = omega + (int64_t)iy * L;
 #pragma unroll 4
     for (int ix = threadIdx.x; ix < L; ix += TH) {
         const int ixn = (L - ix) & (L - 1);
-        const float kx = (float)wave_number(ix, L, a.dk);
+        const float kx = __ldg(kf + ix);
         const float2 A1 = __ldg(rowA + ix);
         const float2 A2 = __ldg(rowB + ixn);
         // e^{-j omega t}: omega t / 2 pi = w t with w = hi + lo, t = t_hi + t_lo
@@ -113,7 +122,7 @@ __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2*
         buf0[NP + pad16(ix)] = make_float2(hx.x - hy.y, hx.y + hy.x);  // H_vx + j H_vy
     }
     __syncthreads();
-    fft_rows_reg<16>(buf0, 2, L, a.log2L, tw, 1.0f);   // 2 L <= 16 x TH
+    fft_rows_reg<16>(buf0, 2, L, a.log2L, tw, 1.0f, NP);   // 2 L <= 16 x TH
 #pragma unroll 4
     for (int ix = threadIdx.x; ix < L; ix += TH) {
         tmp[(int64_t)iy * L + ix] = buf0[pad16(ix)];
@@ -121,33 +130,39 @@ __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2*
     }
 }
 
+// Column stride in shared memory: padded_len(L) + 4 elements, so that the C columns of one
+// row (32 bytes apart per column) fall in different banks when a row is loaded or stored.
+__host__ __device__ constexpr int cols_stride(int L) { return padded_len(L) + 4; }
+
 // Columns pass: one CTA per block of C columns of one packed transform (gridDim.y); the
 // column pieces (32 bytes of every row for C = 4) are copied asynchronously, all of a
 // thread's copies in flight at once.
-__global__ void __launch_bounds__(kColsThreads) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
-                                                        float* __restrict__ z, float* __restrict__ vx,
-                                                        float* __restrict__ vy, float* __restrict__ vz) {
+__global__ void __launch_bounds__(kColsThreads, 2) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
+                                                           const float2* __restrict__ twf_g,
+                                                           float* __restrict__ z, float* __restrict__ vx,
+                                                           float* __restrict__ vy, float* __restrict__ vz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = a.L, C = a.cols, NP = padded_len(L);
+    const int L = a.L, C = a.cols, NP = cols_stride(L);
     float2* tw = reinterpret_cast<float2*>(smem_raw);
-    float2* buf0 = tw + (L >> 1);
+    float2* buf0 = tw + L;
     const int ix0 = blockIdx.x * C;
     const int pair = blockIdx.y;
     const float2* src = tmp + (int64_t)pair * L * L + ix0;
+    const int lc = __ffs(C) - 1;                          // C is a power of two
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        const int iy = idx / C, c = idx - iy * C;
+        const int iy = idx >> lc, c = idx & (C - 1);
         cp_async8(buf0 + c * NP + pad16(iy), src + (int64_t)iy * L + c);
     }
+    for (int r = threadIdx.x; r < L; r += blockDim.x) cp_async8(tw + r, twf_g + r);
     cp_async_commit();
-    for (int r = threadIdx.x; r < (L >> 1); r += blockDim.x) twiddle(r, L, 1.0f, tw[r]);
     cp_async_wait<0>();
     __syncthreads();
-    fft_rows_reg<16>(buf0, C, L, a.log2L, tw, 1.0f);   // C L <= 16 x 512
+    fft_rows_reg<16>(buf0, C, L, a.log2L, tw, 1.0f, NP);   // C L <= 16 x 512
     float* fa = pair == 0 ? z : vx;
     float* fb = pair == 0 ? vz : vy;
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        const int iy = idx / C, c = idx - iy * C;
+        const int iy = idx >> lc, c = idx & (C - 1);
         const float2 v = buf0[c * NP + pad16(iy)];
         const int64_t o = (int64_t)iy * L + ix0 + c;
         fa[o] = v.x * a.scale_over_L2;
@@ -158,21 +173,33 @@ __global__ void __launch_bounds__(kColsThreads) surf_cols_kernel(SurfArgs a, con
 }  // namespace
 
 size_t surf_rows_smem(int L) {
-    return sizeof(float2) * ((size_t)(L / 2) + 2 * (size_t)padded_len(L));
+    return sizeof(float2) * ((size_t)L + 2 * (size_t)padded_len(L));
 }
 size_t surf_cols_smem(int L, int cols) {
-    return sizeof(float2) * ((size_t)(L / 2) + (size_t)cols * padded_len(L));
+    return sizeof(float2) * ((size_t)L + (size_t)cols * cols_stride(L));
 }
 
-cudaError_t launch_surf_prepare(const SurfArgs& a, float2* omega, int n_sms, cudaStream_t stream) {
+SurfTables surf_tables(int L, void* workspace) {
+    SurfTables t;
+    char* base = static_cast<char*>(workspace);
+    const size_t n = (size_t)L * L;
+    t.omega = reinterpret_cast<float2*>(base);
+    t.tmp = reinterpret_cast<float2*>(base + 8 * n);
+    t.twf = reinterpret_cast<float2*>(base + 24 * n);
+    t.kf = reinterpret_cast<float*>(base + 24 * n + 8 * (size_t)L);
+    return t;
+}
+
+cudaError_t launch_surf_prepare(const SurfArgs& a, const SurfTables& t, int n_sms,
+                                cudaStream_t stream) {
     const int64_t n = (int64_t)a.L * a.L;
     const int64_t want = (n + 255) / 256;
     const unsigned blocks = (unsigned)(want < (int64_t)n_sms * 8 ? want : (int64_t)n_sms * 8);
-    surf_prepare_kernel<<<blocks, 256, 0, stream>>>(a, omega);
+    surf_prepare_kernel<<<blocks, 256, 0, stream>>>(a, t.omega, t.kf, t.twf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const float2* omega, float2* tmp,
+cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const SurfTables& t,
                            float* z, float* vx, float* vy, float* vz, cudaStream_t stream) {
     const size_t s1 = surf_rows_smem(a.L), s2 = surf_cols_smem(a.L, a.cols);
     cudaError_t e;
@@ -190,12 +217,13 @@ cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const float2* om
         return e;
     if (big)
         surf_rows_kernel<kRowsThreadsBig><<<(unsigned)a.L, kRowsThreadsBig, s1, stream>>>(
-            a, static_cast<const float2*>(coef), omega, tmp);
+            a, static_cast<const float2*>(coef), t.omega, t.kf, t.twf, t.tmp);
     else
         surf_rows_kernel<kRowsThreads><<<(unsigned)a.L, kRowsThreads, s1, stream>>>(
-            a, static_cast<const float2*>(coef), omega, tmp);
+            a, static_cast<const float2*>(coef), t.omega, t.kf, t.twf, t.tmp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), kColsThreads, s2, stream>>>(a, tmp, z, vx, vy, vz);
+    surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), kColsThreads, s2, stream>>>(
+        a, t.tmp, t.twf, z, vx, vy, vz);
     return cudaGetLastError();
 }
 

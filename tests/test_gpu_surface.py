@@ -22,10 +22,10 @@ def rsim():
 
 # every pass plan of the mixed-radix transforms: 4 (radix 4), 8 (8), 16 (16), 32 (16, 2),
 # 64 (16, 4), 128 (16, 8), 256 (16, 16), 512 (16, 16, 2), 1024 (16, 16, 4),
-# 4096 (16, 16, 16; two columns per block)
+# 2048 (16, 16, 8), 4096 (16, 16, 16; two columns per block)
 @pytest.mark.parametrize("L,spacing", [(64, 1.0), (256, 1.0), (128, 2.5), (4, 1.0), (8, 1.0),
                                        (16, 1.0), (32, 2.0), (512, 1.0), (1024, 1.0),
-                                       (4096, 1.0)])
+                                       (2048, 1.0), (4096, 1.0)])
 def test_fields_match_oracle(rsim, L, spacing):
     spec = sg.sea_spectrum(L, 40 + L, spacing=spacing)
     surf = rsim.EvolvingSurface(spec)
