@@ -223,6 +223,7 @@ __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, in
     const bool st_fast = (s & 15) == 0 || R * s == 16;
     const int ld_step = ld + (ld >> 4);
     const int st_step = (s & 15) == 0 ? s + (s >> 4) : s;
+    const bool last = log2s + log2R == log2N;
     float2 x[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -252,15 +253,36 @@ __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, in
             dft_reg<R>(x[u], sign);
             const int e = p * s;
             const int o = q + s * (R * p);
+            // the last pass (s = N / R, so p = 0) has unit twiddles
+            if (!last) {
+                if (R == 16) {
+                    // w^j from the four table powers w, w^2, w^4, w^8 (at most three products
+                    // each): four shared-memory reads per butterfly instead of fifteen
+                    float2 w[R];
+                    w[1] = twf[e];
+                    w[2] = twf[2 * e];
+                    w[4] = twf[4 * e];
+                    w[8] = twf[8 * e];
+                    w[3] = cmul(w[1], w[2]);
+                    w[5] = cmul(w[1], w[4]);
+                    w[6] = cmul(w[2], w[4]);
+                    w[7] = cmul(w[3], w[4]);
+#pragma unroll
+                    for (int j = 9; j < 16; ++j) w[j] = cmul(w[j - 8], w[8]);
+#pragma unroll
+                    for (int j = 1; j < R; ++j) x[u][j] = cmul(x[u][j], w[j]);
+                } else {
+#pragma unroll
+                    for (int j = 1; j < R; ++j) x[u][j] = cmul(x[u][j], twf[j * e]);
+                }
+            }
             if (st_fast) {
                 float2* ab = ar + pad16(o);
-                ab[0] = x[u][0];
 #pragma unroll
-                for (int j = 1; j < R; ++j) ab[j * st_step] = cmul(x[u][j], twf[j * e]);
+                for (int j = 0; j < R; ++j) ab[j * st_step] = x[u][j];
             } else {
-                ar[pad16(o)] = x[u][0];
 #pragma unroll
-                for (int j = 1; j < R; ++j) ar[pad16(o + s * j)] = cmul(x[u][j], twf[j * e]);
+                for (int j = 0; j < R; ++j) ar[pad16(o + s * j)] = x[u][j];
             }
         }
     }

@@ -9,9 +9,9 @@
 // H(k) = (X(k) + conj(X(-k))) / 2 of its spectrum X, so two real fields share one complex
 // transform: IFFT2[H_a + j H_b] = a + j b.  Two packed transforms (eta + j v_z,
 // v_x + j v_y) per update:
-//   rows pass    : one CTA per row iy builds both packed rows from A(k), A(-k) and the
-//                  phase e^{-j omega t} (read straight from global memory) and transforms
-//                  them along x (shared memory);
+//   rows pass    : one CTA per pair of rows iy, -iy builds the packed rows of both from
+//                  A(k), A(-k) and the phase e^{-j omega t} (read straight from global
+//                  memory; H(-k) = conj(H(k))) and transforms them along x (shared memory);
 //   columns pass : one CTA per block of columns (32 bytes of every row) transforms along y
 //                  and writes the fields.
 // Both passes use the register mixed-radix transform (radix-16 passes, one shared-memory
@@ -62,13 +62,17 @@ __global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega, floa
     }
 }
 
-constexpr int kRowsThreads = 256;   // two rows of at most 2048 points: 16 per thread
-constexpr int kRowsThreadsBig = 512; // two rows of 4096 points
-constexpr int kColsThreads = 512;   // at most 8192 points: 16 per thread
+constexpr int kRowsThreads = 512;    // rows k and -k, two packed transforms: 4 rows of <= 2048
+constexpr int kRowsThreadsBig = 1024; // 4 rows of 4096 points
+constexpr int kColsThreads = 512;    // at most 8192 points: 16 per thread
 
-// Rows pass: one CTA per row iy.  The coefficients of rows iy and -iy and the omega row are
-// read straight from global memory (coalesced; the row of -k in reverse order) into the
-// two packed rows in shared memory, which then hold the only shared-memory copy.
+// Rows pass: one CTA per pair of rows iy and -iy (rows 0 and L/2 are their own partners).
+// The coefficients of both rows and the omega row of iy are read straight from global memory
+// (coalesced; the row of -k in reverse order).  Each grid point k gives the Hermitian parts
+// H(k) of the four spectra, and H(-k) = conj(H(k)) exactly, so one evaluation fills both
+// rows' entries: half the coefficient reads and half the phase work of a CTA per row.  The
+// packed rows (eta + j v_z, v_x + j v_y of row iy, then of row -iy) hold the only
+// shared-memory copy.
 template <int TH>
 __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2* __restrict__ coef,
                                                        const float2* __restrict__ omega,
@@ -79,8 +83,9 @@ __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2*
     const int L = a.L, NP = padded_len(L);
     float2* tw = reinterpret_cast<float2*>(smem_raw);     // exp(+j 2 pi r / L), r < L
     float2* buf0 = tw + L;
-    const int iy = blockIdx.x;
+    const int iy = blockIdx.x;                              // 0 .. L / 2
     const int iyn = (L - iy) & (L - 1);                     // row of -k
+    const bool pair = iyn != iy;
     for (int r = threadIdx.x; r < L; r += TH) tw[r] = __ldg(twf_g + r);
     const float ky = __ldg(kf + iy);
     const float2* rowA = coef + (int64_t)iy * L;
@@ -120,13 +125,22 @@ __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2*
                                       0.5f * om * fmaf(uy, F1.y, -uyn * F2.y));
         buf0[pad16(ix)] = make_float2(he.x - hz.y, he.y + hz.x);       // H_eta + j H_vz
         buf0[NP + pad16(ix)] = make_float2(hx.x - hy.y, hx.y + hy.x);  // H_vx + j H_vy
+        if (pair) {  // at -n: conj(H_eta) + j conj(H_vz), conj(H_vx) + j conj(H_vy)
+            buf0[2 * NP + pad16(ixn)] = make_float2(he.x + hz.y, hz.x - he.y);
+            buf0[3 * NP + pad16(ixn)] = make_float2(hx.x + hy.y, hy.x - hx.y);
+        }
     }
     __syncthreads();
-    fft_rows_reg<16>(buf0, 2, L, a.log2L, tw, 1.0f, NP);   // 2 L <= 16 x TH
+    const int rows = pair ? 4 : 2;
+    fft_rows_reg<16>(buf0, rows, L, a.log2L, tw, 1.0f, NP);   // rows L <= 16 x TH
 #pragma unroll 4
     for (int ix = threadIdx.x; ix < L; ix += TH) {
         tmp[(int64_t)iy * L + ix] = buf0[pad16(ix)];
         tmp[(int64_t)L * L + (int64_t)iy * L + ix] = buf0[NP + pad16(ix)];
+        if (pair) {
+            tmp[(int64_t)iyn * L + ix] = buf0[2 * NP + pad16(ix)];
+            tmp[(int64_t)L * L + (int64_t)iyn * L + ix] = buf0[3 * NP + pad16(ix)];
+        }
     }
 }
 
@@ -173,7 +187,7 @@ __global__ void __launch_bounds__(kColsThreads, 2) surf_cols_kernel(SurfArgs a, 
 }  // namespace
 
 size_t surf_rows_smem(int L) {
-    return sizeof(float2) * ((size_t)L + 2 * (size_t)padded_len(L));
+    return sizeof(float2) * ((size_t)L + 4 * (size_t)padded_len(L));
 }
 size_t surf_cols_smem(int L, int cols) {
     return sizeof(float2) * ((size_t)L + (size_t)cols * cols_stride(L));
@@ -215,11 +229,12 @@ cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const SurfTables
         (e = cudaFuncSetAttribute(surf_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)s2)) != cudaSuccess)
         return e;
+    const unsigned row_pairs = (unsigned)(a.L / 2 + 1);   // rows 0 .. L/2 with their partners
     if (big)
-        surf_rows_kernel<kRowsThreadsBig><<<(unsigned)a.L, kRowsThreadsBig, s1, stream>>>(
+        surf_rows_kernel<kRowsThreadsBig><<<row_pairs, kRowsThreadsBig, s1, stream>>>(
             a, static_cast<const float2*>(coef), t.omega, t.kf, t.twf, t.tmp);
     else
-        surf_rows_kernel<kRowsThreads><<<(unsigned)a.L, kRowsThreads, s1, stream>>>(
+        surf_rows_kernel<kRowsThreads><<<row_pairs, kRowsThreads, s1, stream>>>(
             a, static_cast<const float2*>(coef), t.omega, t.kf, t.twf, t.tmp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), kColsThreads, s2, stream>>>(
