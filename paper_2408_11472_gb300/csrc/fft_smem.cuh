@@ -201,6 +201,25 @@ template <> __device__ __forceinline__ void dft_reg<2>(float2 (&x)[2], float) {
     x[1] = csub(t, x[1]);
 }
 
+// x[j] *= w^(j e), j = 1..15, with w^(j e) from the four table entries twf[e], twf[2e],
+// twf[4e], twf[8e] (at most three products each): four shared-memory reads per radix-16
+// butterfly instead of fifteen.
+__device__ __forceinline__ void twiddle16(float2 (&x)[16], const float2* __restrict__ twf, int e) {
+    float2 w[16];
+    w[1] = twf[e];
+    w[2] = twf[2 * e];
+    w[4] = twf[4 * e];
+    w[8] = twf[8 * e];
+    w[3] = cmul(w[1], w[2]);
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+#pragma unroll
+    for (int j = 9; j < 16; ++j) w[j] = cmul(w[j - 8], w[8]);
+#pragma unroll
+    for (int j = 1; j < 16; ++j) x[j] = cmul(x[j], w[j]);
+}
+
 // One pass of radix R over `rows` padded rows, row r at element r * NP; U = work units per
 // thread (the caller guarantees rows * N / R <= U * blockDim.x).  twf: the full table
 // twf[n] = exp(sign j 2 pi n / N), n < N (see twiddle_full).
@@ -255,22 +274,8 @@ __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, in
             const int o = q + s * (R * p);
             // the last pass (s = N / R, so p = 0) has unit twiddles
             if (!last) {
-                if (R == 16) {
-                    // w^j from the four table powers w, w^2, w^4, w^8 (at most three products
-                    // each): four shared-memory reads per butterfly instead of fifteen
-                    float2 w[R];
-                    w[1] = twf[e];
-                    w[2] = twf[2 * e];
-                    w[4] = twf[4 * e];
-                    w[8] = twf[8 * e];
-                    w[3] = cmul(w[1], w[2]);
-                    w[5] = cmul(w[1], w[4]);
-                    w[6] = cmul(w[2], w[4]);
-                    w[7] = cmul(w[3], w[4]);
-#pragma unroll
-                    for (int j = 9; j < 16; ++j) w[j] = cmul(w[j - 8], w[8]);
-#pragma unroll
-                    for (int j = 1; j < R; ++j) x[u][j] = cmul(x[u][j], w[j]);
+                if constexpr (R == 16) {
+                    twiddle16(x[u], twf, e);
                 } else {
 #pragma unroll
                     for (int j = 1; j < R; ++j) x[u][j] = cmul(x[u][j], twf[j * e]);
@@ -295,9 +300,9 @@ __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, in
 // place, natural order.
 template <int MAXE>
 __device__ void fft_rows_reg(float2* a, int rows, int N, int log2N, const float2* __restrict__ twf,
-                             float sign, int NP) {
+                             float sign, int NP, int log2s0 = 0) {
     static_assert(MAXE % 16 == 0, "elements per thread");
-    int log2s = 0;
+    int log2s = log2s0;   // > 0: the first passes were done by the caller
     while (log2N - log2s >= 4) {
         stockham_pass_reg<16, MAXE / 16>(a, rows, N, log2N, log2s, twf, sign, NP);
         log2s += 4;

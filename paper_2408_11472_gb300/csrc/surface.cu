@@ -163,15 +163,37 @@ __global__ void __launch_bounds__(kColsThreads, 2) surf_cols_kernel(SurfArgs a, 
     const int pair = blockIdx.y;
     const float2* src = tmp + (int64_t)pair * L * L + ix0;
     const int lc = __ffs(C) - 1;                          // C is a power of two
-    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        const int iy = idx >> lc, c = idx & (C - 1);
-        cp_async8(buf0 + c * NP + pad16(iy), src + (int64_t)iy * L + c);
-    }
     for (int r = threadIdx.x; r < L; r += blockDim.x) cp_async8(tw + r, twf_g + r);
     cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    fft_rows_reg<16>(buf0, C, L, a.log2L, tw, 1.0f, NP);   // C L <= 16 x 512
+    int log2s0 = 0;
+    if (C * (L >> 4) == (int)blockDim.x && a.log2L >= 8) {
+        // first radix-16 pass straight from global memory: butterfly p of column c takes rows
+        // p + k L / 16 (the C columns of a row are adjacent in memory and in the warp, so four
+        // threads read one 32-byte sector); written to the padded columns in shared memory
+        const int nb = L >> 4;
+        const int c = threadIdx.x & (C - 1), p = threadIdx.x >> lc;   // one butterfly each
+        float2 x[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = __ldg(src + (int64_t)(p + k * nb) * L + c);
+        cp_async_wait<0>();
+        __syncthreads();                                  // the twiddle table is in place
+        dft_reg<16>(x, 1.0f);
+        twiddle16(x, tw, p);
+        float2* ab = buf0 + c * NP + pad16(16 * p);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) ab[j] = x[j];
+        __syncthreads();
+        log2s0 = 4;
+    } else {
+        for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+            const int iy = idx >> lc, cc = idx & (C - 1);
+            cp_async8(buf0 + cc * NP + pad16(iy), src + (int64_t)iy * L + cc);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+    fft_rows_reg<16>(buf0, C, L, a.log2L, tw, 1.0f, NP, log2s0);   // C L <= 16 x 512
     float* fa = pair == 0 ? z : vx;
     float* fb = pair == 0 ? vz : vy;
 #pragma unroll 4
