@@ -819,8 +819,9 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
         refine1 |= fabsf(bd.y) > fmaf(-fabsf(b.y), kEpsSlope, 0.5f - kBinEps);
     }
     const unsigned cells = (unsigned)(m.n_gates * m.n_doppler);
-    int c0 = (int)min((unsigned)(g0 * m.n_doppler + kb0), cells);
-    int c1 = (int)min((unsigned)(g1 * m.n_doppler + kb1), cells);
+    // (without DOPPLER there is one bin: n_doppler = 1, key = gate)
+    int c0 = (int)min((unsigned)(DOPPLER ? g0 * m.n_doppler + kb0 : g0), cells);
+    int c1 = (int)min((unsigned)(DOPPLER ? g1 * m.n_doppler + kb1 : g1), cells);
     if (!RSIM_CHECK_OK((unsigned)kb0 < (unsigned)m.n_doppler, kChkBin, kb0)) c0 = (int)cells;
     if (!RSIM_CHECK_OK((unsigned)kb1 < (unsigned)m.n_doppler, kChkBin, kb1)) c1 = (int)cells;
     const bool d0 = refine0 || (!ANT && qb.x < m.qb_wide);
