@@ -596,7 +596,7 @@ static rsim_status surface_args(const rsim_wave_spectrum* sp, rsim::SurfArgs* a)
     a->log2L = 0;
     while ((1 << a->log2L) < sp->L) ++a->log2L;
     int c = 8;
-    while (c > 1 && ((int64_t)c * sp->L > 8192 || c > sp->L)) c >>= 1;  // one 64 KB buffer per CTA
+    while (c > 1 && ((int64_t)c * sp->L > 16384 || c > sp->L)) c >>= 1;  // <= 16384 points per CTA
     a->cols = c;
     a->dk = 6.283185307179586476925 / ((double)sp->L * sp->spacing);
     a->g = sp->g;

@@ -315,5 +315,69 @@ __device__ void fft_rows_reg(float2* a, int rows, int N, int log2N, const float2
     }
 }
 
+// All passes of fft_rows_reg but the last (from log2s0); returns the log2 stride of the last
+// pass, whose radix is 2^(log2N - returned value), one of 2, 4, 8, 16 (N >= 2).
+template <int MAXE>
+__device__ int fft_rows_reg_but_last(float2* a, int rows, int N, int log2N,
+                                     const float2* __restrict__ twf, float sign, int NP,
+                                     int log2s0 = 0) {
+    int log2s = log2s0;
+    while (log2N - log2s > 4) {
+        stockham_pass_reg<16, MAXE / 16>(a, rows, N, log2N, log2s, twf, sign, NP);
+        log2s += 4;
+    }
+    return log2s;
+}
+
+// The last pass (radix R, stride s = N / R, unit twiddles) of `rows` padded rows that went
+// through the others, handing output element n = q + s j of row `row` to store(row, n, value)
+// instead of writing it back to shared memory: butterfly (row, q) reads elements q + s k.
+// ROW_FAST: consecutive threads take consecutive rows (rows = 2^lr), so that one output index
+// of several rows is stored by adjacent threads; otherwise consecutive q.  U: rows * s <= U *
+// blockDim.x.  The caller's last barrier is stockham_pass_reg's.
+template <int R, int U, bool ROW_FAST, typename Store>
+__device__ __forceinline__ void last_pass_store(const float2* a, int rows, int lr, int log2N,
+                                                int NP, float sign, Store store) {
+    constexpr int log2R = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
+    const int log2s = log2N - log2R, sd = 1 << log2s;
+    const int total = rows << log2s;
+    const bool fast = (sd & 15) == 0;
+    const int ld_step = sd + (sd >> 4);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = threadIdx.x + u * blockDim.x;
+        if (idx < total) {
+            const int row = ROW_FAST ? (idx & (rows - 1)) : (idx >> log2s);
+            const int q = ROW_FAST ? (idx >> lr) : (idx & (sd - 1));
+            const float2* ar = a + row * NP;
+            float2 x[R];
+            if (fast) {
+                const float2* ab = ar + pad16(q);
+#pragma unroll
+                for (int k = 0; k < R; ++k) x[k] = ab[k * ld_step];
+            } else {
+#pragma unroll
+                for (int k = 0; k < R; ++k) x[k] = ar[pad16(q + sd * k)];
+            }
+            dft_reg<R>(x, sign);
+#pragma unroll
+            for (int j = 0; j < R; ++j) store(row, q + sd * j, x[j]);
+        }
+    }
+}
+
+// The last pass of fft_rows_reg_but_last's rows with its outputs sent to store (see
+// last_pass_store); MAXE as fft_rows_reg.
+template <int MAXE, bool ROW_FAST, typename Store>
+__device__ __forceinline__ void fft_last_pass_store(const float2* a, int rows, int lr, int log2N,
+                                                    int log2s, int NP, float sign, Store store) {
+    switch (log2N - log2s) {
+        case 4: last_pass_store<16, MAXE / 16, ROW_FAST>(a, rows, lr, log2N, NP, sign, store); break;
+        case 3: last_pass_store<8, MAXE / 8, ROW_FAST>(a, rows, lr, log2N, NP, sign, store); break;
+        case 2: last_pass_store<4, MAXE / 4, ROW_FAST>(a, rows, lr, log2N, NP, sign, store); break;
+        default: last_pass_store<2, MAXE / 2, ROW_FAST>(a, rows, lr, log2N, NP, sign, store); break;
+    }
+}
+
 }  // namespace fft
 }  // namespace rsim

@@ -64,7 +64,7 @@ __global__ void surf_prepare_kernel(SurfArgs a, float2* __restrict__ omega, floa
 
 constexpr int kRowsThreads = 512;    // rows k and -k, two packed transforms: 4 rows of <= 2048
 constexpr int kRowsThreadsBig = 1024; // 4 rows of 4096 points
-constexpr int kColsThreads = 512;    // at most 8192 points: 16 per thread
+constexpr int kColsMaxThreads = 1024; // at most 16384 points (C columns of L): 16 per thread
 
 // Rows pass: one CTA per pair of rows iy and -iy (rows 0 and L/2 are their own partners).
 // The coefficients of both rows and the omega row of iy are read straight from global memory
@@ -132,26 +132,26 @@ __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2*
     }
     __syncthreads();
     const int rows = pair ? 4 : 2;
-    fft_rows_reg<16>(buf0, rows, L, a.log2L, tw, 1.0f, NP);   // rows L <= 16 x TH
-#pragma unroll 4
-    for (int ix = threadIdx.x; ix < L; ix += TH) {
-        tmp[(int64_t)iy * L + ix] = buf0[pad16(ix)];
-        tmp[(int64_t)L * L + (int64_t)iy * L + ix] = buf0[NP + pad16(ix)];
-        if (pair) {
-            tmp[(int64_t)iyn * L + ix] = buf0[2 * NP + pad16(ix)];
-            tmp[(int64_t)L * L + (int64_t)iyn * L + ix] = buf0[3 * NP + pad16(ix)];
-        }
-    }
+    // rows L <= 16 x TH; the last pass writes the transformed rows straight to global memory
+    // (consecutive threads: consecutive points of a row)
+    const int log2s = fft_rows_reg_but_last<16>(buf0, rows, L, a.log2L, tw, 1.0f, NP);
+    fft_last_pass_store<16, false>(buf0, rows, 0, a.log2L, log2s, NP, 1.0f,
+                                   [&](int row, int n, float2 v) {
+        const int y = (row & 2) ? iyn : iy;                 // rows: iy, iy, -iy, -iy
+        tmp[(int64_t)(row & 1) * L * L + (int64_t)y * L + n] = v;
+    });
 }
 
 // Column stride in shared memory: padded_len(L) + 4 elements, so that the C columns of one
-// row (32 bytes apart per column) fall in different banks when a row is loaded or stored.
+// row (32 bytes apart per column) fall in different bank groups when a row is stored or read.
 __host__ __device__ constexpr int cols_stride(int L) { return padded_len(L) + 4; }
 
-// Columns pass: one CTA per block of C columns of one packed transform (gridDim.y); the
-// column pieces (32 bytes of every row for C = 4) are copied asynchronously, all of a
-// thread's copies in flight at once.
-__global__ void __launch_bounds__(kColsThreads, 2) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
+// Columns pass: one CTA per block of C columns of one packed transform (gridDim.y), one
+// radix-16 butterfly per thread (C L / 16 threads).  For L >= 256 the first pass reads its
+// butterflies straight from global memory (the C columns of a row side by side: 64 bytes for
+// C = 8) and the last pass writes the fields straight back; the passes between run in shared
+// memory.
+__global__ void __launch_bounds__(kColsMaxThreads) surf_cols_kernel(SurfArgs a, const float2* __restrict__ tmp,
                                                            const float2* __restrict__ twf_g,
                                                            float* __restrict__ z, float* __restrict__ vx,
                                                            float* __restrict__ vy, float* __restrict__ vz) {
@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(kColsThreads, 2) surf_cols_kernel(SurfArgs a, 
     int log2s0 = 0;
     if (C * (L >> 4) == (int)blockDim.x && a.log2L >= 8) {
         // first radix-16 pass straight from global memory: butterfly p of column c takes rows
-        // p + k L / 16 (the C columns of a row are adjacent in memory and in the warp, so four
-        // threads read one 32-byte sector); written to the padded columns in shared memory
+        // p + k L / 16 (the C columns of a row are adjacent in memory and in the warp);
+        // written to the padded columns in shared memory
         const int nb = L >> 4;
         const int c = threadIdx.x & (C - 1), p = threadIdx.x >> lc;   // one butterfly each
         float2 x[16];
@@ -193,17 +193,18 @@ __global__ void __launch_bounds__(kColsThreads, 2) surf_cols_kernel(SurfArgs a, 
         cp_async_wait<0>();
         __syncthreads();
     }
-    fft_rows_reg<16>(buf0, C, L, a.log2L, tw, 1.0f, NP, log2s0);   // C L <= 16 x 512
     float* fa = pair == 0 ? z : vx;
     float* fb = pair == 0 ? vz : vy;
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        const int iy = idx >> lc, c = idx & (C - 1);
-        const float2 v = buf0[c * NP + pad16(iy)];
+    // C L <= 16 x blockDim.x; the last pass writes the fields straight to global memory, the
+    // C columns of one row from adjacent threads (32 bytes per row and field for C = 8)
+    const int log2s = fft_rows_reg_but_last<16>(buf0, C, L, a.log2L, tw, 1.0f, NP, log2s0);
+    const float sc = a.scale_over_L2;
+    fft_last_pass_store<16, true>(buf0, C, lc, a.log2L, log2s, NP, 1.0f,
+                                  [&](int c, int iy, float2 v) {
         const int64_t o = (int64_t)iy * L + ix0 + c;
-        fa[o] = v.x * a.scale_over_L2;
-        fb[o] = v.y * a.scale_over_L2;
-    }
+        fa[o] = v.x * sc;
+        fb[o] = v.y * sc;
+    });
 }
 
 }  // namespace
@@ -259,7 +260,10 @@ cudaError_t launch_surf_at(const SurfArgs& a, const void* coef, const SurfTables
         surf_rows_kernel<kRowsThreads><<<row_pairs, kRowsThreads, s1, stream>>>(
             a, static_cast<const float2*>(coef), t.omega, t.kf, t.twf, t.tmp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), kColsThreads, s2, stream>>>(
+    int cols_threads = a.cols * a.L / 16;                 // one radix-16 butterfly per thread
+    cols_threads = cols_threads < 32 ? 32 : (cols_threads + 31) / 32 * 32;
+    if (cols_threads > kColsMaxThreads) return cudaErrorInvalidValue;
+    surf_cols_kernel<<<dim3((unsigned)(a.L / a.cols), 2), cols_threads, s2, stream>>>(
         a, t.tmp, t.twf, z, vx, vy, vz);
     return cudaGetLastError();
 }
