@@ -42,6 +42,34 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
+// L2 eviction priorities (createpolicy + .L2::cache_hint): the row pass writes the packed
+// intermediate (64 MB at L = 2048) as evict_last so that the column pass finds it in L2, and
+// the data read or written once (coefficients, omega table, the intermediate's second read,
+// the fields) go as evict_first.
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float2 ld_l2hint(const float2* p, unsigned long long pol) {
+    float2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+        : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_l2hint(float2* p, float2 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_l2hint(float* p, float v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" :: "l"(p), "f"(v), "l"(pol) : "memory");
+}
+
 // The spectrum's tables: omega / (2 pi) as hi + lo floats for every grid point, the wave
 // numbers 2 pi fftfreq(L, spacing) as floats, and the full inverse-transform twiddle table
 // (so that the per-update kernels run no FP64 and no sine per CTA).
@@ -91,14 +119,15 @@ __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2*
     const float2* rowA = coef + (int64_t)iy * L;
     const float2* rowB = coef + (int64_t)iyn * L;
     const float2* rowW = omega + (int64_t)iy * L;
+    const unsigned long long first = l2_evict_first(), last = l2_evict_last();
 #pragma unroll 4
     for (int ix = threadIdx.x; ix < L; ix += TH) {
         const int ixn = (L - ix) & (L - 1);
         const float kx = __ldg(kf + ix);
-        const float2 A1 = __ldg(rowA + ix);
-        const float2 A2 = __ldg(rowB + ixn);
+        const float2 A1 = ld_l2hint(rowA + ix, first);
+        const float2 A2 = ld_l2hint(rowB + ixn, first);
         // e^{-j omega t}: omega t / 2 pi = w t with w = hi + lo, t = t_hi + t_lo
-        const float2 w = __ldg(rowW + ix);
+        const float2 w = ld_l2hint(rowW + ix, first);
         const float p = w.x * a.t_hi;
         const float pe = fmaf(w.x, a.t_hi, -p);
         float f = (p - rintf(p)) + (pe + fmaf(w.x, a.t_lo, w.y * a.t_hi));
@@ -138,7 +167,7 @@ __global__ void __launch_bounds__(TH) surf_rows_kernel(SurfArgs a, const float2*
     fft_last_pass_store<16, false>(buf0, rows, 0, a.log2L, log2s, NP, 1.0f,
                                    [&](int row, int n, float2 v) {
         const int y = (row & 2) ? iyn : iy;                 // rows: iy, iy, -iy, -iy
-        tmp[(int64_t)(row & 1) * L * L + (int64_t)y * L + n] = v;
+        st_l2hint(tmp + (int64_t)(row & 1) * L * L + (int64_t)y * L + n, v, last);
     });
 }
 
@@ -173,8 +202,9 @@ __global__ void __launch_bounds__(kColsMaxThreads) surf_cols_kernel(SurfArgs a, 
         const int nb = L >> 4;
         const int c = threadIdx.x & (C - 1), p = threadIdx.x >> lc;   // one butterfly each
         float2 x[16];
+        const unsigned long long first = l2_evict_first();
 #pragma unroll
-        for (int k = 0; k < 16; ++k) x[k] = __ldg(src + (int64_t)(p + k * nb) * L + c);
+        for (int k = 0; k < 16; ++k) x[k] = ld_l2hint(src + (int64_t)(p + k * nb) * L + c, first);
         cp_async_wait<0>();
         __syncthreads();                                  // the twiddle table is in place
         dft_reg<16>(x, 1.0f);
@@ -199,11 +229,12 @@ __global__ void __launch_bounds__(kColsMaxThreads) surf_cols_kernel(SurfArgs a, 
     // C columns of one row from adjacent threads (32 bytes per row and field for C = 8)
     const int log2s = fft_rows_reg_but_last<16>(buf0, C, L, a.log2L, tw, 1.0f, NP, log2s0);
     const float sc = a.scale_over_L2;
+    const unsigned long long out_pol = l2_evict_first();
     fft_last_pass_store<16, true>(buf0, C, lc, a.log2L, log2s, NP, 1.0f,
                                   [&](int c, int iy, float2 v) {
         const int64_t o = (int64_t)iy * L + ix0 + c;
-        fa[o] = v.x * sc;
-        fb[o] = v.y * sc;
+        st_l2hint(fa + o, v.x * sc, out_pol);
+        st_l2hint(fb + o, v.y * sc, out_pol);
     });
 }
 
