@@ -782,7 +782,9 @@ class EvolvingFastMode:
 
     def __init__(self, radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
                  n_doppler: int, window: str = "sqrt_raised_cosine", precision: str = "split",
-                 pulse0: int = 0):
+                 pulse0: int = 0, block: int = EVOLVING_BLOCK):
+        if not 1 <= block <= _lib.MAX_STATES:
+            raise ValueError("block must be in [1, %d]" % _lib.MAX_STATES)
         self.radar, self.platform, self.surface = radar, platform, surface
         self.n_pulses, self.n_fast, self.n_doppler = n_pulses, n_fast, n_doppler
         self.window, self.precision, self.pulse0 = window, precision, pulse0
@@ -795,7 +797,7 @@ class EvolvingFastMode:
                                      dtype=torch.uint8, device=dev)
         # two groups of field sets and a side stream: block b + 1 is synthesised while block b
         # is summed
-        K = max(1, min(self.S, EVOLVING_BLOCK))
+        K = max(1, min(self.S, block))
         self.groups = [surface.field_sets(K), surface.field_sets(K)]
         self.side = torch.cuda.Stream(device=dev)
         self.graph = None

@@ -98,6 +98,25 @@ __device__ __forceinline__ void item_motion(const Model& m, ItemF& it, float3 dq
     it.beta = fmaf(vx, ex, fmaf(vy, ey, vz * ez)) + epv;
 }
 
+// item_motion for two items as the lanes of packed FP32 pairs: the same operations in the
+// same order, each lane rounded as the scalar operation (negations moved onto the constants
+// are exact), so each lane's gam and beta equal item_motion's, which the deferred exact
+// re-evaluation uses.
+__device__ __forceinline__ void item_motion2(const Model& m, ItemF2& it, float3 dq) {
+    const float2 vx = it.vx, vy = it.vy, vz = it.vz, z = it.z;
+    const float2 epv = __ffma2_rn(f2(m.ep[0]), vx,
+                                  __ffma2_rn(f2(m.ep[1]), vy, __fmul2_rn(f2(m.ep[2]), vz)));
+    const float2 vv = __ffma2_rn(vx, vx, __ffma2_rn(vy, vy, __fmul2_rn(vz, vz)));
+    const float2 c1 = __fmul2_rn(f2(m.dt_f), __ffma2_rn(f2(-m.hdt_f), vv, epv));
+    const float2 ex = __ffma2_rn(vx, f2(-m.dt_f), f2(m.ep[0]));
+    const float2 ey = __ffma2_rn(vy, f2(-m.dt_f), f2(m.ep[1]));
+    const float2 ez = __ffma2_rn(vz, f2(-m.dt_f), f2(m.ep[2]));
+    it.gam = __fadd2_rn(
+        __ffma2_rn(it.lx0, ex, __ffma2_rn(it.ly0, ey, __ffma2_rn(z, ez, c1))),
+        __ffma2_rn(f2(dq.x), vx, __ffma2_rn(f2(dq.y), vy, __fmul2_rn(f2(dq.z), vz))));
+    it.beta = __fadd2_rn(__ffma2_rn(vx, ex, __ffma2_rn(vy, ey, __fmul2_rn(vz, ez))), epv);
+}
+
 __device__ __forceinline__ ItemF item_split(const Model& m, float x, float y, float z, float vx,
                                             float vy, float vz, float nrcs, float cx, float cy,
                                             float area, float3 dq) {
@@ -534,31 +553,25 @@ __device__ __forceinline__ void accumulate_split_states_chunk(const Model& m, co
         const SampleF k = load_sample(tab[j]);
         const float3 dq = state_dq(m, k);
         ItemF2 it2[IT / 2];
-        {
-            ItemF it[IT];
 #pragma unroll
-            for (int h = 0; h < IT / 4; ++h) {
-                const float4 z4 = s_st[j & 1][0][h][threadIdx.x];
-                const float4 vx4 = s_st[j & 1][1][h][threadIdx.x];
-                const float4 vy4 = s_st[j & 1][2][h][threadIdx.x];
-                const float4 vz4 = s_st[j & 1][3][h][threadIdx.x];
-                const float zz[4] = {z4.x, z4.y, z4.z, z4.w}, ax[4] = {vx4.x, vx4.y, vx4.z, vx4.w};
-                const float ay[4] = {vy4.x, vy4.y, vy4.z, vy4.w}, az[4] = {vz4.x, vz4.y, vz4.z, vz4.w};
+        for (int h = 0; h < IT / 4; ++h) {
+            const float4 z4 = s_st[j & 1][0][h][threadIdx.x];
+            const float4 vx4 = s_st[j & 1][1][h][threadIdx.x];
+            const float4 vy4 = s_st[j & 1][2][h][threadIdx.x];
+            const float4 vz4 = s_st[j & 1][3][h][threadIdx.x];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = 4 * h + u;
-                    it[q].lx0 = lx0[q];
-                    it[q].ly0 = ly0[q];
-                    it[q].z = zz[u];
-                    it[q].vx = ax[u];
-                    it[q].vy = ay[u];
-                    it[q].vz = az[u];
-                    it[q].amp0 = amp0[q];
-                    item_motion(m, it[q], dq);
-                }
+            for (int u = 0; u < 2; ++u) {      // the pairs (4h, 4h + 1) and (4h + 2, 4h + 3)
+                const int q = 4 * h + 2 * u;
+                ItemF2& t = it2[q / 2];
+                t.lx0 = make_float2(lx0[q], lx0[q + 1]);
+                t.ly0 = make_float2(ly0[q], ly0[q + 1]);
+                t.z = u ? make_float2(z4.z, z4.w) : make_float2(z4.x, z4.y);
+                t.vx = u ? make_float2(vx4.z, vx4.w) : make_float2(vx4.x, vx4.y);
+                t.vy = u ? make_float2(vy4.z, vy4.w) : make_float2(vy4.x, vy4.y);
+                t.vz = u ? make_float2(vz4.z, vz4.w) : make_float2(vz4.x, vz4.y);
+                t.amp0 = make_float2(amp0[q], amp0[q + 1]);
+                item_motion2(m, t, dq);
             }
-#pragma unroll
-            for (int p = 0; p < IT / 2; ++p) it2[p] = pack_items(it[2 * p], it[2 * p + 1]);
         }
         int key[IT];
         float re[IT], im[IT];
