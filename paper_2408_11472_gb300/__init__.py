@@ -698,7 +698,7 @@ class EvolvingSurface:
 
 
 # updates per summation launch of the evolving surface (each needs its own field set)
-EVOLVING_BLOCK = 16
+EVOLVING_BLOCK = 22
 
 
 def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int, n_fast: int,
