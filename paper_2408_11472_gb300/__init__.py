@@ -667,10 +667,23 @@ class EvolvingSurface:
         _lib.check(_lib.lib.rsim_surface_prepare(ctypes.byref(self.spec), _ptr(self.workspace),
                                                  n, _stream(None)))
 
-    def at(self, t: float, stream=None, fields=None) -> Scatterers:
+    def new_workspace(self) -> torch.Tensor:
+        """Another prepared synthesis workspace (its own copy of the tables and of the packed
+        intermediate), so that two syntheses can run at once on different streams."""
+        n = self.workspace.numel()
+        ws = torch.empty(n, dtype=torch.uint8, device=self.workspace.device)
+        _lib.check(_lib.lib.rsim_surface_prepare(ctypes.byref(self.spec), _ptr(ws), n,
+                                                 _stream(None)))
+        return ws
+
+    def at(self, t: float, stream=None, fields=None, workspace=None) -> Scatterers:
         """The surface at t; ``fields``: optional (z, vx, vy, vz) float32 [L*L] tensors to
         write instead of the surface's own (e.g. a second set from ``new_fields()``, so
-        one update can be synthesised while the last one is still being read)."""
+        one update can be synthesised while the last one is still being read);
+        ``workspace``: optional one from ``new_workspace()`` instead of the surface's own."""
+        ws = self.workspace if workspace is None else workspace
+        if ws.numel() < self.workspace.numel() or ws.device != self.workspace.device:
+            raise ValueError("workspace must come from new_workspace()")
         z, vx, vy, vz = fields if fields is not None else (self.z, self.vx, self.vy, self.vz)
         for f in (z, vx, vy, vz):
             if f.dtype != torch.float32 or f.numel() != self.L * self.L or f.device != self.z.device \
@@ -678,7 +691,7 @@ class EvolvingSurface:
                 raise ValueError("fields must be contiguous float32 [L*L] tensors on the surface's device")
         _lib.check(_lib.lib.rsim_surface_at(
             ctypes.byref(self.spec), float(t), _ptr(z), _ptr(vx), _ptr(vy),
-            _ptr(vz), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
+            _ptr(vz), _ptr(ws), ws.numel(), _stream(stream)))
         return Scatterers(self.x, self.y, z, vx, vy, vz, self.nrcs,
                           origin=self.origin, area=self.area, t0=float(t))
 
@@ -698,12 +711,12 @@ class EvolvingSurface:
 
 
 # updates per summation launch of the evolving surface (each needs its own field set)
-EVOLVING_BLOCK = 22
+EVOLVING_BLOCK = 33
 
 
 def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int, n_fast: int,
                       n_doppler: int, precision: str, T: torch.Tensor, ws: torch.Tensor,
-                      stream=None, groups=None, side=None):
+                      stream=None, groups=None, side=None, side2=None, ws2=None):
     """Spectra T[s] (+=) of updates u0 + s, the surface regenerated at each update, in blocks of
     K updates: the K surfaces are synthesised into K field sets, then one summation launch
     (rsim_doppler_accumulate_states) adds the block's spectra to their slots of the exact
@@ -711,7 +724,10 @@ def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int
 
     ``groups``: one or two lists of K field sets (default: one of min(S, EVOLVING_BLOCK)).
     With two and a ``side`` stream the syntheses of block b + 1 run on the side stream into
-    the other group while block b is summed (same kernels and inputs: the same bits)."""
+    the other group while block b is summed (same kernels and inputs: the same bits).  With a
+    second side stream ``side2`` and a second synthesis workspace ``ws2``
+    (``surface.new_workspace()``) the block's syntheses alternate between the two, so that
+    one synthesis's passes fill the SMs the other's last wave leaves idle."""
     G = radar.n_gates
     nbytes = ws.numel() * ws.element_size()
     cur = stream if stream is not None else torch.cuda.current_stream()
@@ -724,26 +740,34 @@ def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int
     overlap = len(groups) > 1 and side is not None
     grid = surface.grid()
     read = [None] * len(groups)     # event after the summation that last read a group
+    sides = [side] + ([side2] if (overlap and side2 is not None and ws2 is not None) else [])
+    wss = [None, ws2][:len(sides)]
     if overlap:
         fork = torch.cuda.Event()
         fork.record(cur)
-        side.wait_event(fork)
+        for sd in sides:
+            sd.wait_event(fork)
     for b, s0 in enumerate(range(0, S, K)):
         s1 = min(S, s0 + K)
         gi = b % len(groups)
         sets = groups[gi]
-        syn = side if overlap else cur
         if overlap and read[gi] is not None:
-            side.wait_event(read[gi])   # the summation two blocks back has read this group
+            for sd in sides:
+                sd.wait_event(read[gi])  # the summation two blocks back has read this group
         states = []
         for i, s in enumerate(range(s0, s1)):
             t = (u0 + s) * n_fast / radar.prf_hz
-            surface.at(t, stream=syn, fields=sets[i])
+            if overlap:
+                surface.at(t, stream=sides[i % len(sides)], fields=sets[i],
+                           workspace=wss[i % len(sides)])
+            else:
+                surface.at(t, stream=cur, fields=sets[i])
             states.append(sets[i] + (t,))
         if overlap:
-            made = torch.cuda.Event()
-            made.record(side)
-            cur.wait_event(made)
+            for sd in sides:
+                made = torch.cuda.Event()
+                made.record(sd)
+                cur.wait_event(made)
         doppler_accumulate_states(radar, platform, grid, u0 + s0, states, n_fast, n_doppler,
                                   precision, workspace=ws[s0 * slot:], stream=cur)
         if overlap:
@@ -800,13 +824,16 @@ class EvolvingFastMode:
         K = max(1, min(self.S, block))
         self.groups = [surface.field_sets(K), surface.field_sets(K)]
         self.side = torch.cuda.Stream(device=dev)
+        # a second synthesis stream and workspace: consecutive syntheses run two at a time
+        self.side2 = torch.cuda.Stream(device=dev)
+        self.ws2 = surface.new_workspace()
         self.graph = None
 
     def _run(self):
         self.spectra.zero_()
         _evolving_spectra(self.radar, self.platform, self.surface, self.u0, self.S, self.n_fast,
                           self.n_doppler, self.precision, self.spectra, self.workspace,
-                          groups=self.groups, side=self.side)
+                          groups=self.groups, side=self.side, side2=self.side2, ws2=self.ws2)
         synth_pulses(self.radar, self.spectra, self.u0, self.n_fast, self.pulse0, self.n_pulses,
                      self.window, out=self.iq)
 
