@@ -799,10 +799,11 @@ class EvolvingFastMode:
     """simulate_fast_evolving with every buffer allocated once, so the whole update loop
     (per block of updates the surface syntheses and one summation launch, then the
     post-processing) can be captured into a CUDA graph (``capture()``) and replayed
-    (``replay()``).  The syntheses run on a side stream into two alternating groups of field
-    sets, overlapped with the summations; the results are those of simulate_fast_evolving
-    bit for bit.  ``spectra`` and ``iq`` hold the results; ``run()`` enqueues the same work
-    eagerly."""
+    (``replay()``).  The syntheses run on two side streams (alternately, each with its own
+    synthesis workspace) into two alternating groups of field sets, overlapped with the
+    summations; the results are those of simulate_fast_evolving bit for bit.  ``block``:
+    updates per summation launch (each needs its own field set in both groups).  ``spectra``
+    and ``iq`` hold the results; ``run()`` enqueues the same work eagerly."""
 
     def __init__(self, radar, platform, surface: EvolvingSurface, n_pulses: int, n_fast: int,
                  n_doppler: int, window: str = "sqrt_raised_cosine", precision: str = "split",
@@ -819,7 +820,7 @@ class EvolvingFastMode:
         self.iq = torch.empty((n_pulses, G), dtype=cdt, device=dev)
         self.workspace = torch.empty(max(16, workspace_size(self.S, G, n_doppler)),
                                      dtype=torch.uint8, device=dev)
-        # two groups of field sets and a side stream: block b + 1 is synthesised while block b
+        # two groups of field sets and side streams: block b + 1 is synthesised while block b
         # is summed
         K = max(1, min(self.S, block))
         self.groups = [surface.field_sets(K), surface.field_sets(K)]
