@@ -656,7 +656,8 @@ def run_delay_doppler(torch, rsim, args):
                         "achieved_gbs": round(bytes_moved / (t / 1e3) / 1e9, 1),
                         "peak_gbs": peak, "peak_basis": basis,
                         "frac": round(bytes_moved / (t / 1e3) / 1e9 / peak, 4),
-                        "note": "one CTA per burst (%d CTAs): the launch is latency-bound" % nb}
+                        "note": "one cluster of 4 CTAs per burst (%d CTAs, the burst exchanged "
+                                "through distributed shared memory): latency-bound" % (4 * nb)}
     line["normalised_mean_waveform"] = {
         "fast": [round(float(v), 5) for v in nf], "regular": [round(float(v), 5) for v in nr],
         "rel_l2_fast_vs_regular": float(torch.linalg.vector_norm(nf - nr) / torch.linalg.vector_norm(nr)),

@@ -365,7 +365,7 @@ rsim_status rsim_scatterer_cells(const rsim_radar *radar, const rsim_platform *p
  * focused   : [bursts][burst][n_gates] complex64 (beam-major), OVERWRITTEN, or NULL;
  * multilook : [bursts][n_gates] float, OVERWRITTEN.
  * burst and n_gates must be powers of two >= 2 with burst <= 1024 and
- * burst * n_gates <= 12288 (one burst in shared memory), else RSIM_ERR_UNSUPPORTED.
+ * burst * n_gates <= 12288 (one burst held on chip), else RSIM_ERR_UNSUPPORTED.
  * Complex64 only (RSIM_SPLIT output). */
 rsim_status rsim_delay_doppler(const rsim_radar *radar, const rsim_platform *platform,
                                const void *iq, int64_t pulse0, int32_t n_pulses, int32_t burst,

@@ -19,8 +19,12 @@ def rsim():
     return m
 
 
+# a cluster of four CTAs per burst splits its gates and beams in four; bursts or gate counts
+# below four take one CTA per burst ((2, 2) and (8, 2))
 @pytest.mark.parametrize("burst,n_gates,n_pulses,pulse0", [(64, 128, 1000, 0), (16, 32, 256, 333),
-                                                           (128, 64, 384, 7), (2, 2, 9, 0)])
+                                                           (128, 64, 384, 7), (2, 2, 9, 0),
+                                                           (4, 4, 41, 1), (8, 2, 24, 3),
+                                                           (1024, 8, 2048, 0)])
 def test_random_iq_matches_oracle(rsim, burst, n_gates, n_pulses, pulse0):
     rd = sg.RadarParams(n_gates=n_gates)
     pf = dataclasses.replace(sg.nadir_track(n_pulses), v=(7000.0, 450.0, 2.5), r_ref_rate=1.7)
