@@ -578,6 +578,10 @@ rsim_status rsim_delay_doppler(const rsim_radar* radar, const rsim_platform* pla
     a.gate_width = radar->gate_width_m;
     a.r_ref0 = platform->r_ref0;
     a.r_ref_rate = platform->r_ref_rate;
+    {
+        const double q = a.vh > 0.0 ? a.lambda * a.prf / (2.0 * a.vh) : 0.0;
+        a.mig_c = q * q / (2.0 * a.gate_width * (double)a.n_gates);
+    }
     const cudaError_t e = rsim::launch_dd_focus(a, n_bursts, iq, focused, multilook, stream);
     if (e != cudaSuccess) return cuda_fail(e, "delay-Doppler kernel launch");
     return RSIM_OK;

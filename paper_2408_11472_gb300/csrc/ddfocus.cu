@@ -1,7 +1,7 @@
 // ddfocus.cu -- delay-Doppler focusing of the simulated IQ (Section IV.C), for sm_103a.
 //
-// One thread-block cluster of `cl` CTAs per burst of `burst` consecutive pulses (cl = 4 when
-// the burst and the gate count allow it, else 1); the burst (burst x n_gates complex) is
+// One thread-block cluster of `cl` CTAs per burst of `burst` consecutive pulses (cl = 8, or
+// fewer when the burst or the gate count is below 8); the burst (burst x n_gates complex) is
 // spread over the cluster's shared memory and exchanged through distributed shared memory:
 //   1. each CTA loads its n_gates / cl gates of every pulse, applies the Doppler centroid
 //      correction y_k *= exp(-j 2 pi nu_c k) and the factor (-1)^k that centres the beams
@@ -63,17 +63,22 @@ __global__ void __launch_bounds__(kDdThreads) dd_focus_kernel(DdArgs a, int lcl,
     // per beam: the migration in range-transform cycles s_f / G as hi + lo floats
     const double r0 = fma(a.r_ref_rate, (double)(a.pulse0 + b * Nb + Nb / 2) * a.inv_prf, a.r_ref0);
     for (int k = threadIdx.x; k < Nb; k += blockDim.x) {
+        // nu_c k reduced to [-1/2, 1/2] cycles in FP64, its sine and cosine in FP32 (a few
+        // 1e-8 of error; the FP64 pipe runs 1/64 of the FP32 rate)
         double ph = a.nu_c * (double)k;                    // cycles
         ph -= rint(ph);
-        double sn, cs;
-        sincospi(-2.0 * ph, &sn, &cs);
+        float sn, cs;
+        sincospif(-2.0f * (float)ph, &sn, &cs);
         const float sg = (k & 1) ? -1.0f : 1.0f;
-        cent[k] = make_float2(sg * (float)cs, sg * (float)sn);
-        const double nu = (double)(k - Nb / 2) / (double)Nb;
-        const double x = a.vh > 0.0 ? nu * a.lambda * r0 * a.prf / (2.0 * a.vh) : 0.0;
-        const double sfg = x * x / (2.0 * r0 * a.gate_width) / (double)G;
-        const float hi = (float)sfg;
-        shift[k] = make_float2(hi, (float)(sfg - (double)hi));
+        cent[k] = make_float2(sg * cs, sg * sn);
+        if ((k >> lnl) == r) {       // the migration of this CTA's beams only
+            // s_f / G = x_f^2 / (2 R_0 gate_width G) = nu_f^2 R_0 (lambda PRF / (2 V))^2
+            // / (2 gate_width G): the constant factor comes from the host (no FP64 divide)
+            const double nu = (double)(k - Nb / 2) * (1.0 / (double)Nb);
+            const double sfg = nu * nu * r0 * a.mig_c;
+            const float hi = (float)sfg;
+            shift[k] = make_float2(hi, (float)(sfg - (double)hi));
+        }
     }
     __syncthreads();
     // 1. this CTA's gates of every pulse (pulse-major rows), gate-major ([gl][k]) for the
@@ -138,8 +143,13 @@ __global__ void __launch_bounds__(kDdThreads) dd_focus_kernel(DdArgs a, int lcl,
 
 }  // namespace
 
-// Cluster size (log2) for a burst: 4 CTAs when both the gates and the beams split in four
-int dd_cluster_log2(int burst, int n_gates) { return (burst >= 4 && n_gates >= 4) ? 2 : 0; }
+// Cluster size (log2) for a burst: up to 8 CTAs (the portable cluster size), as many as both
+// the gates and the beams split into
+int dd_cluster_log2(int burst, int n_gates) {
+    int l = 0;
+    while (l < 3 && (burst >> (l + 1)) >= 1 && (n_gates >> (l + 1)) >= 1) ++l;
+    return l;
+}
 
 size_t dd_focus_smem_bytes(int burst, int n_gates) {
     const int cl = 1 << dd_cluster_log2(burst, n_gates);

@@ -66,6 +66,7 @@ struct DdArgs {
     int64_t pulse0;
     double nu_c;                 // Doppler centroid, cycles per pulse
     double lambda, prf, inv_prf, vh, gate_width, r_ref0, r_ref_rate;
+    double mig_c;                // (lambda PRF / (2 vh))^2 / (2 gate_width n_gates), 0 if vh = 0
 };
 size_t dd_focus_smem_bytes(int burst, int n_gates);
 cudaError_t launch_dd_focus(const DdArgs& a, int64_t n_bursts, const void* iq, void* focused,

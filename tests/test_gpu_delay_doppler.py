@@ -19,8 +19,8 @@ def rsim():
     return m
 
 
-# a cluster of four CTAs per burst splits its gates and beams in four; bursts or gate counts
-# below four take one CTA per burst ((2, 2) and (8, 2))
+# a cluster of up to eight CTAs per burst splits its gates and beams; small bursts or gate
+# counts take smaller clusters (down to one gate or one beam per CTA: (2, 2), (8, 2), (4, 4))
 @pytest.mark.parametrize("burst,n_gates,n_pulses,pulse0", [(64, 128, 1000, 0), (16, 32, 256, 333),
                                                            (128, 64, 384, 7), (2, 2, 9, 0),
                                                            (4, 4, 41, 1), (8, 2, 24, 3),
