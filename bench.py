@@ -541,14 +541,26 @@ def run_extras(rsim, torch, rd, pf, fp, P, S, dev, scene, ws, T, Y, args, dev_na
     # -- the FP64 oracle on the host cores, bounded sample of the same workload.
     try:
         import oracle
-        v, cores, desc, secs = oracle_fast_sample(rd, pf, scene, P, fp)
-        v1, c1, desc1, secs1 = oracle_fast_sample(rd, pf, scene, P, fp, target_s=8.0, threads=1)
+        def best_of_3(**kw):
+            """Best rate of three runs of the bounded sample (one run when it takes over
+            20 s, so that the three stay under a minute)."""
+            r = oracle_fast_sample(rd, pf, scene, P, fp, **kw)
+            runs = [r]
+            if r[3] < 20.0:
+                runs += [oracle_fast_sample(rd, pf, scene, P, fp, **kw) for _ in range(2)]
+            best = max(runs, key=lambda x: x[0])
+            return best + (len(runs),)
+
+        v, cores, desc, secs, n_runs = best_of_3()
+        v1, c1, desc1, secs1, n1 = best_of_3(target_s=8.0, threads=1)
         oracle.Oracle(cores)                 # restore the thread count for later users
         out["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": cores,
                                "kind": "oracle", "sample": desc, "seconds": round(secs, 2),
+                               "runs": "best of %d" % n_runs,
                                "compiler": " ".join([oracle.CC] + oracle.CFLAGS),
                                "one_core": {"value": round(v1, 3), "unit": UNIT, "cores": c1,
-                                            "sample": desc1, "seconds": round(secs1, 2)}}
+                                            "sample": desc1, "seconds": round(secs1, 2),
+                                            "runs": "best of %d" % n1}}
     except Exception as e:  # the oracle needs gcc on the host
         out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                "sample": "failed: %s" % e}

@@ -96,12 +96,19 @@ def _np(t):
 
 
 def _cpu_leg(fn):
-    """Run one oracle computation on the host cores: (result, seconds, threads)."""
+    """Run an oracle computation on the host cores: (result, seconds, threads).  The time is
+    the best of three runs when one takes under 20 s (the three stay under a minute)."""
     import oracle
     orc = oracle.Oracle()
     t = time.perf_counter()
     res = fn(orc)
-    return res, time.perf_counter() - t, orc.threads
+    secs = time.perf_counter() - t
+    if secs < 20.0:
+        for _ in range(2):
+            t = time.perf_counter()
+            fn(orc)
+            secs = min(secs, time.perf_counter() - t)
+    return res, secs, orc.threads
 
 
 def _base_line(cfg_name, metric, unit, value, higher=True, dtype="f32"):
