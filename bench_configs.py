@@ -708,6 +708,29 @@ def run_surface_update(torch, rsim, args):
     surf = rsim.EvolvingSurface(spec)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     t_surf = _timed(torch, lambda: surf.at(0.1234), 20, flush)
+    # the syntheses as the update loop runs them: consecutive ones alternating between two
+    # streams with their own workspaces and field sets, 64 per timed run
+    n_loop = 64
+    side = [torch.cuda.Stream(), torch.cuda.Stream()]
+    wss = [None, surf.new_workspace()]
+    loop_sets = surf.field_sets(2)
+
+    def syntheses():
+        cur = torch.cuda.current_stream()
+        fork = torch.cuda.Event()
+        fork.record(cur)
+        for sd in side:
+            sd.wait_event(fork)
+        for i in range(n_loop):
+            surf.at(0.1234 + 0.0035 * i, stream=side[i % 2], fields=loop_sets[i % 2],
+                    workspace=wss[i % 2])
+        for sd in side:
+            done = torch.cuda.Event()
+            done.record(sd)
+            cur.wait_event(done)
+
+    t_surf_loop = _timed(torch, syntheses, 5, flush) / n_loop
+    del loop_sets
     S = (P - 1) // fp.n_fast + 2
     ws = torch.empty(rsim.workspace_size(S, rd.n_gates, fp.n_doppler), dtype=torch.uint8,
                      device="cuda")
@@ -757,7 +780,14 @@ def run_surface_update(torch, rsim, args):
     line["surface_synthesis_roofline"] = {"bound": "hbm", "bytes": nbytes,
                                           "achieved_gbs": round(nbytes / (t_surf / 1e3) / 1e9, 1),
                                           "peak_gbs": peak, "peak_basis": basis,
-                                          "frac": round(nbytes / (t_surf / 1e3) / 1e9 / peak, 4)}
+                                          "frac": round(nbytes / (t_surf / 1e3) / 1e9 / peak, 4),
+                                          "basis": "one synthesis after an L2 flush"}
+    line["surface_synthesis_in_loop"] = {
+        "ms_per_synthesis": round(t_surf_loop, 4),
+        "achieved_gbs": round(nbytes / (t_surf_loop / 1e3) / 1e9, 1),
+        "frac": round(nbytes / (t_surf_loop / 1e3) / 1e9 / peak, 4),
+        "basis": "64 consecutive syntheses alternating between two streams (workspaces and "
+                 "field sets), as the update loop runs them"}
     line["states_summation"] = {"updates_per_launch": K, "ms_per_launch": round(t_states, 4),
                                 "ms_per_update": round(t_states / K, 4),
                                 "hbm_bytes_per_update": 16 * L * L,

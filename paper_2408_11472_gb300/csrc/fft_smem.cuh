@@ -294,29 +294,13 @@ __device__ __forceinline__ void stockham_pass_reg(float2* a, int rows, int N, in
     __syncthreads();
 }
 
-// The whole transform of `rows` padded rows of N = 2^log2N points (N >= 2), row r at element
-// r * NP (NP >= padded_len(N)).  MAXE bounds the elements per thread: rows * N <= MAXE *
-// blockDim.x (MAXE a multiple of 16).  twf: the full twiddle table (twiddle_full).  Result in
-// place, natural order.
-template <int MAXE>
-__device__ void fft_rows_reg(float2* a, int rows, int N, int log2N, const float2* __restrict__ twf,
-                             float sign, int NP, int log2s0 = 0) {
-    static_assert(MAXE % 16 == 0, "elements per thread");
-    int log2s = log2s0;   // > 0: the first passes were done by the caller
-    while (log2N - log2s >= 4) {
-        stockham_pass_reg<16, MAXE / 16>(a, rows, N, log2N, log2s, twf, sign, NP);
-        log2s += 4;
-    }
-    switch (log2N - log2s) {
-        case 3: stockham_pass_reg<8, MAXE / 8>(a, rows, N, log2N, log2s, twf, sign, NP); break;
-        case 2: stockham_pass_reg<4, MAXE / 4>(a, rows, N, log2N, log2s, twf, sign, NP); break;
-        case 1: stockham_pass_reg<2, MAXE / 2>(a, rows, N, log2N, log2s, twf, sign, NP); break;
-        default: break;
-    }
-}
-
-// All passes of fft_rows_reg but the last (from log2s0); returns the log2 stride of the last
-// pass, whose radix is 2^(log2N - returned value), one of 2, 4, 8, 16 (N >= 2).
+// The register-radix transform of `rows` padded rows of N = 2^log2N points (N >= 2), row r at
+// element r * NP (NP >= padded_len(N)): radix-16 passes, then one last pass of radix 2, 4, 8
+// or 16.  This runs every pass but the last (from log2s0: the caller may have done the
+// first ones) and returns the log2 stride of the last pass, whose radix is
+// 2^(log2N - returned value); fft_last_pass_store runs it.  MAXE bounds the elements per
+// thread: rows * N <= MAXE * blockDim.x (MAXE a multiple of 16).  twf: the full twiddle
+// table (twiddle_full).
 template <int MAXE>
 __device__ int fft_rows_reg_but_last(float2* a, int rows, int N, int log2N,
                                      const float2* __restrict__ twf, float sign, int NP,
@@ -367,7 +351,7 @@ __device__ __forceinline__ void last_pass_store(const float2* a, int rows, int l
 }
 
 // The last pass of fft_rows_reg_but_last's rows with its outputs sent to store (see
-// last_pass_store); MAXE as fft_rows_reg.
+// last_pass_store); MAXE as for fft_rows_reg_but_last.
 template <int MAXE, bool ROW_FAST, typename Store>
 __device__ __forceinline__ void fft_last_pass_store(const float2* a, int rows, int lr, int log2N,
                                                     int log2s, int NP, float sign, Store store) {
