@@ -163,8 +163,7 @@ int rsim_version(void);
  * adjoint gather cell against n_gates x n_doppler.  A failed check skips the addition or
  * read it guards and records itself; the entry point then returns RSIM_ERR_CHECK, with the
  * check and the offending value in rsim_last_error().  Those entry points synchronise their
- * stream to read the record, so the debug build is for testing: not for timing, and its
- * calls cannot be recorded into a CUDA graph. */
+ * stream to read the record, so the debug build is for testing, not for timing. */
 int rsim_check_build(void);
 
 /* Number of consecutive scatterers that share one FP64 reference point in RSIM_SPLIT
