@@ -79,18 +79,21 @@ def test_fast_mode_with_evolving_surface_matches_oracle(rsim, orc, precision):
     assert rel_l2(np_(T)[-1], np_(T_lin)[-1]) > 1e-2
 
 
-@pytest.mark.parametrize("precision", ["split", "fp64"])
-def test_evolving_loop_graph_replay_is_bit_identical(rsim, precision):
+@pytest.mark.parametrize("precision,block", [("split", 33), ("fp64", 33), ("split", 2),
+                                             ("split", 3), ("fp64", 2)])
+def test_evolving_loop_graph_replay_is_bit_identical(rsim, precision, block):
     """The update loop with buffers allocated once (EvolvingFastMode): eager run and CUDA
     graph replays give the spectra and pulses of simulate_fast_evolving bit for bit, on a
-    ragged pulse range."""
+    ragged pulse range (7 spectra: one block, or several blocks synthesised on two streams
+    into two alternating groups of field sets while the previous block is summed)."""
     rd = sg.RadarParams()
     P, p0, nf, nd = 333, 40, 64, 64
     pf = sg.nadir_track(P + p0)
     surf = rsim.EvolvingSurface(sg.sea_spectrum(128, 22))
     T, Y = rsim.simulate_fast_evolving(rd, pf, surf, P, nf, nd, "sqrt_raised_cosine", precision,
                                        p0)
-    em = rsim.EvolvingFastMode(rd, pf, surf, P, nf, nd, "sqrt_raised_cosine", precision, p0)
+    em = rsim.EvolvingFastMode(rd, pf, surf, P, nf, nd, "sqrt_raised_cosine", precision, p0,
+                               block=block)
     Te, Ye = em.run()
     assert torch.equal(Te, T) and torch.equal(Ye, Y)
     em.capture()
