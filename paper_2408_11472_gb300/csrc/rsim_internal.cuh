@@ -172,7 +172,8 @@ __device__ __forceinline__ float2 pattern_near_f(const Model& m, float u, float 
     const float fu = __fmul_rn(u - m.ant_u0_f, m.ant_idu_f);  // not contracted into tu below
     const float fv = __fmul_rn(v - m.ant_v0_f, m.ant_idv_f);
     const float iu = floorf(fu), iv = floorf(fv);
-    if (iu != c.iu || iv != c.iv) return pattern_f(m, u, v);
+    // (a first point outside the table has no corners to reuse: c.iu = -1)
+    if (c.iu < 0.0f || iu != c.iu || iv != c.iv) return pattern_f(m, u, v);
     const float tu = fu - iu, tv = fv - iv;
     const float ax = fmaf(tu, c.g10.x - c.g00.x, c.g00.x), ay = fmaf(tu, c.g10.y - c.g00.y, c.g00.y);
     const float bx = fmaf(tu, c.g11.x - c.g01.x, c.g01.x), by = fmaf(tu, c.g11.y - c.g01.y, c.g01.y);
@@ -617,7 +618,8 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
     float pu = 0.f, pv = 0.f, pat_bins = 0.f;
     if (ANT) {
         // C = a G(u, v) e^{-j 2 pi f}, (u, v) = -(d_x, d_y) / R, 1 / R = (1 / R_c)(1 - dR / R_c)
-        const float invR = k.invRc * (1.0f - xr);
+        // (the bracket one FMA, as the paired evaluation forms it)
+        const float invR = k.invRc * fmaf(dR, -k.invRc, 1.0f);
         pu = __fmul_rn(-dx, invR);  // rounded before the table look-up subtracts u0
         pv = __fmul_rn(-dy, invR);
         if (DERIV) G = pattern_f(m, pu, pv, &gu, &gv);
@@ -659,7 +661,7 @@ __device__ __forceinline__ int eval_split(const Model& m, const SampleF& k, cons
         // dR/dz = -d_z / R, dtheta/dz = rho / R^2,
         // d ln a / dz = 2 d_z / R^2 - 4 ln2 theta rho / (theta_b^2 R^2), d phi / dz = 4 pi d_z / (lambda R)
         const float dz = k.Dz - lz;
-        const float invR = k.invRc * (1.0f - xr);
+        const float invR = k.invRc * fmaf(dR, -k.invRc, 1.0f);
         const float invR2 = invR * invR;
         dv->dphi = kTwoPiF * (m.chi_hi + m.chi_lo) * dz * invR;  // chi = 2 / lambda
         if (ANT) {
@@ -723,13 +725,96 @@ __device__ __forceinline__ ItemF2 pack_items(const ItemF& a, const ItemF& b) {
 
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 
+// Bilinear interpolation of the corners of cells c0 and c1 at (tu, tv) for two points as
+// the lanes of pairs (real parts in gx, imaginary parts in gy): each lane's operations are
+// those of pattern_cell_f's interpolation (b - a as fma(a, -1, b), exact).
+__device__ __forceinline__ void pattern_interp_f2(const PatCellF& c0, const PatCellF& c1,
+                                                  float2 tu, float2 tv, float2& gx,
+                                                  float2& gy) {
+    const float2 neg1 = f2(-1.0f);
+    const float2 g00x = make_float2(c0.g00.x, c1.g00.x), g00y = make_float2(c0.g00.y, c1.g00.y);
+    const float2 g10x = make_float2(c0.g10.x, c1.g10.x), g10y = make_float2(c0.g10.y, c1.g10.y);
+    const float2 g01x = make_float2(c0.g01.x, c1.g01.x), g01y = make_float2(c0.g01.y, c1.g01.y);
+    const float2 g11x = make_float2(c0.g11.x, c1.g11.x), g11y = make_float2(c0.g11.y, c1.g11.y);
+    const float2 ax = __ffma2_rn(tu, __ffma2_rn(g00x, neg1, g10x), g00x);
+    const float2 ay = __ffma2_rn(tu, __ffma2_rn(g00y, neg1, g10y), g00y);
+    const float2 bx = __ffma2_rn(tu, __ffma2_rn(g01x, neg1, g11x), g01x);
+    const float2 by = __ffma2_rn(tu, __ffma2_rn(g01y, neg1, g11y), g01y);
+    gx = __ffma2_rn(tv, __ffma2_rn(ax, neg1, bx), ax);
+    gy = __ffma2_rn(tv, __ffma2_rn(ay, neg1, by), ay);
+}
+
+// pattern_cell_f for two points as the lanes of pairs, without a branch: a point outside
+// the table loads the table's first cell and gives 0 (and c.iu = -1), as pattern_cell_f.
+// Per lane the same values as two pattern_cell_f calls.  The grid coordinates
+// (u - u0) / du are formed lane by lane in scalar FP32: u is a paired product, and a paired
+// product that feeds a paired addition can come out of code generation as one paired FMA
+// (one rounding where the scalar form rounds twice), even from the _rn intrinsics.
+__device__ __forceinline__ void pattern_cell_f2(const Model& m, float2 u, float2 v, float2& gx,
+                                                float2& gy, PatCellF& c0, PatCellF& c1) {
+    const float2 fu = make_float2(__fmul_rn(u.x - m.ant_u0_f, m.ant_idu_f),
+                                  __fmul_rn(u.y - m.ant_u0_f, m.ant_idu_f));
+    const float2 fv = make_float2(__fmul_rn(v.x - m.ant_v0_f, m.ant_idv_f),
+                                  __fmul_rn(v.y - m.ant_v0_f, m.ant_idv_f));
+    const float2 iu = make_float2(floorf(fu.x), floorf(fu.y));
+    const float2 iv = make_float2(floorf(fv.x), floorf(fv.y));
+    const float umax = (float)(m.ant_nu - 2), vmax = (float)(m.ant_nv - 2);
+    const bool in0 = iu.x >= 0.0f && iu.x <= umax && iv.x >= 0.0f && iv.x <= vmax;
+    const bool in1 = iu.y >= 0.0f && iu.y <= umax && iv.y >= 0.0f && iv.y <= vmax;
+    const int o0 = in0 ? (int)iv.x * m.ant_nu + (int)iu.x : 0;
+    const int o1 = in1 ? (int)iv.y * m.ant_nu + (int)iu.y : 0;
+    c0.g00 = __ldg(m.ant + o0);
+    c0.g10 = __ldg(m.ant + o0 + 1);
+    c0.g01 = __ldg(m.ant + o0 + m.ant_nu);
+    c0.g11 = __ldg(m.ant + o0 + m.ant_nu + 1);
+    c1.g00 = __ldg(m.ant + o1);
+    c1.g10 = __ldg(m.ant + o1 + 1);
+    c1.g01 = __ldg(m.ant + o1 + m.ant_nu);
+    c1.g11 = __ldg(m.ant + o1 + m.ant_nu + 1);
+    c0.iu = in0 ? iu.x : -1.0f;
+    c0.iv = iv.x;
+    c1.iu = in1 ? iu.y : -1.0f;
+    c1.iv = iv.y;
+    const float2 neg1 = f2(-1.0f);
+    pattern_interp_f2(c0, c1, __ffma2_rn(iu, neg1, fu), __ffma2_rn(iv, neg1, fv), gx, gy);
+    if (!in0) { gx.x = 0.0f; gy.x = 0.0f; }
+    if (!in1) { gx.y = 0.0f; gy.y = 0.0f; }
+}
+
+// pattern_near_f for two points as the lanes of pairs: both in their first point's cell
+// (the usual case over one pulse), the corners are reused as pairs; otherwise each lane
+// takes pattern_near_f.  Per lane the same values as two pattern_near_f calls (the grid
+// coordinates lane by lane, as pattern_cell_f2).
+__device__ __forceinline__ void pattern_near_f2(const Model& m, float2 u, float2 v,
+                                                const PatCellF& c0, const PatCellF& c1,
+                                                float2& gx, float2& gy) {
+    const float2 fu = make_float2(__fmul_rn(u.x - m.ant_u0_f, m.ant_idu_f),
+                                  __fmul_rn(u.y - m.ant_u0_f, m.ant_idu_f));
+    const float2 fv = make_float2(__fmul_rn(v.x - m.ant_v0_f, m.ant_idv_f),
+                                  __fmul_rn(v.y - m.ant_v0_f, m.ant_idv_f));
+    const float2 iu = make_float2(floorf(fu.x), floorf(fu.y));
+    const float2 iv = make_float2(floorf(fv.x), floorf(fv.y));
+    const bool same = c0.iu >= 0.0f && iu.x == c0.iu && iv.x == c0.iv &&
+                      c1.iu >= 0.0f && iu.y == c1.iu && iv.y == c1.iv;
+    if (same) {
+        const float2 neg1 = f2(-1.0f);
+        pattern_interp_f2(c0, c1, __ffma2_rn(iu, neg1, fu), __ffma2_rn(iv, neg1, fv), gx, gy);
+    } else {
+        const float2 h0 = pattern_near_f(m, u.x, v.x, c0), h1 = pattern_near_f(m, u.y, v.y, c1);
+        gx = make_float2(h0.x, h1.x);
+        gy = make_float2(h0.y, h1.y);
+    }
+}
+
 // eval_split<DOPPLER, GENERAL = false, DERIV = false, ANT> for two scatterers at once on
 // the paired FP32 instructions (fma / add / mul .f32x2: one issue slot for both); the
 // tabulated pattern's look-ups run per lane.
 // Every pair operation rounds each lane as the scalar operation it replaces, and the
 // negations the pair forms cannot take as operand modifiers are exact rewrites
 // (fma(x, -1, y) = y - x, products with negated constants), so each lane's key, re and im
-// are bit-identical to the scalar evaluation's.
+// are bit-identical to the scalar evaluation's.  No paired product is an operand of a
+// paired addition (code generation may fuse the two into one FFMA2): such a sum is written
+// as an FMA on both sides, or taken per lane in scalar FP32.
 // Keys: g n_doppler + bin inside the range window; every item outside it gets the one key
 // n_gates n_doppler (an unsigned minimum: negative gates wrap to large unsigned values), which
 // the emission drops; items the exact evaluation must take get kKeyDeferred, and `defer`
@@ -782,27 +867,30 @@ __device__ __forceinline__ void eval_split_pair(const Model& m, const SampleF& k
         re = __fmul2_rn(a, cs);
         im = __fmul2_rn(a, sn);
     } else {
-        // (u, v) = -(d_x, d_y) / R with 1 / R = (1 / R_c)(1 - x_r), as eval_split
-        const float2 invR = __fmul2_rn(f2(k.invRc), __fadd2_rn(one, nxr));
+        // (u, v) = -(d_x, d_y) / R with 1 / R = (1 / R_c)(1 - dR / R_c), the bracket one FMA,
+        // as eval_split
+        const float2 invR = __fmul2_rn(f2(k.invRc), __ffma2_rn(dR, f2(-k.invRc), one));
         const float2 pu = __fmul2_rn(ndx, invR), pv = __fmul2_rn(ndy, invR);
+        // the two look-ups as pairs (per lane the operations of pattern_cell_f /
+        // pattern_near_f); products negated exactly as -(x y) = x (-y)
         PatCellF c0, c1;
-        const float2 G0 = pattern_cell_f(m, pu.x, pv.x, c0);
-        const float2 G1 = pattern_cell_f(m, pu.y, pv.y, c1);
+        float2 gx, gy;
+        pattern_cell_f2(m, pu, pv, gx, gy, c0, c1);
         if (DOPPLER) {
             // -(d + e) at the second pulse, e = e_p - v dt carried as -e (exact)
             const float2 nex = __ffma2_rn(it.vx, f2(m.dt_f), f2(-m.ep[0]));
             const float2 ney = __ffma2_rn(it.vy, f2(m.dt_f), f2(-m.ep[1]));
             const float2 u2 = __fmul2_rn(__fadd2_rn(ndx, nex), invR);
             const float2 v2 = __fmul2_rn(__fadd2_rn(ndy, ney), invR);
-            const float2 H0 = pattern_near_f(m, u2.x, v2.x, c0);
-            const float2 H1 = pattern_near_f(m, u2.y, v2.y, c1);
-            pat_bins.x = __fmul_rn(small_arg_f(fmaf(H0.y, G0.x, -H0.x * G0.y),
-                                               fmaf(H0.x, G0.x, H0.y * G0.y)), m.nd_over_2pi_f);
-            pat_bins.y = __fmul_rn(small_arg_f(fmaf(H1.y, G1.x, -H1.x * G1.y),
-                                               fmaf(H1.x, G1.x, H1.y * G1.y)), m.nd_over_2pi_f);
+            float2 hx, hy;
+            pattern_near_f2(m, u2, v2, c0, c1, hx, hy);
+            const float2 pi = __ffma2_rn(hy, gx, __fmul2_rn(hx, __fmul2_rn(gy, neg1)));
+            const float2 pr = __ffma2_rn(hx, gx, __fmul2_rn(hy, gy));
+            pat_bins = make_float2(__fmul_rn(small_arg_f(pi.x, pr.x), m.nd_over_2pi_f),
+                                   __fmul_rn(small_arg_f(pi.y, pr.y), m.nd_over_2pi_f));
         }
-        re = make_float2(a.x * fmaf(G0.x, cs.x, -G0.y * sn.x), a.y * fmaf(G1.x, cs.y, -G1.y * sn.y));
-        im = make_float2(a.x * fmaf(G0.y, cs.x, G0.x * sn.x), a.y * fmaf(G1.y, cs.y, G1.x * sn.y));
+        re = __fmul2_rn(a, __ffma2_rn(gx, cs, __fmul2_rn(gy, __fmul2_rn(sn, neg1))));
+        im = __fmul2_rn(a, __ffma2_rn(gy, cs, __fmul2_rn(gx, sn)));
     }
     bool refine0 = fabsf(gd.x) > k.gthr, refine1 = fabsf(gd.y) > k.gthr;
     int kb0 = 0, kb1 = 0;
