@@ -1017,7 +1017,7 @@ __device__ __forceinline__ int eval_fp64(const Model& m, const Fp64Const& k, con
 __device__ __forceinline__ long long fixed_from_f32(float v) {
     const float t = truncf(v);
     const float r = v - t;
-    const long long hi = (long long)__float2int_rz(t);
+    const long long hi = (long long)__float2int_rz(v);  // = (int) t, without waiting for t
     const long long lo = (long long)__float2int_rn(r * 2147483648.0f);
     return (long long)((unsigned long long)hi << 32) + lo * 2;
 }
@@ -1115,12 +1115,25 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
     const unsigned heads = __ballot_sync(kFull, !uniform || !link);  // bit 0 always set
     const int dist = lane - (31 - __clz(heads & (kFull >> (31 - lane))));
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    for (int d = 1; d < 8; d <<= 1) {
         const T ur = __shfl_up_sync(kFull, cr, d);
         const T ui = __shfl_up_sync(kFull, ci, d);
         if (dist >= d) {
             cr = ur + cr;
             ci = ui + ci;
+        }
+    }
+    // segments of more than 8 lanes are rare (a lane continues its left neighbour's last
+    // run and has no run end of its own): the last two steps only when the warp has one
+    if (__any_sync(kFull, dist >= 8)) {
+#pragma unroll
+        for (int d = 8; d < 32; d <<= 1) {
+            const T ur = __shfl_up_sync(kFull, cr, d);
+            const T ui = __shfl_up_sync(kFull, ci, d);
+            if (dist >= d) {
+                cr = ur + cr;
+                ci = ui + ci;
+            }
         }
     }
     T in_r = __shfl_up_sync(kFull, cr, 1), in_i = __shfl_up_sync(kFull, ci, 1);
