@@ -57,8 +57,10 @@
  *     a multiple of 2^-32 (a 64-bit integer) and the integers are summed, so results
  *     are bitwise reproducible run to run regardless of scheduling.  Valid while every
  *     contribution's |re|, |im| < 2^30 and every cell's sum stays within +-2^31; the
- *     library does not check this, and beyond it the values saturate or wrap silently
- *     (sea-surface facets give contributions of order sqrt(nrcs * area), a few units).
+ *     default build does not check this, and beyond it the values saturate or wrap
+ *     silently (sea-surface facets give contributions of order sqrt(nrcs * area), a few
+ *     units).  The debug build (rsim_check_build() == 1) reports an emitted sum at or
+ *     beyond 2^30 as RSIM_ERR_CHECK.
  */
 #ifndef RSIM_H
 #define RSIM_H
@@ -219,10 +221,10 @@ rsim_status rsim_doppler_accumulate(const rsim_radar *radar, const rsim_platform
 size_t rsim_batched_workspace_size(int32_t n_real, int32_t n_samples, int32_t n_gates,
                                    int32_t n_doppler);
 
-/* Blockwise summation into one exact fixed-point workspace, for a scatterer set that
+/* Blockwise summation into one deterministic fixed-point workspace, for a scatterer set that
  * arrives in blocks (streamed from host memory, or larger than device memory):
  *   rsim_workspace_clear, then rsim_doppler_accumulate_partial for every block (each adds
- *   its contributions to the workspace's exact sums; no clear, no conversion), then
+ *   its contributions to the workspace's fixed-point sums; no clear, no conversion), then
  *   rsim_workspace_finalize (adds the sums to the complex spectra, +=).
  * Blocks that start at multiples of rsim_block_scatterers() keep every scatterer's FP64
  * reference point, so the spectra are bit-identical to one rsim_doppler_accumulate call on
@@ -256,7 +258,7 @@ typedef struct {
  * (Algorithm 1 with the surface regenerated at every update): update update0 + s takes the
  * positions x, y and NRCS of `scat` (its origin and facet area; its z, vx, vy, vz and t0 are
  * not read and may be NULL / 0) with the heights, velocities and epoch of states[s], and
- * adds its spectrum to slot s of the exact fixed-point workspace (cleared before by
+ * adds its spectrum to slot s of the deterministic fixed-point workspace (cleared before by
  * rsim_workspace_clear, converted after by rsim_workspace_finalize).  One launch covers
  * the n_updates updates: the horizontal positions are read once, each update's heights and
  * velocities (16 bytes per scatterer) once per update.  Every (block, update) pair is
