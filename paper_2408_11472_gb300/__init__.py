@@ -217,7 +217,7 @@ def doppler_accumulate_states(radar, platform, scat: Scatterers, update0: int, s
                               workspace: Optional[torch.Tensor] = None, stream=None):
     """Spectra of updates update0 + s whose heights and velocities are states[s] = (z, vx, vy,
     vz, t0) (float32 [n] tensors and the epoch), the x, y and NRCS being ``scat``'s: added to
-    the exact workspace slots s (rsim_doppler_accumulate_states; clear and convert with
+    the fixed-point workspace slots s (rsim_doppler_accumulate_states; clear and convert with
     rsim_workspace_clear / rsim_workspace_finalize).  At most 64 states per call."""
     n = len(states)
     if n > _lib.MAX_STATES:
@@ -486,7 +486,7 @@ class HostStreamer:
     ``rsim_block_scatterers()``; "waves": one block per full wave of CTAs), block i+1
     copied while block i is summed (the summation
     adds, so the blocks' sums make the set's; every scatterer keeps its FP64 reference
-    point).  All blocks add into one exact workspace, so the spectra are bit-identical to a
+    point).  All blocks add into one fixed-point workspace, so the spectra are bit-identical to a
     single call on the whole set.  Buffers and workspace are allocated once.
 
     ``run(..., host_out=pinned)`` also reads the IQ back into a pinned host tensor on a
@@ -565,7 +565,7 @@ class HostStreamer:
         G, nbytes = radar.n_gates, self.ws.numel()
         rd, pf, prec = _lib.make_radar(radar), _lib.make_platform(platform), _prec(self.precision)
         st = _stream(cur)
-        # one exact fixed-point workspace for all blocks: the spectra are bit-identical to
+        # one fixed-point workspace for all blocks: the spectra are bit-identical to
         # a single call on the whole set
         _lib.check(_lib.lib.rsim_workspace_clear(S, G, n_doppler, _ptr(self.ws), nbytes, st))
         for (a, b), ev in zip(self.ranges, self.events):
@@ -719,7 +719,7 @@ def _evolving_spectra(radar, platform, surface: EvolvingSurface, u0: int, S: int
                       stream=None, groups=None, side=None, side2=None, ws2=None):
     """Spectra T[s] (+=) of updates u0 + s, the surface regenerated at each update, in blocks of
     K updates: the K surfaces are synthesised into K field sets, then one summation launch
-    (rsim_doppler_accumulate_states) adds the block's spectra to their slots of the exact
+    (rsim_doppler_accumulate_states) adds the block's spectra to their slots of the
     fixed-point workspace; one clear before, one conversion of all slots at the end.
 
     ``groups``: one or two lists of K field sets (default: one of min(S, EVOLVING_BLOCK)).
