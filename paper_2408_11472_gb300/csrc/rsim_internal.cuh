@@ -1114,8 +1114,12 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
     T cr = sr[J - 1], ci = si[J - 1];
     const unsigned heads = __ballot_sync(kFull, !uniform || !link);  // bit 0 always set
     const int dist = lane - (31 - __clz(heads & (kFull >> (31 - lane))));
+    // FP32: segments of more than 8 lanes are rare (a lane continues its left neighbour's
+    // last run and has no run end of its own), so the last two steps run only when the warp
+    // has one; the FP64 path (bound by its FP64 evaluation) keeps all five
+    constexpr int kFirstSteps = sizeof(T) == sizeof(float) ? 8 : 32;
 #pragma unroll
-    for (int d = 1; d < 8; d <<= 1) {
+    for (int d = 1; d < kFirstSteps; d <<= 1) {
         const T ur = __shfl_up_sync(kFull, cr, d);
         const T ui = __shfl_up_sync(kFull, ci, d);
         if (dist >= d) {
@@ -1123,9 +1127,7 @@ __device__ __forceinline__ void warp_reduce_emit(const int (&key)[J], const T (&
             ci = ui + ci;
         }
     }
-    // segments of more than 8 lanes are rare (a lane continues its left neighbour's last
-    // run and has no run end of its own): the last two steps only when the warp has one
-    if (__any_sync(kFull, dist >= 8)) {
+    if (kFirstSteps < 32 && __any_sync(kFull, dist >= 8)) {
 #pragma unroll
         for (int d = 8; d < 32; d <<= 1) {
             const T ur = __shfl_up_sync(kFull, cr, d);
