@@ -237,8 +237,14 @@ def main():
                     help="skip the e2e / regular / FP64 / oracle legs (profiling runs)")
     ap.add_argument("--config", default=None, choices=["0", "2", "3", "4", "nfast", "antenna", "dda", "surface"],
                     help="run another measurement configuration instead (bench_configs.py)")
+    ap.add_argument("--profile-target", default=None, choices=["surface", "antenna"],
+                    help="only run a small repeatable workload for a one-kernel ncu capture")
     args = ap.parse_args()
 
+    if args.profile_target is not None:
+        import bench_configs
+        bench_configs.profile_target(args.profile_target, reps=4)
+        return
     if args.config is not None:
         import bench_configs
         print(json.dumps(bench_configs.run(args.config, args)), flush=True)

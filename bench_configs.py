@@ -816,3 +816,48 @@ def run(k: str, args):
     line["clocks"] = clocks.stop(windows=list(_TIMED_WINDOWS))
     line["clocks"]["timed_regions"] = len(_TIMED_WINDOWS)
     return line
+
+
+# ------------------------------------------------------------------ ncu capture targets
+def profile_target(kind: str, reps: int = 4):
+    """Small, repeatable workloads for one-kernel ncu captures (no JSON line, no timing
+    contract): `reps` untimed calls, then one timed call whose CUDA-event time is printed.
+      surface  syntheses of the 2048 x 2048 evolving surface at successive times
+               (surf_rows_kernel, surf_cols_kernel);
+      antenna  the 2048 x 2048 fast-mode pass with the 129 x 129 tabulated pattern
+               (accumulate_split_kernel<DOPPLER, ANT>).
+    Device memory: about 0.4 GB (surface) or 1 GB (antenna)."""
+    import dataclasses
+    import torch
+    import paper_2408_11472_gb300 as rsim
+    torch.cuda.set_device(0)
+    c = sg.config(1)
+    rd0, pf, fp, P, L = c["radar"], c["platform"], c["fast"], c["n_pulses"], c["L"]
+    if kind == "surface":
+        surf = rsim.EvolvingSurface(sg.sea_spectrum(L, c["seed"]))
+
+        def call(r):
+            surf.at(0.01 * r)
+    elif kind == "antenna":
+        rd = dataclasses.replace(rd0, antenna=sg.antenna_table(77))
+        dev = rsim.Scatterers.from_arrays(sg.sea_surface(L, c["seed"]))
+        S = (P - 1) // fp.n_fast + 2
+        ws = torch.empty(rsim.workspace_size(S, rd.n_gates, fp.n_doppler), dtype=torch.uint8,
+                         device="cuda")
+        T = torch.zeros((S, rd.n_gates, fp.n_doppler), dtype=torch.complex64, device="cuda")
+
+        def call(r):
+            T.zero_()
+            rsim.doppler_accumulate(rd, pf, dev, 0, S, fp.n_fast, fp.n_doppler, "split", out=T,
+                                    workspace=ws)
+    else:
+        raise ValueError("unknown profile target %r" % kind)
+    for r in range(reps):
+        call(r)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call(reps)
+    e1.record()
+    torch.cuda.synchronize()
+    print("%s: %.4f ms per call" % (kind, e0.elapsed_time(e1)), flush=True)
